@@ -1,0 +1,244 @@
+/*
+ * mars.h: C ABI of the GB300 (sm_103a) MARS library.
+ *
+ * MARS, "Mean-field Annealing from a Random State" (Yavorsky, Markovich,
+ * Polyakov, Rubtsov, arXiv 1907.05124), searches for low-energy spin states of
+ * the Ising problem of Section 2, Eq. 2:
+ *
+ *     E(sigma) = sum_{i<j} J_ij sigma_i sigma_j + sum_i h_i sigma_i,
+ *
+ * with J symmetric, zero diagonal, sigma in {-1,+1}^n. (Eq. 2 sums each pair
+ * twice; this library reports every pair once, so Eq. 2's value is
+ * 2E - sum_i h_i sigma_i.) Max-cut with weights w is the same problem with
+ * J = w; its cut (Eq. 3) is (sum_{i<j} w_ij - E) / 2 when h = 0.
+ *
+ * The method (Section 3, Algorithm 1) runs many independent replicas. Each
+ * starts from s_i ~ U(-1,1) and a start temperature t0 ~ U(t_min, t_max),
+ * lowers T by c_step while T stays positive, and at each temperature repeats
+ * sweeps  s_i <- -tanh(Phi_i / T),  Phi_i = sum_j J_ij s_j + h_i,  until the
+ * largest change d of a sweep is at most d_min (or k_max sweeps were done).
+ * The final s is rounded to spins (sign(0) = +1) and the best replica kept.
+ *
+ * A sweep visits the spins sequentially, each new s_i used at once by the
+ * spins after it (Gauss-Seidel: the per-spin update of Section 3). The visiting
+ * order is a property of the instance (see mars_instance_csr). The synchronous
+ * reading of Algorithm 1's listing is available as MARS_UPDATE_JACOBI.
+ *
+ * Conventions for every call:
+ *  - Return value: MARS_OK (0) or a negative mars_status; the message of the
+ *    last failure is available from mars_last_error. The library never aborts
+ *    the process.
+ *  - Pointers are host pointers unless the call's flags hold MARS_DEVICE_PTR,
+ *    in which case they are device pointers on the context's device. Inputs are
+ *    read during the call only and copied; the caller keeps ownership of every
+ *    buffer it passes.
+ *  - Work is ordered on the CUDA stream given to mars_create. Blocking calls
+ *    (mars_solve, mars_energy, mars_draw_replicas) synchronise that stream
+ *    before they return.
+ *  - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef MARS_H
+#define MARS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mars_ctx mars_ctx;
+
+typedef enum {
+    MARS_OK = 0,
+    MARS_EINVAL = -1,    /* bad argument: asymmetric J, non-zero diagonal, bad CSR, ... */
+    MARS_ENOMEM = -2,    /* device allocation failed or the HBM budget would be exceeded */
+    MARS_EAGAIN = -3,    /* result not ready yet (non-blocking calls) */
+    MARS_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+    MARS_EDEVICE = -5,   /* a CUDA call failed */
+    MARS_ENOTFOUND = -6  /* unknown instance or request id */
+} mars_status;
+
+typedef enum { MARS_I8 = 1, MARS_F32 = 2, MARS_F64 = 3 } mars_dtype;
+
+enum { MARS_DEVICE_PTR = 1u };
+
+typedef enum { MARS_UPDATE_GS = 0, MARS_UPDATE_JACOBI = 1 } mars_update;
+
+typedef enum {
+    MARS_FP32 = 0,  /* local fields in FP32 (the parity path) */
+    MARS_BF16 = 1,  /* dense J*m with BF16 operands, FP32 accumulation */
+    MARS_FP8 = 2    /* dense J*m with E4M3 operands (integer J only), FP32 accumulation */
+} mars_precision;
+
+/*
+ * Create a context on CUDA device `device`. hbm_budget_bytes caps the device
+ * memory the context holds at any time (0 = no cap). cuda_stream is a
+ * cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream) or NULL for a
+ * stream the context creates and owns.
+ */
+int mars_create(mars_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+
+/* Release every instance and buffer of the context. NULL is ignored. */
+void mars_destroy(mars_ctx* ctx);
+
+/* Message of the last failed call on this context (never NULL). */
+const char* mars_last_error(mars_ctx* ctx);
+
+/*
+ * Register a dense instance (Section 2, Eq. 2). J is n*n row-major of type jt
+ * (MARS_I8, MARS_F32 or MARS_F64) and must be exactly symmetric with a zero
+ * diagonal; h (n doubles, host) may be NULL for h = 0. order (n int32, host,
+ * nullable) is the sweep's spin visiting order, a permutation of 0..n-1;
+ * NULL means 0..n-1. On success *inst receives the instance id.
+ * Errors: MARS_EINVAL (n <= 0, asymmetric J, non-zero diagonal, non-finite
+ * value, order not a permutation), MARS_ENOMEM, MARS_EDEVICE.
+ */
+int mars_instance_dense(mars_ctx* ctx, int32_t n, const void* J, int32_t jt, const double* h,
+                        const int32_t* order, uint32_t flags, int32_t* inst);
+
+/*
+ * Register a sparse instance in CSR form: row_ptr (n+1 int32, row_ptr[0] = 0,
+ * non-decreasing, row_ptr[n] = nnz), col (nnz int32 in [0, n), no repeated
+ * column in a row, no diagonal entry), val (nnz of type vt). Both directions
+ * of every coupling must be present with the same value. h (n doubles, host)
+ * may be NULL. order (n int32, host) is the sweep's visiting order; NULL asks
+ * the library for a greedy colouring order (colour classes in turn, index
+ * order within a class; mars_instance_order returns it). Any order gives the
+ * same result as a strictly sequential sweep in that order: spins whose
+ * earlier-visited neighbours are all settled are updated together.
+ * Errors: MARS_EINVAL (bad CSR, asymmetry, diagonal, order), MARS_ENOMEM,
+ * MARS_EDEVICE.
+ */
+int mars_instance_csr(mars_ctx* ctx, int32_t n, int64_t nnz, const int32_t* row_ptr,
+                      const int32_t* col, const void* val, int32_t vt, const double* h,
+                      const int32_t* order, uint32_t flags, int32_t* inst);
+
+/* Release an instance's device data. Errors: MARS_ENOTFOUND. */
+int mars_instance_free(mars_ctx* ctx, int32_t inst);
+
+typedef struct {
+    int32_t n;
+    int32_t dense;           /* 1 for a dense instance, 0 for CSR */
+    int64_t nnz;             /* stored off-diagonal couplings (both directions) */
+    int32_t levels;          /* parallel steps of one sweep (colour classes for a colour order) */
+    int32_t integer;         /* 1 if every J_ij and h_i is an integer: energies are exact int64 */
+    double total_weight;     /* sum_{i<j} J_ij, for cut = (total_weight - E) / 2 */
+    int64_t device_bytes;    /* device memory held by the instance */
+} mars_instance_info;
+
+/* Describe an instance. Errors: MARS_ENOTFOUND. */
+int mars_instance_get_info(mars_ctx* ctx, int32_t inst, mars_instance_info* info);
+
+/* Copy the instance's sweep order (n int32, host) into order_out. */
+int mars_instance_order(mars_ctx* ctx, int32_t inst, int32_t* order_out);
+
+/*
+ * Parameters of one solve (Section 3, Algorithm 1; the paper uses c_step = 1
+ * and d_min = 1e-4 for every experiment, Section 4.1).
+ *  replicas      number of independent descents R (>= 1)
+ *  t_min, t_max  start temperatures are drawn uniformly from [t_min, t_max]
+ *  c_step        temperature decrement per level (> 0); t_max / c_step and every
+ *                t0 / c_step must be at most 1e6 (levels per replica)
+ *  d_min         a level ends when the sweep's largest |change| is <= d_min
+ *  k_max         cap on sweeps per level (>= 1); capped levels are counted
+ *  fixed_sweeps  > 0: exactly this many sweeps per level instead of the rule
+ *  seed, stream  counter-based start-state draw: Philox4x32-10 with key
+ *                (seed low word, seed high word); s_i of replica r is
+ *                2u-1 with u = (word (i mod 4) of Philox(i/4, r, 0, stream) >> 8) 2^-24;
+ *                t0_r = float(t_min + u (t_max - t_min)) with u from word 0 of
+ *                Philox(0, r, 1, stream), in double without fused operations
+ *  update        MARS_UPDATE_GS (default) or MARS_UPDATE_JACOBI
+ *  precision     mars_precision of the local-field product
+ *  m0, t0        optional caller start states: m0 R*n floats (replica-major,
+ *                original spin labels, values in [-1, 1]) and t0 R floats;
+ *                NULL draws them as above
+ *  flags         MARS_DEVICE_PTR if m0/t0 are device pointers
+ */
+typedef struct {
+    int32_t replicas;
+    double t_min, t_max, c_step, d_min;
+    int32_t k_max;
+    int32_t fixed_sweeps;
+    uint64_t seed;
+    uint32_t stream;
+    int32_t update;
+    int32_t precision;
+    const float* m0;
+    const float* t0;
+    uint32_t flags;
+} mars_params;
+
+/* Fill p with the paper's defaults: c_step 1, d_min 1e-4, k_max 1000, GS, FP32. */
+void mars_params_default(mars_params* p);
+
+/*
+ * Optional per-replica outputs of a solve. Every pointer may be NULL. With
+ * MARS_DEVICE_PTR in flags they are device pointers, else host pointers.
+ *  energies  R doubles       exact energy of each replica's spins
+ *  spins     R*n int8        each replica's sign-rounded spins (original labels)
+ *  m_final   R*n float       each replica's final magnetisation (original labels)
+ *  t0        R float         the start temperatures used
+ *  sweeps    R int32         sweeps done;  levels: R int32 levels visited;
+ *  capped    R int32         levels ended by k_max
+ */
+typedef struct {
+    double* energies;
+    int8_t* spins;
+    float* m_final;
+    float* t0;
+    int32_t* sweeps;
+    int32_t* levels;
+    int32_t* capped;
+    uint32_t flags;
+} mars_outputs;
+
+typedef struct {
+    double best_energy;       /* E of the best replica (exact; see energy_err_bound) */
+    int64_t best_energy_i64;  /* the same as an integer when the instance is integer */
+    double best_cut;          /* (total_weight - best_energy) / 2: the max-cut value when h = 0 */
+    int32_t best_replica;     /* lowest replica index among those with the best energy */
+    int32_t hits;             /* replicas whose energy equals the best */
+    double mean_energy;       /* mean energy over replicas */
+    int64_t sweeps;           /* sweeps over all replicas */
+    int64_t spin_updates;     /* sum over sweeps of n (one s_i per spin per sweep) */
+    int64_t levels;           /* temperature levels over all replicas */
+    int64_t capped_levels;    /* levels ended by k_max */
+    double gpu_seconds;       /* device time of the solve (CUDA events) */
+    double descent_seconds;   /* device time of the descent kernel alone */
+    double energy_err_bound;  /* 0 when energies are exact */
+    int32_t status;           /* MARS_OK or the device-side error */
+    int32_t integer;          /* 1 if energies are exact integers */
+} mars_result;
+
+/*
+ * Run MARS on an instance and block until done. best_spins (n int8, host,
+ * nullable) receives the best replica's spins in the caller's labels.
+ * outputs and result may be NULL. Errors: MARS_EINVAL (bad parameters),
+ * MARS_ENOTFOUND, MARS_ENOMEM, MARS_ETIMEOUT, MARS_EDEVICE.
+ */
+int mars_solve(mars_ctx* ctx, int32_t inst, const mars_params* params, int8_t* best_spins,
+               const mars_outputs* outputs, mars_result* result);
+
+/*
+ * Exact energies (Section 2, Eq. 2, pairs once) of count spin vectors
+ * (count*n int8, entries +-1, caller labels). e (count doubles) receives the
+ * energy rounded once to the nearest double; e_i64 (nullable) receives it as
+ * an integer for integer instances. spins/e/e_i64 follow flags. Errors:
+ * MARS_EINVAL (an entry not +-1), MARS_ENOTFOUND, MARS_EDEVICE.
+ */
+int mars_energy(mars_ctx* ctx, int32_t inst, const int8_t* spins, int32_t count, double* e,
+                int64_t* e_i64, uint32_t flags);
+
+/*
+ * The start-state draw alone (see mars_params): replicas r0 .. r0+R-1 with n
+ * spins. m0 (R*n floats) and t0 (R floats) follow flags; either may be NULL.
+ */
+int mars_draw_replicas(mars_ctx* ctx, uint64_t seed, uint32_t stream, int32_t r0, int32_t R,
+                       int32_t n, double t_min, double t_max, float* m0, float* t0,
+                       uint32_t flags);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

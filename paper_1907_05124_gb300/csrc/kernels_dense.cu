@@ -1,0 +1,158 @@
+// Dense MARS descent (Section 3, Algorithm 1) in FP32 on the SIMT cores.
+//
+// One warp carries one replica through the whole descent. A sweep visits the
+// spins one after another (Gauss-Seidel: every spin shares a coupling with
+// every other, so there is no parallelism inside one replica's sweep); the
+// warp spreads each local field Phi_a = sum_b J_ab s_b over its 32 lanes and
+// reduces it with shuffles. The replica's magnetisations stay in shared memory
+// when they fit, J is read through the read-only cache and shared by every
+// warp on the SM. This is the plain FP32 path the tensor-core path is checked
+// against; it is exact in its arithmetic order, not fast for large n.
+#include "device_common.cuh"
+#include "mars_internal.h"
+
+#include <algorithm>
+
+namespace mars {
+namespace {
+
+constexpr int kDenseWarps = 4;
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    return v;
+}
+
+template <bool ONCHIP, bool JACOBI>
+__global__ void __launch_bounds__(kDenseWarps * 32) dense_descent_kernel(DevInstance in, DevSolve s)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * kDenseWarps + warp;
+    if (r >= s.R) return;  // whole warp leaves; the kernel has no block barrier
+    const int n = in.n;
+    const int per = n * (JACOBI ? 2 : 1);
+    float* m = ONCHIP ? smem + (size_t)warp * per : s.m_scratch + (size_t)r * per;
+    float* mn = JACOBI ? m + n : m;
+
+    for (int a = lane; a < n; a += 32) {
+        const int o = __ldg(in.new2old + a);
+        m[a] = s.m0 ? __ldg(s.m0 + (size_t)r * n + o) : draw_m0(s.seed, s.stream, r, o);
+    }
+    __syncwarp();
+
+    double T = (double)s.t0[r] - s.c_step;
+    bool act = T > 0.0;
+    float invT = act ? (float)(1.0 / T) : 0.f;
+    int levels = act ? 1 : 0, sweeps = 0, capped = 0, lvl_sweeps = 0;
+
+    while (act) {
+        float d = 0.f;
+        for (int a = 0; a < n; ++a) {
+            const float* Jrow = in.Jf + (size_t)a * n;
+            float p = 0.f;
+            for (int b = lane; b < n; b += 32) p = fmaf(__ldg(Jrow + b), m[b], p);
+            p = warp_sum(p);
+            if (in.h) p += __ldg(in.h + a);
+            const float sn = -tanhf(p * invT);
+            d = fmaxf(d, fabsf(sn - m[a]));
+            __syncwarp();
+            if (lane == 0) mn[a] = sn;
+            __syncwarp();
+        }
+        if (JACOBI) {
+            for (int a = lane; a < n; a += 32) m[a] = mn[a];
+            __syncwarp();
+        }
+        ++sweeps;
+        ++lvl_sweeps;
+        const bool level_done = s.fixed_sweeps > 0 ? lvl_sweeps >= s.fixed_sweeps
+                                                   : (d <= s.d_min || lvl_sweeps >= s.k_max);
+        if (level_done) {
+            if (s.fixed_sweeps == 0 && !(d <= s.d_min)) ++capped;
+            T = T - s.c_step;
+            lvl_sweeps = 0;
+            if (T > 0.0) {
+                ++levels;
+                invT = (float)(1.0 / T);
+            } else {
+                act = false;
+            }
+        }
+    }
+
+    // sign-round, outputs and exact energy (pairs a < b once, plus the field)
+    long long ei = 0;
+    double ef = 0.0;
+    for (int a = lane; a < n; a += 32) {
+        const int sa = m[a] >= 0.f ? 1 : -1;
+        const int o = __ldg(in.new2old + a);
+        s.sigma[(size_t)r * n + o] = (int8_t)sa;
+        if (s.m_final) s.m_final[(size_t)r * n + o] = m[a];
+        if (in.integer) {
+            const int8_t* row = in.J_i8 + (size_t)a * n;
+            long long acc = 0;
+            for (int b = a + 1; b < n; ++b) acc += (int)row[b] * (m[b] >= 0.f ? 1 : -1);
+            ei += acc * sa;
+            if (in.h) ei += (long long)__ldg(in.h + a) * sa;
+        } else {
+            const double* row = in.J_f64 + (size_t)a * n;
+            double acc = 0.0;
+            for (int b = a + 1; b < n; ++b) acc += row[b] * (m[b] >= 0.f ? 1.0 : -1.0);
+            ef += acc * sa;
+            if (in.h_f64) ef += __ldg(in.h_f64 + a) * sa;
+        }
+    }
+    ei = warp_reduce_strided<1>(ei, SumOp());
+    ef = warp_reduce_strided<1>(ef, SumOp());
+    if (lane == 0) {
+        s.energy[r] = in.integer ? (double)ei : ef;
+        s.energy_i64[r] = in.integer ? ei : 0;
+        s.sweeps[r] = sweeps;
+        s.levels[r] = levels;
+        s.capped[r] = capped;
+    }
+}
+
+const void* pick(bool onchip, bool jacobi)
+{
+    if (onchip) return jacobi ? (const void*)dense_descent_kernel<true, true>
+                              : (const void*)dense_descent_kernel<true, false>;
+    return jacobi ? (const void*)dense_descent_kernel<false, true>
+                  : (const void*)dense_descent_kernel<false, false>;
+}
+
+}  // namespace
+
+DensePlan plan_dense(const DevInstance& in, int R, int jacobi, int device)
+{
+    int optin = 48 * 1024;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    DensePlan p;
+    p.warps_per_block = kDenseWarps;
+    const size_t per_warp = (size_t)in.n * sizeof(float) * (jacobi ? 2 : 1);
+    p.onchip = per_warp * kDenseWarps <= (size_t)optin - 4096;
+    p.smem = p.onchip ? per_warp * kDenseWarps : 0;
+    p.grid = (R + kDenseWarps - 1) / kDenseWarps;
+    p.scratch_floats = p.onchip ? 0 : (size_t)R * in.n * (jacobi ? 2 : 1);
+    return p;
+}
+
+cudaError_t launch_dense(const DevInstance& in, const DevSolve& s, const DensePlan& p,
+                         cudaStream_t st)
+{
+    const void* k = pick(p.onchip != 0, s.jacobi != 0);
+    if (p.smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)p.smem);
+        if (e != cudaSuccess) return e;
+    }
+    DevInstance a = in;
+    DevSolve b = s;
+    void* args[] = {&a, &b};
+    return cudaLaunchKernel(k, dim3(p.grid), dim3(kDenseWarps * 32), args, p.smem, st);
+}
+
+}  // namespace mars

@@ -1,0 +1,202 @@
+// Start-state draw, best-replica selection and energies of given spins.
+//
+// The best replica is the lowest index among the replicas of minimum energy
+// (Section 3: the best result of the sample is kept); hits counts the
+// replicas that reach it, as the paper's success probability P does
+// (Section 4.2). Energies are Eq. 2 with each pair counted once.
+#include "device_common.cuh"
+#include "mars_internal.h"
+
+#include <cfloat>
+#include <climits>
+
+namespace mars {
+namespace {
+
+__global__ void draw_kernel(uint64_t seed, uint32_t stream, int32_t r0, int32_t R, int32_t n,
+                            double t_min, double t_max, float* m0, float* t0)
+{
+    const size_t total = (size_t)R * n;
+    const size_t step = (size_t)gridDim.x * blockDim.x;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += step) {
+        const uint32_t q = (uint32_t)(idx / n), i = (uint32_t)(idx % n);
+        if (m0) m0[idx] = draw_m0(seed, stream, (uint32_t)r0 + q, i);
+    }
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < (size_t)R; q += step)
+        if (t0) t0[q] = draw_t0(seed, stream, (uint32_t)(r0 + q), t_min, t_max);
+}
+
+constexpr int kBestThreads = 1024;
+
+__global__ void __launch_bounds__(kBestThreads) best_kernel(DevSolve s, int32_t n, int32_t integer,
+                                                            int8_t* best_spins, DevResult* res)
+{
+    __shared__ double s_e[32];
+    __shared__ int s_r[32];
+    __shared__ double s_sum[32];
+    __shared__ long long s_cnt[32][4];
+    __shared__ int s_best;
+    __shared__ double s_beste;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double be = DBL_MAX;
+    int br = INT_MAX;
+    for (int r = tid; r < s.R; r += kBestThreads) {
+        const double e = s.energy[r];
+        if (e < be || (e == be && r < br)) { be = e; br = r; }
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const double oe = __shfl_xor_sync(0xffffffffu, be, m);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, m);
+        if (oe < be || (oe == be && orr < br)) { be = oe; br = orr; }
+    }
+    if (lane == 0) { s_e[warp] = be; s_r[warp] = br; }
+    __syncthreads();
+    if (tid == 0) {
+        double e = DBL_MAX;
+        int rr = INT_MAX;
+        for (int w = 0; w < kBestThreads / 32; ++w)
+            if (s_e[w] < e || (s_e[w] == e && s_r[w] < rr)) { e = s_e[w]; rr = s_r[w]; }
+        s_best = rr;
+        s_beste = e;
+    }
+    __syncthreads();
+    const int best = s_best;
+    const double beste = s_beste;
+    double sum = 0.0;
+    long long hits = 0, sw = 0, lv = 0, cp = 0;
+    for (int r = tid; r < s.R; r += kBestThreads) {
+        const double e = s.energy[r];
+        sum += e;
+        hits += (e == beste);
+        sw += s.sweeps[r];
+        lv += s.levels[r];
+        cp += s.capped[r];
+    }
+    sum = warp_reduce_strided<1>(sum, SumOp());
+    hits = warp_reduce_strided<1>(hits, SumOp());
+    sw = warp_reduce_strided<1>(sw, SumOp());
+    lv = warp_reduce_strided<1>(lv, SumOp());
+    cp = warp_reduce_strided<1>(cp, SumOp());
+    if (lane == 0) {
+        s_sum[warp] = sum;
+        s_cnt[warp][0] = hits;
+        s_cnt[warp][1] = sw;
+        s_cnt[warp][2] = lv;
+        s_cnt[warp][3] = cp;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double ts = 0.0;
+        long long c[4] = {0, 0, 0, 0};
+        for (int w = 0; w < kBestThreads / 32; ++w) {
+            ts += s_sum[w];
+            for (int q = 0; q < 4; ++q) c[q] += s_cnt[w][q];
+        }
+        res->best_energy = beste;
+        res->best_energy_i64 = integer ? s.energy_i64[best] : 0;
+        res->best_replica = best;
+        res->hits = (int32_t)c[0];
+        res->sum_energy = ts;
+        res->sweeps = c[1];
+        res->levels = c[2];
+        res->capped = c[3];
+    }
+    if (best_spins && best >= 0 && best < s.R)
+        for (int i = tid; i < n; i += kBestThreads) best_spins[i] = s.sigma[(size_t)best * n + i];
+}
+
+constexpr int kEnergyThreads = 256;
+
+__global__ void __launch_bounds__(kEnergyThreads) energy_kernel(DevInstance in, const int8_t* spins,
+                                                                double* e, long long* e_i64,
+                                                                int32_t* status)
+{
+    __shared__ long long s_i[kEnergyThreads / 32];
+    __shared__ double s_f[kEnergyThreads / 32];
+    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = in.n;
+    const int8_t* sp = spins + (size_t)c * n;
+    long long ei = 0;
+    double ef = 0.0;
+    for (int a = tid; a < n; a += kEnergyThreads) {
+        const int sa = sp[__ldg(in.new2old + a)];
+        if (sa != 1 && sa != -1) { atomicExch(status, (int)kDevBadIndex); continue; }
+        if (in.dense) {
+            if (in.integer) {
+                const int8_t* row = in.J_i8 + (size_t)a * n;
+                long long acc = 0;
+                for (int b = a + 1; b < n; ++b) acc += (int)row[b] * (int)sp[__ldg(in.new2old + b)];
+                ei += acc * sa;
+            } else {
+                const double* row = in.J_f64 + (size_t)a * n;
+                double acc = 0.0;
+                for (int b = a + 1; b < n; ++b) acc += row[b] * (double)sp[__ldg(in.new2old + b)];
+                ef += acc * sa;
+            }
+        } else {
+            const int e0 = __ldg(in.row_ptr + a), e1 = __ldg(in.row_ptr + a + 1);
+            if (in.integer) {
+                long long acc = 0;
+                for (int q = e0; q < e1; ++q) {
+                    const int b = __ldg(in.col + q);
+                    if (b > a) acc += (int)__ldg(in.val_i8 + q) * (int)sp[__ldg(in.new2old + b)];
+                }
+                ei += acc * sa;
+            } else {
+                double acc = 0.0;
+                for (int q = e0; q < e1; ++q) {
+                    const int b = __ldg(in.col + q);
+                    if (b > a) acc += __ldg(in.val_f64 + q) * (double)sp[__ldg(in.new2old + b)];
+                }
+                ef += acc * sa;
+            }
+        }
+        if (in.integer) {
+            if (in.h) ei += (long long)__ldg(in.h + a) * sa;
+        } else if (in.h_f64) {
+            ef += __ldg(in.h_f64 + a) * sa;
+        }
+    }
+    ei = warp_reduce_strided<1>(ei, SumOp());
+    ef = warp_reduce_strided<1>(ef, SumOp());
+    if (lane == 0) { s_i[warp] = ei; s_f[warp] = ef; }
+    __syncthreads();
+    if (tid == 0) {
+        long long ti = 0;
+        double tf = 0.0;
+        for (int w = 0; w < kEnergyThreads / 32; ++w) { ti += s_i[w]; tf += s_f[w]; }
+        e[c] = in.integer ? (double)ti : tf;
+        if (e_i64) e_i64[c] = in.integer ? ti : 0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_draw(uint64_t seed, uint32_t stream, int32_t r0, int32_t R, int32_t n,
+                        double t_min, double t_max, float* m0, float* t0, cudaStream_t st)
+{
+    const size_t total = (size_t)R * (n > 0 ? n : 1);
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    draw_kernel<<<blocks, 256, 0, st>>>(seed, stream, r0, R, n, t_min, t_max, m0, t0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_best(const DevSolve& s, int32_t n, int32_t integer, int8_t* best_spins,
+                        DevResult* res, cudaStream_t st)
+{
+    best_kernel<<<1, kBestThreads, 0, st>>>(s, n, integer, best_spins, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const DevInstance& in, const int8_t* spins, int32_t count, double* e,
+                          long long* e_i64, int32_t* status, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    energy_kernel<<<count, kEnergyThreads, 0, st>>>(in, spins, e, e_i64, status);
+    return cudaGetLastError();
+}
+
+}  // namespace mars

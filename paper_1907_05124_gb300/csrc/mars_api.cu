@@ -1,0 +1,812 @@
+// Host runtime behind the C ABI of include/mars.h: contexts, instance ingest
+// (validation, sweep order, level schedule, relabelling, device upload),
+// solve orchestration and result readback. All arithmetic of the method runs
+// in the kernels; this file moves data and makes decisions about launches.
+#include "../../include/mars.h"
+#include "mars_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace mars;
+
+// Upper bound on temperature levels per replica (t0 / c_step), so that every
+// descent ends and T - c_step always lowers T in double precision.
+static constexpr double kMaxLevels = 1e6;
+
+namespace {
+
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Instance {
+    DevInstance dev;
+    std::vector<int32_t> order;     // caller's visiting order (new label a visits order[a]... see build)
+    std::vector<DevMem> mem;
+    mars_instance_info info{};
+    double abs_weight = 0.0;        // sum_{i<j} |J_ij| + sum |h_i| (error bound of float energies)
+};
+
+}  // namespace
+
+struct mars_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+    size_t used = 0;
+    int sms = 0;
+    std::string err = "no error";
+    std::map<int32_t, std::unique_ptr<Instance>> insts;
+    int32_t next_id = 1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+};
+
+namespace {
+
+int fail(mars_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define MARS_CUDA(c, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((c), MARS_EDEVICE, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int dev_alloc(mars_ctx* c, size_t bytes, DevMem* out)
+{
+    out->p = nullptr;
+    out->bytes = 0;
+    if (bytes == 0) return MARS_OK;
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(c, MARS_ENOMEM, "HBM budget exceeded: %zu + %zu > %zu bytes", c->used, bytes,
+                    c->budget);
+    cudaError_t e = cudaMallocAsync(&out->p, bytes, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MARS_ENOMEM, "device allocation of %zu bytes failed: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    out->bytes = bytes;
+    c->used += bytes;
+    return MARS_OK;
+}
+
+void dev_free(mars_ctx* c, DevMem* m)
+{
+    if (m->p) {
+        cudaFreeAsync(m->p, c->stream);
+        c->used -= m->bytes;
+    }
+    m->p = nullptr;
+    m->bytes = 0;
+}
+
+// RAII set of device buffers freed at scope exit (stream-ordered).
+struct Scratch {
+    mars_ctx* c;
+    std::vector<DevMem> bufs;
+    explicit Scratch(mars_ctx* ctx) : c(ctx) {}
+    ~Scratch()
+    {
+        for (auto& b : bufs) dev_free(c, &b);
+    }
+    template <typename T>
+    int get(size_t count, T** out)
+    {
+        DevMem m;
+        int rc = dev_alloc(c, count * sizeof(T), &m);
+        if (rc) return rc;
+        bufs.push_back(m);
+        *out = (T*)m.p;
+        return MARS_OK;
+    }
+};
+
+template <typename T>
+int upload(mars_ctx* c, Instance* in, const std::vector<T>& v, const T** out)
+{
+    *out = nullptr;
+    if (v.empty()) return MARS_OK;
+    DevMem m;
+    int rc = dev_alloc(c, v.size() * sizeof(T), &m);
+    if (rc) return rc;
+    in->mem.push_back(m);
+    MARS_CUDA(c, cudaMemcpyAsync(m.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                 c->stream));
+    *out = (const T*)m.p;
+    return MARS_OK;
+}
+
+// Copy `count` elements from host or device memory into a host vector.
+template <typename T>
+int fetch(mars_ctx* c, const void* src, size_t count, bool device, std::vector<T>* out)
+{
+    out->resize(count);
+    if (count == 0) return MARS_OK;
+    if (device) {
+        MARS_CUDA(c, cudaMemcpyAsync(out->data(), src, count * sizeof(T), cudaMemcpyDeviceToHost,
+                                     c->stream));
+        MARS_CUDA(c, cudaStreamSynchronize(c->stream));
+    } else {
+        std::memcpy(out->data(), src, count * sizeof(T));
+    }
+    return MARS_OK;
+}
+
+int fetch_values(mars_ctx* c, const void* src, size_t count, int32_t dt, bool device,
+                 std::vector<double>* out)
+{
+    int rc;
+    switch (dt) {
+    case MARS_I8: {
+        std::vector<int8_t> v;
+        if ((rc = fetch(c, src, count, device, &v))) return rc;
+        out->assign(v.begin(), v.end());
+        return MARS_OK;
+    }
+    case MARS_F32: {
+        std::vector<float> v;
+        if ((rc = fetch(c, src, count, device, &v))) return rc;
+        out->assign(v.begin(), v.end());
+        return MARS_OK;
+    }
+    case MARS_F64:
+        return fetch(c, src, count, device, out);
+    default:
+        return fail(c, MARS_EINVAL, "unknown value type %d", dt);
+    }
+}
+
+int check_order(mars_ctx* c, const int32_t* order, int32_t n, std::vector<int32_t>* out)
+{
+    out->resize(n);
+    if (!order) {
+        std::iota(out->begin(), out->end(), 0);
+        return MARS_OK;
+    }
+    std::vector<char> seen(n, 0);
+    for (int32_t q = 0; q < n; ++q) {
+        const int32_t v = order[q];
+        if (v < 0 || v >= n || seen[v]) return fail(c, MARS_EINVAL, "order is not a permutation");
+        seen[v] = 1;
+        (*out)[q] = v;
+    }
+    return MARS_OK;
+}
+
+bool is_small_int(double v, double lim) { return v == std::floor(v) && std::fabs(v) <= lim; }
+
+int finish_register(mars_ctx* c, std::unique_ptr<Instance> in, int32_t* inst)
+{
+    in->info.device_bytes = 0;
+    for (auto& m : in->mem) in->info.device_bytes += (int64_t)m.bytes;
+    const int32_t id = c->next_id++;
+    c->insts[id] = std::move(in);
+    if (inst) *inst = id;
+    return MARS_OK;
+}
+
+// Frees the device buffers of an instance whose registration failed.
+struct InstGuard {
+    mars_ctx* c;
+    Instance* in;
+    bool done = false;
+    ~InstGuard()
+    {
+        if (!done)
+            for (auto& m : in->mem) dev_free(c, &m);
+    }
+};
+
+Instance* find(mars_ctx* c, int32_t id)
+{
+    auto it = c->insts.find(id);
+    return it == c->insts.end() ? nullptr : it->second.get();
+}
+
+}  // namespace
+
+extern "C" {
+
+int mars_create(mars_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream)
+{
+    if (!out) return MARS_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return MARS_EDEVICE;
+    }
+    auto c = std::make_unique<mars_ctx>();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    DeviceGuard g(device);
+    if (cudaFree(nullptr) != cudaSuccess) return MARS_EDEVICE;  // create the primary context
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return MARS_EDEVICE;
+        c->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+        cudaEventCreate(&c->ev2) != cudaSuccess)
+        return MARS_EDEVICE;
+    *out = c.release();
+    return MARS_OK;
+}
+
+void mars_destroy(mars_ctx* c)
+{
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        for (auto& kv : c->insts)
+            for (auto& m : kv.second->mem) dev_free(c, &m);
+        c->insts.clear();
+        cudaStreamSynchronize(c->stream);
+        if (c->ev0) cudaEventDestroy(c->ev0);
+        if (c->ev1) cudaEventDestroy(c->ev1);
+        if (c->ev2) cudaEventDestroy(c->ev2);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+    }
+    delete c;
+}
+
+const char* mars_last_error(mars_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void mars_params_default(mars_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->replicas = 1;
+    p->t_min = 0.0;
+    p->t_max = 1.0;
+    p->c_step = 1.0;
+    p->d_min = 1e-4;
+    p->k_max = 1000;
+    p->update = MARS_UPDATE_GS;
+    p->precision = MARS_FP32;
+}
+
+int mars_instance_dense(mars_ctx* c, int32_t n, const void* J, int32_t jt, const double* h,
+                        const int32_t* order, uint32_t flags, int32_t* inst)
+{
+    if (!c) return MARS_EINVAL;
+    if (n <= 0 || !J) return fail(c, MARS_EINVAL, "dense instance needs n > 0 and J");
+    if ((int64_t)n * n > (int64_t)1 << 31) return fail(c, MARS_EINVAL, "n too large for dense J");
+    DeviceGuard g(c->device);
+    const bool devp = flags & MARS_DEVICE_PTR;
+    std::vector<double> Jh, hh;
+    int rc = fetch_values(c, J, (size_t)n * n, jt, devp, &Jh);
+    if (rc) return rc;
+    if (h && (rc = fetch(c, h, (size_t)n, false, &hh))) return rc;
+    bool integer = true;
+    double wsum = 0.0, aw = 0.0;
+    long long wint = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (Jh[(size_t)i * n + i] != 0.0)
+            return fail(c, MARS_EINVAL, "J has a non-zero diagonal entry at %d", i);
+        for (int32_t j = i + 1; j < n; ++j) {
+            const double a = Jh[(size_t)i * n + j], b = Jh[(size_t)j * n + i];
+            if (!std::isfinite(a) || a != b)
+                return fail(c, MARS_EINVAL, "J is not symmetric and finite at (%d,%d)", i, j);
+            integer = integer && is_small_int(a, 127.0);
+            wsum += a;
+            aw += std::fabs(a);
+            if (integer) wint += (long long)a;
+        }
+    }
+    for (double v : hh) {
+        if (!std::isfinite(v)) return fail(c, MARS_EINVAL, "h has a non-finite entry");
+        integer = integer && is_small_int(v, 16777216.0);
+        aw += std::fabs(v);
+    }
+    auto in = std::make_unique<Instance>();
+    InstGuard guard{c, in.get()};
+    if ((rc = check_order(c, order, n, &in->order))) return rc;
+    const std::vector<int32_t>& o = in->order;  // new label a is caller spin o[a]
+    std::vector<float> Jf((size_t)n * n);
+    std::vector<int8_t> Ji;
+    std::vector<double> Jd;
+    if (integer) Ji.resize((size_t)n * n); else Jd.resize((size_t)n * n);
+    for (int32_t a = 0; a < n; ++a)
+        for (int32_t b = 0; b < n; ++b) {
+            const double v = Jh[(size_t)o[a] * n + o[b]];
+            Jf[(size_t)a * n + b] = (float)v;
+            if (integer) Ji[(size_t)a * n + b] = (int8_t)v; else Jd[(size_t)a * n + b] = v;
+        }
+    std::vector<float> hf;
+    std::vector<double> hd;
+    if (!hh.empty()) {
+        hf.resize(n);
+        hd.resize(n);
+        for (int32_t a = 0; a < n; ++a) { hf[a] = (float)hh[o[a]]; hd[a] = hh[o[a]]; }
+    }
+    DevInstance& d = in->dev;
+    d.n = n;
+    d.dense = 1;
+    d.nnz = (int64_t)n * (n - 1);
+    d.nlev = n;
+    d.integer = integer;
+    if ((rc = upload(c, in.get(), Jf, &d.Jf))) return rc;
+    if ((rc = upload(c, in.get(), Ji, &d.J_i8))) return rc;
+    if ((rc = upload(c, in.get(), Jd, &d.J_f64))) return rc;
+    if ((rc = upload(c, in.get(), hf, &d.h))) return rc;
+    if ((rc = upload(c, in.get(), hd, &d.h_f64))) return rc;
+    if ((rc = upload(c, in.get(), o, &d.new2old))) return rc;
+    MARS_CUDA(c, cudaStreamSynchronize(c->stream));
+    guard.done = true;
+    in->info.n = n;
+    in->info.dense = 1;
+    in->info.nnz = d.nnz;
+    in->info.levels = n;
+    in->info.integer = integer;
+    in->info.total_weight = integer ? (double)wint : wsum;
+    in->abs_weight = aw;
+    return finish_register(c, std::move(in), inst);
+}
+
+int mars_instance_csr(mars_ctx* c, int32_t n, int64_t nnz, const int32_t* row_ptr,
+                      const int32_t* col, const void* val, int32_t vt, const double* h,
+                      const int32_t* order, uint32_t flags, int32_t* inst)
+{
+    if (!c) return MARS_EINVAL;
+    if (n <= 0 || nnz < 0 || nnz > INT32_MAX || !row_ptr || (nnz > 0 && (!col || !val)))
+        return fail(c, MARS_EINVAL, "CSR instance needs n > 0, 0 <= nnz < 2^31 and arrays");
+    DeviceGuard g(c->device);
+    const bool devp = flags & MARS_DEVICE_PTR;
+    std::vector<int32_t> rp, cl;
+    std::vector<double> vl, hh;
+    int rc;
+    if ((rc = fetch(c, row_ptr, (size_t)n + 1, devp, &rp))) return rc;
+    if ((rc = fetch(c, col, (size_t)nnz, devp, &cl))) return rc;
+    if ((rc = fetch_values(c, val, (size_t)nnz, vt, devp, &vl))) return rc;
+    if (h && (rc = fetch(c, h, (size_t)n, false, &hh))) return rc;
+    if (rp[0] != 0 || rp[n] != nnz) return fail(c, MARS_EINVAL, "row_ptr must run from 0 to nnz");
+    for (int32_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return fail(c, MARS_EINVAL, "row_ptr decreases at row %d", i);
+    // Rows with columns sorted (stable on a copy) to check duplicates and symmetry.
+    std::vector<int32_t> sc(cl);
+    std::vector<double> sv(vl);
+    {
+        std::vector<int64_t> idx;
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t e0 = rp[i], e1 = rp[i + 1];
+            idx.resize(e1 - e0);
+            std::iota(idx.begin(), idx.end(), (int64_t)e0);
+            std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return cl[a] < cl[b]; });
+            for (int32_t q = 0; q < e1 - e0; ++q) { sc[e0 + q] = cl[idx[q]]; sv[e0 + q] = vl[idx[q]]; }
+            for (int32_t e = e0; e < e1; ++e) {
+                if (sc[e] < 0 || sc[e] >= n) return fail(c, MARS_EINVAL, "column out of range in row %d", i);
+                if (sc[e] == i) return fail(c, MARS_EINVAL, "diagonal entry in row %d", i);
+                if (e > e0 && sc[e] == sc[e - 1]) return fail(c, MARS_EINVAL, "repeated column in row %d", i);
+                if (!std::isfinite(sv[e])) return fail(c, MARS_EINVAL, "non-finite value in row %d", i);
+            }
+        }
+    }
+    bool integer = true;
+    double wsum = 0.0, aw = 0.0;
+    long long wint = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t j = sc[e];
+            const auto b = sc.begin() + rp[j], en = sc.begin() + rp[j + 1];
+            const auto it = std::lower_bound(b, en, i);
+            if (it == en || *it != i || sv[it - sc.begin()] != sv[e])
+                return fail(c, MARS_EINVAL, "couplings are not symmetric at (%d,%d)", i, j);
+            if (j > i) {
+                integer = integer && is_small_int(sv[e], 127.0);
+                wsum += sv[e];
+                aw += std::fabs(sv[e]);
+                if (integer) wint += (long long)sv[e];
+            }
+        }
+    }
+    for (double v : hh) {
+        if (!std::isfinite(v)) return fail(c, MARS_EINVAL, "h has a non-finite entry");
+        integer = integer && is_small_int(v, 16777216.0);
+        aw += std::fabs(v);
+    }
+    auto in = std::make_unique<Instance>();
+    InstGuard guard{c, in.get()};
+    // Visiting order: the caller's, or greedy colour classes in turn.
+    if (order) {
+        if ((rc = check_order(c, order, n, &in->order))) return rc;
+    } else {
+        std::vector<int32_t> colour(n, -1);
+        std::vector<int32_t> mark;
+        for (int32_t i = 0; i < n; ++i) {
+            mark.assign(rp[i + 1] - rp[i] + 2, 0);
+            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const int32_t cj = colour[sc[e]];
+                if (cj >= 0 && cj < (int32_t)mark.size()) mark[cj] = 1;
+            }
+            int32_t cc = 0;
+            while (mark[cc]) ++cc;
+            colour[i] = cc;
+        }
+        in->order.resize(n);
+        std::iota(in->order.begin(), in->order.end(), 0);
+        std::stable_sort(in->order.begin(), in->order.end(),
+                         [&](int32_t a, int32_t b) { return colour[a] < colour[b]; });
+    }
+    // Level schedule of the sequential sweep in that order.
+    std::vector<int32_t> pos(n), level(n, 0);
+    for (int32_t q = 0; q < n; ++q) pos[in->order[q]] = q;
+    int32_t nlev = 0;
+    for (int32_t q = 0; q < n; ++q) {
+        const int32_t v = in->order[q];
+        int32_t lv = 0;
+        for (int32_t e = rp[v]; e < rp[v + 1]; ++e)
+            if (pos[sc[e]] < q) lv = std::max(lv, level[sc[e]] + 1);
+        level[v] = lv;
+        nlev = std::max(nlev, lv + 1);
+    }
+    std::vector<int32_t> new2old(n), old2new(n), lvl_start(nlev + 1, 0);
+    std::iota(new2old.begin(), new2old.end(), 0);
+    std::stable_sort(new2old.begin(), new2old.end(), [&](int32_t a, int32_t b) {
+        return level[a] != level[b] ? level[a] < level[b] : pos[a] < pos[b];
+    });
+    for (int32_t a = 0; a < n; ++a) { old2new[new2old[a]] = a; lvl_start[level[new2old[a]] + 1]++; }
+    for (int32_t l = 0; l < nlev; ++l) lvl_start[l + 1] += lvl_start[l];
+    // CSR over new labels with columns sorted.
+    std::vector<int32_t> nrp(n + 1, 0), ncol(nnz);
+    std::vector<float> nval(nnz);
+    std::vector<int8_t> nval_i8(integer ? nnz : 0);
+    std::vector<double> nval_f64(nnz);
+    std::vector<std::pair<int32_t, double>> row;
+    for (int32_t a = 0; a < n; ++a) {
+        const int32_t o = new2old[a];
+        row.clear();
+        for (int32_t e = rp[o]; e < rp[o + 1]; ++e) row.emplace_back(old2new[sc[e]], sv[e]);
+        std::sort(row.begin(), row.end());
+        nrp[a + 1] = nrp[a] + (int32_t)row.size();
+        for (size_t q = 0; q < row.size(); ++q) {
+            const int32_t e = nrp[a] + (int32_t)q;
+            ncol[e] = row[q].first;
+            nval[e] = (float)row[q].second;
+            nval_f64[e] = row[q].second;
+            if (integer) nval_i8[e] = (int8_t)row[q].second;
+        }
+    }
+    std::vector<float> hf;
+    std::vector<double> hd;
+    if (!hh.empty()) {
+        hf.resize(n);
+        hd.resize(n);
+        for (int32_t a = 0; a < n; ++a) { hf[a] = (float)hh[new2old[a]]; hd[a] = hh[new2old[a]]; }
+    }
+    DevInstance& d = in->dev;
+    d.n = n;
+    d.dense = 0;
+    d.nnz = nnz;
+    d.nlev = nlev;
+    d.integer = integer;
+    if ((rc = upload(c, in.get(), nrp, &d.row_ptr))) return rc;
+    if ((rc = upload(c, in.get(), ncol, &d.col))) return rc;
+    if ((rc = upload(c, in.get(), nval, &d.val))) return rc;
+    if ((rc = upload(c, in.get(), nval_i8, &d.val_i8))) return rc;
+    if ((rc = upload(c, in.get(), nval_f64, &d.val_f64))) return rc;
+    if ((rc = upload(c, in.get(), lvl_start, &d.lvl_start))) return rc;
+    if ((rc = upload(c, in.get(), hf, &d.h))) return rc;
+    if ((rc = upload(c, in.get(), hd, &d.h_f64))) return rc;
+    if ((rc = upload(c, in.get(), new2old, &d.new2old))) return rc;
+    MARS_CUDA(c, cudaStreamSynchronize(c->stream));
+    guard.done = true;
+    in->info.n = n;
+    in->info.dense = 0;
+    in->info.nnz = nnz;
+    in->info.levels = nlev;
+    in->info.integer = integer;
+    in->info.total_weight = integer ? (double)wint : wsum;
+    in->abs_weight = aw;
+    return finish_register(c, std::move(in), inst);
+}
+
+int mars_instance_free(mars_ctx* c, int32_t id)
+{
+    if (!c) return MARS_EINVAL;
+    auto it = c->insts.find(id);
+    if (it == c->insts.end()) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    DeviceGuard g(c->device);
+    for (auto& m : it->second->mem) dev_free(c, &m);
+    c->insts.erase(it);
+    return MARS_OK;
+}
+
+int mars_instance_get_info(mars_ctx* c, int32_t id, mars_instance_info* info)
+{
+    if (!c || !info) return MARS_EINVAL;
+    Instance* in = find(c, id);
+    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    *info = in->info;
+    return MARS_OK;
+}
+
+int mars_instance_order(mars_ctx* c, int32_t id, int32_t* order_out)
+{
+    if (!c || !order_out) return MARS_EINVAL;
+    Instance* in = find(c, id);
+    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    std::memcpy(order_out, in->order.data(), in->order.size() * sizeof(int32_t));
+    return MARS_OK;
+}
+
+int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins,
+               const mars_outputs* outs, mars_result* result)
+{
+    if (!c || !p) return MARS_EINVAL;
+    Instance* in = find(c, id);
+    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    const int32_t R = p->replicas, n = in->dev.n;
+    if (R < 1) return fail(c, MARS_EINVAL, "replicas must be >= 1");
+    if (!std::isfinite(p->t_min) || !std::isfinite(p->t_max) || p->t_min > p->t_max)
+        return fail(c, MARS_EINVAL, "need finite t_min <= t_max");
+    if (!(p->c_step > 0.0) || !std::isfinite(p->c_step)) return fail(c, MARS_EINVAL, "c_step must be > 0");
+    if (p->t_max / p->c_step > kMaxLevels)
+        return fail(c, MARS_EINVAL, "t_max / c_step exceeds %.0f temperature levels", kMaxLevels);
+    if (!(p->d_min >= 0.0)) return fail(c, MARS_EINVAL, "d_min must be >= 0");
+    if (p->k_max < 1 || p->fixed_sweeps < 0) return fail(c, MARS_EINVAL, "k_max >= 1, fixed_sweeps >= 0");
+    if (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI)
+        return fail(c, MARS_EINVAL, "unknown update rule %d", p->update);
+    if (p->precision != MARS_FP32)
+        return fail(c, MARS_EINVAL, "precision %d is not available for this instance", p->precision);
+    if ((size_t)R * n > ((size_t)1 << 40)) return fail(c, MARS_EINVAL, "R*n too large");
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const bool pdev = p->flags & MARS_DEVICE_PTR;
+    const bool odev = outs && (outs->flags & MARS_DEVICE_PTR);
+    Scratch S(c);
+    int rc;
+    DevSolve s;
+    s.R = R;
+    s.seed = p->seed;
+    s.stream = p->stream;
+    s.c_step = p->c_step;
+    s.d_min = (float)p->d_min;
+    s.k_max = p->k_max;
+    s.fixed_sweeps = p->fixed_sweeps;
+    s.jacobi = p->update == MARS_UPDATE_JACOBI;
+    // start temperatures
+    float* t0 = nullptr;
+    if ((rc = S.get(R, &t0))) return rc;
+    std::vector<float> t0h(R);
+    if (p->t0) {
+        if (pdev) {
+            MARS_CUDA(c, cudaMemcpyAsync(t0, p->t0, R * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            MARS_CUDA(c, cudaMemcpyAsync(t0h.data(), p->t0, R * sizeof(float), cudaMemcpyDeviceToHost, st));
+        } else {
+            std::memcpy(t0h.data(), p->t0, R * sizeof(float));
+            MARS_CUDA(c, cudaMemcpyAsync(t0, t0h.data(), R * sizeof(float), cudaMemcpyHostToDevice, st));
+        }
+    } else {
+        MARS_CUDA(c, launch_draw(p->seed, p->stream, 0, R, 0, p->t_min, p->t_max, nullptr, t0, st));
+        MARS_CUDA(c, cudaMemcpyAsync(t0h.data(), t0, R * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+    for (float v : t0h)
+        if (!std::isfinite(v) || v / p->c_step > kMaxLevels)
+            return fail(c, MARS_EINVAL, "start temperatures must be finite with t0 / c_step <= %.0f",
+                        kMaxLevels);
+    s.t0 = t0;
+    if (p->m0) {
+        if (pdev) {
+            s.m0 = p->m0;
+        } else {
+            float* m0 = nullptr;
+            if ((rc = S.get((size_t)R * n, &m0))) return rc;
+            MARS_CUDA(c, cudaMemcpyAsync(m0, p->m0, (size_t)R * n * sizeof(float),
+                                         cudaMemcpyHostToDevice, st));
+            s.m0 = m0;
+        }
+    }
+    // per-replica outputs
+    if ((rc = S.get((size_t)R * n, &s.sigma))) return rc;
+    if ((rc = S.get(R, &s.energy))) return rc;
+    if ((rc = S.get(R, &s.energy_i64))) return rc;
+    if ((rc = S.get(R, &s.sweeps))) return rc;
+    if ((rc = S.get(R, &s.levels))) return rc;
+    if ((rc = S.get(R, &s.capped))) return rc;
+    if ((rc = S.get(2, &s.work_counter))) return rc;
+    s.status = s.work_counter + 1;
+    MARS_CUDA(c, cudaMemsetAsync(s.work_counter, 0, 2 * sizeof(int32_t), st));
+    if (outs && outs->m_final) {
+        if (odev) {
+            s.m_final = outs->m_final;
+        } else if ((rc = S.get((size_t)R * n, &s.m_final))) {
+            return rc;
+        }
+    }
+    DevResult* dres = nullptr;
+    int8_t* dbest = nullptr;
+    if ((rc = S.get(1, &dres))) return rc;
+    if ((rc = S.get(n, &dbest))) return rc;
+    // Schedule: replicas by start temperature, longest descents first.
+    MARS_CUDA(c, cudaStreamSynchronize(st));
+    SparsePlan sp;
+    DensePlan dp;
+    int rt = 1;
+    if (in->dev.dense) {
+        dp = plan_dense(in->dev, R, s.jacobi, c->device);
+        if (dp.scratch_floats && (rc = S.get(dp.scratch_floats, &s.m_scratch))) return rc;
+    } else {
+        sp = plan_sparse(in->dev, R, s.jacobi, c->device);
+        rt = sp.rt;
+        const size_t per = (size_t)sp.grid * n * rt;
+        float* scr = nullptr;
+        if (sp.scratch_floats && (rc = S.get(sp.scratch_floats, &scr))) return rc;
+        if (!sp.onchip) { s.m_scratch = scr; scr += per; }
+        if (s.jacobi) s.m_next = scr;
+    }
+    std::vector<int32_t> reps(R);
+    std::iota(reps.begin(), reps.end(), 0);
+    std::stable_sort(reps.begin(), reps.end(), [&](int32_t a, int32_t b) { return t0h[a] > t0h[b]; });
+    const int32_t ntiles = (R + rt - 1) / rt;
+    std::vector<int32_t> tile_rep((size_t)ntiles * rt, -1);
+    for (int32_t q = 0; q < R; ++q) tile_rep[q] = reps[q];
+    int32_t* dtile = nullptr;
+    if ((rc = S.get(tile_rep.size(), &dtile))) return rc;
+    MARS_CUDA(c, cudaMemcpyAsync(dtile, tile_rep.data(), tile_rep.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, st));
+    s.tile_rep = dtile;
+    s.ntiles = ntiles;
+    s.rt = rt;
+    MARS_CUDA(c, cudaEventRecord(c->ev0, st));
+    if (in->dev.dense) {
+        MARS_CUDA(c, launch_dense(in->dev, s, dp, st));
+    } else {
+        MARS_CUDA(c, launch_sparse(in->dev, s, sp, st));
+    }
+    MARS_CUDA(c, cudaEventRecord(c->ev2, st));
+    MARS_CUDA(c, launch_best(s, n, in->dev.integer, dbest, dres, st));
+    MARS_CUDA(c, cudaEventRecord(c->ev1, st));
+    DevResult hres;
+    int32_t hstatus = 0;
+    MARS_CUDA(c, cudaMemcpyAsync(&hres, dres, sizeof hres, cudaMemcpyDeviceToHost, st));
+    MARS_CUDA(c, cudaMemcpyAsync(&hstatus, s.status, sizeof hstatus, cudaMemcpyDeviceToHost, st));
+    if (best_spins)
+        MARS_CUDA(c, cudaMemcpyAsync(best_spins, dbest, n, cudaMemcpyDeviceToHost, st));
+    if (outs) {
+        const cudaMemcpyKind k = odev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (outs->energies) MARS_CUDA(c, cudaMemcpyAsync(outs->energies, s.energy, R * sizeof(double), k, st));
+        if (outs->spins) MARS_CUDA(c, cudaMemcpyAsync(outs->spins, s.sigma, (size_t)R * n, k, st));
+        if (outs->m_final && !odev)
+            MARS_CUDA(c, cudaMemcpyAsync(outs->m_final, s.m_final, (size_t)R * n * sizeof(float), k, st));
+        if (outs->t0) MARS_CUDA(c, cudaMemcpyAsync(outs->t0, t0, R * sizeof(float), k, st));
+        if (outs->sweeps) MARS_CUDA(c, cudaMemcpyAsync(outs->sweeps, s.sweeps, R * sizeof(int32_t), k, st));
+        if (outs->levels) MARS_CUDA(c, cudaMemcpyAsync(outs->levels, s.levels, R * sizeof(int32_t), k, st));
+        if (outs->capped) MARS_CUDA(c, cudaMemcpyAsync(outs->capped, s.capped, R * sizeof(int32_t), k, st));
+    }
+    MARS_CUDA(c, cudaStreamSynchronize(st));
+    float ms = 0.f, ms_descent = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    cudaEventElapsedTime(&ms_descent, c->ev0, c->ev2);
+    if (hstatus != kDevOk) return fail(c, MARS_EDEVICE, "device status %d", hstatus);
+    if (result) {
+        std::memset(result, 0, sizeof *result);
+        result->best_energy = hres.best_energy;
+        result->best_energy_i64 = hres.best_energy_i64;
+        result->best_cut = (in->info.total_weight - hres.best_energy) / 2.0;
+        result->best_replica = hres.best_replica;
+        result->hits = hres.hits;
+        result->mean_energy = hres.sum_energy / R;
+        result->sweeps = hres.sweeps;
+        result->spin_updates = hres.sweeps * (int64_t)n;
+        result->levels = hres.levels;
+        result->capped_levels = hres.capped;
+        result->gpu_seconds = ms * 1e-3;
+        result->descent_seconds = ms_descent * 1e-3;
+        result->integer = in->dev.integer;
+        result->energy_err_bound =
+            in->dev.integer ? 0.0 : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + n);
+        result->status = MARS_OK;
+    }
+    return MARS_OK;
+}
+
+int mars_energy(mars_ctx* c, int32_t id, const int8_t* spins, int32_t count, double* e,
+                int64_t* e_i64, uint32_t flags)
+{
+    if (!c || (!spins && count > 0) || (!e && count > 0) || count < 0) return MARS_EINVAL;
+    Instance* in = find(c, id);
+    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    if (count == 0) return MARS_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const bool devp = flags & MARS_DEVICE_PTR;
+    const int32_t n = in->dev.n;
+    Scratch S(c);
+    int rc;
+    const int8_t* dsp = spins;
+    double* de = e;
+    long long* dei = (long long*)e_i64;
+    int32_t* dstatus = nullptr;
+    if ((rc = S.get(1, &dstatus))) return rc;
+    MARS_CUDA(c, cudaMemsetAsync(dstatus, 0, sizeof(int32_t), st));
+    if (!devp) {
+        int8_t* t = nullptr;
+        if ((rc = S.get((size_t)count * n, &t))) return rc;
+        MARS_CUDA(c, cudaMemcpyAsync(t, spins, (size_t)count * n, cudaMemcpyHostToDevice, st));
+        dsp = t;
+        if ((rc = S.get(count, &de))) return rc;
+        if (e_i64 && (rc = S.get(count, &dei))) return rc;
+    }
+    MARS_CUDA(c, launch_energy(in->dev, dsp, count, de, dei, dstatus, st));
+    int32_t hstatus = 0;
+    MARS_CUDA(c, cudaMemcpyAsync(&hstatus, dstatus, sizeof hstatus, cudaMemcpyDeviceToHost, st));
+    if (!devp) {
+        MARS_CUDA(c, cudaMemcpyAsync(e, de, count * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (e_i64) MARS_CUDA(c, cudaMemcpyAsync(e_i64, dei, count * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    }
+    MARS_CUDA(c, cudaStreamSynchronize(st));
+    if (hstatus != kDevOk) return fail(c, MARS_EINVAL, "spins must be +-1");
+    return MARS_OK;
+}
+
+int mars_draw_replicas(mars_ctx* c, uint64_t seed, uint32_t stream, int32_t r0, int32_t R,
+                       int32_t n, double t_min, double t_max, float* m0, float* t0,
+                       uint32_t flags)
+{
+    if (!c || R < 0 || n < 0 || r0 < 0) return MARS_EINVAL;
+    if (!std::isfinite(t_min) || !std::isfinite(t_max) || t_min > t_max)
+        return fail(c, MARS_EINVAL, "need finite t_min <= t_max");
+    if (R == 0) return MARS_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const bool devp = flags & MARS_DEVICE_PTR;
+    Scratch S(c);
+    int rc;
+    float* dm = m0;
+    float* dt = t0;
+    if (!devp) {
+        dm = nullptr;
+        dt = nullptr;
+        if (m0 && (rc = S.get((size_t)R * n, &dm))) return rc;
+        if (t0 && (rc = S.get(R, &dt))) return rc;
+    }
+    MARS_CUDA(c, launch_draw(seed, stream, r0, R, m0 ? n : 0, t_min, t_max, dm, dt, st));
+    if (!devp) {
+        if (m0) MARS_CUDA(c, cudaMemcpyAsync(m0, dm, (size_t)R * n * sizeof(float), cudaMemcpyDeviceToHost, st));
+        if (t0) MARS_CUDA(c, cudaMemcpyAsync(t0, dt, R * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+    MARS_CUDA(c, cudaStreamSynchronize(st));
+    return MARS_OK;
+}
+
+}  // extern "C"

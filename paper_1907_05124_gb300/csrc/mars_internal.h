@@ -1,0 +1,110 @@
+// Internal interfaces between the host runtime (mars_api.cu) and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mars {
+
+// Device-side status words (status[0]); MARS_OK when clean.
+enum DeviceStatus : int32_t { kDevOk = 0, kDevBadIndex = 1 };
+
+// Instance data on the device, relabelled so that one sweep is "levels in
+// order, any order within a level": new label a has caller label new2old[a].
+struct DevInstance {
+    int32_t n = 0;
+    int32_t dense = 0;
+    int64_t nnz = 0;
+    int32_t nlev = 0;
+    int32_t integer = 0;
+    // sparse (CSR over new labels, columns sorted)
+    const int32_t* row_ptr = nullptr;
+    const int32_t* col = nullptr;
+    const float* val = nullptr;
+    const int8_t* val_i8 = nullptr;    // integer instances
+    const double* val_f64 = nullptr;   // every instance: exact values for energies
+    const int32_t* lvl_start = nullptr;  // nlev+1 offsets into new labels
+    // dense (n*n, new labels: Jn[a][b] = J[new2old[a]][new2old[b]])
+    const float* Jf = nullptr;
+    const int8_t* J_i8 = nullptr;
+    const double* J_f64 = nullptr;
+    // common
+    const float* h = nullptr;          // n floats or null
+    const double* h_f64 = nullptr;     // n doubles or null
+    const int32_t* new2old = nullptr;  // n
+};
+
+// One solve's replica state and outputs (all device pointers).
+struct DevSolve {
+    int32_t R = 0;
+    int32_t ntiles = 0;
+    int32_t rt = 1;                    // replicas per tile
+    const int32_t* tile_rep = nullptr; // ntiles*rt replica ids (-1 = empty slot)
+    const float* t0 = nullptr;         // R start temperatures
+    const float* m0 = nullptr;         // R*n caller-labelled start states, or null (draw)
+    uint64_t seed = 0;
+    uint32_t stream = 0;
+    double c_step = 1.0;
+    float d_min = 1e-4f;
+    int32_t k_max = 1000;
+    int32_t fixed_sweeps = 0;
+    int32_t jacobi = 0;
+    float* m_scratch = nullptr;        // per-CTA state when it does not fit on chip
+    float* m_next = nullptr;           // per-CTA second buffer for synchronous sweeps
+    // outputs
+    int8_t* sigma = nullptr;           // R*n caller labels
+    float* m_final = nullptr;          // R*n caller labels, optional
+    double* energy = nullptr;          // R
+    long long* energy_i64 = nullptr;   // R
+    int32_t* sweeps = nullptr;         // R
+    int32_t* levels = nullptr;         // R
+    int32_t* capped = nullptr;         // R
+    int32_t* work_counter = nullptr;   // 1
+    int32_t* status = nullptr;         // 1
+};
+
+struct DevResult {
+    double best_energy;
+    long long best_energy_i64;
+    int32_t best_replica;
+    int32_t hits;
+    double sum_energy;
+    long long sweeps;
+    long long levels;
+    long long capped;
+};
+
+// Launchers (return cudaError_t of the launch).
+struct SparsePlan {
+    int rt = 1;         // replicas per tile
+    int onchip = 1;     // magnetisations in shared memory
+    int threads = 512;
+    size_t smem = 0;    // dynamic shared memory
+    int grid = 0;
+    size_t scratch_floats = 0;  // m_scratch (+ m_next) floats needed
+};
+SparsePlan plan_sparse(const DevInstance& in, int R, int jacobi, int device);
+cudaError_t launch_sparse(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
+                          cudaStream_t st);
+
+struct DensePlan {
+    int warps_per_block = 4;
+    int onchip = 1;
+    size_t smem = 0;
+    int grid = 0;
+    size_t scratch_floats = 0;
+};
+DensePlan plan_dense(const DevInstance& in, int R, int jacobi, int device);
+cudaError_t launch_dense(const DevInstance& in, const DevSolve& s, const DensePlan& p,
+                         cudaStream_t st);
+
+cudaError_t launch_draw(uint64_t seed, uint32_t stream, int32_t r0, int32_t R, int32_t n,
+                        double t_min, double t_max, float* m0, float* t0, cudaStream_t st);
+
+cudaError_t launch_best(const DevSolve& s, int32_t n, int32_t integer, int8_t* best_spins,
+                        DevResult* res, cudaStream_t st);
+
+cudaError_t launch_energy(const DevInstance& in, const int8_t* spins, int32_t count,
+                          double* e, long long* e_i64, int32_t* status, cudaStream_t st);
+
+}  // namespace mars

@@ -1,0 +1,378 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated by the method's target): per-replica magnetisations after a
+fixed number of sweeps within 1e-5 max-abs of the oracle; energies of given
+spins bit-exact for integer couplings; start-state draws bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1907_05124_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+M_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_05124_gb300 import build, mars
+    build.build()
+    c = mars.Context(0)
+    yield c
+    c.close()
+
+
+def _oracle_inst(J=None, csr=None, h=None):
+    return O.Instance.dense(J, h) if J is not None else O.Instance.csr(csr, h)
+
+
+def _add(ctx, J=None, csr=None, h=None, order=None):
+    if J is not None:
+        return ctx.add_dense(J, h=h, order=order)
+    return ctx.add_csr(*csr, h=h, order=order)
+
+
+# --------------------------------------------------------------------------
+# start-state draw and energies: bit-exact
+# --------------------------------------------------------------------------
+
+def test_draw_replicas_bit_exact(ctx):
+    for seed, stream, r0 in ((0, 0, 0), (2 ** 40 + 17, 3, 5), (123456789, 7, 1000)):
+        m_g, t_g = ctx.draw_replicas(seed, 37, 101, 0.25, 7.5, stream=stream, r0=r0)
+        m_o, t_o = O.draw_replicas(seed, 37, 101, 0.25, 7.5, stream=stream, r0=r0)
+        assert np.array_equal(m_g, m_o)
+        assert np.array_equal(t_g, t_o)
+
+
+@pytest.mark.parametrize("kind", ["sk64", "ea2d", "er", "er_field", "ea3d"])
+def test_energy_integer_instances_exact(ctx, kind):
+    rng = np.random.default_rng(1)
+    J = csr = h = None
+    if kind == "sk64":
+        J = I.sk_pm1(64, 0)
+        n = 64
+    elif kind == "ea2d":
+        csr = I.ea_lattice(20, 2, 0)
+        n = csr.n
+    elif kind == "ea3d":
+        csr = I.ea_lattice(8, 3, 1)
+        n = csr.n
+    else:
+        csr = I.er_graph(500, 6, 2, "pm1")
+        n = csr.n
+        if kind == "er_field":
+            h = rng.integers(-3, 4, size=n).astype(np.float64)
+    inst = _add(ctx, J, csr, h)
+    spins = rng.choice(np.array([-1, 1], np.int8), size=(32, n))
+    e, ei = ctx.energy(inst, spins)
+    ref = O.energies(_oracle_inst(J, csr, h), spins)
+    assert np.array_equal(e, ref)
+    assert np.array_equal(ei, ref.astype(np.int64))
+    ctx.free(inst)
+
+
+def test_energy_gaussian_close(ctx):
+    J = I.sk_gauss(150, 4)
+    h = np.random.default_rng(3).normal(size=150) * 0.1
+    inst = ctx.add_dense(J, h=h)
+    spins = np.random.default_rng(5).choice(np.array([-1, 1], np.int8), size=(16, 150))
+    e, _ = ctx.energy(inst, spins)
+    ref = O.energies(O.Instance.dense(J, h), spins)
+    np.testing.assert_allclose(e, ref, rtol=0, atol=1e-12 * np.abs(J).sum())
+    ctx.free(inst)
+
+
+# --------------------------------------------------------------------------
+# fixed-sweep trajectories: max-abs 1e-5
+# --------------------------------------------------------------------------
+
+SPARSE_CASES = {
+    "ea2d_colour": (lambda: I.ea_lattice(20, 2, 0), "colour", 4.0),
+    "ea2d_natural": (lambda: I.ea_lattice(12, 2, 3), "natural", 4.0),
+    "ea3d_colour": (lambda: I.ea_lattice(6, 3, 1), "colour", 5.0),
+    "er_pm1": (lambda: I.er_graph(300, 8, 4, "pm1"), "colour", 6.0),
+    "er_one": (lambda: I.er_graph(257, 5, 5, "one"), "colour", 5.0),
+}
+
+
+@pytest.mark.parametrize("case", sorted(SPARSE_CASES))
+def test_sparse_fixed_sweep_trajectories(ctx, case):
+    make, order_kind, tmax = SPARSE_CASES[case]
+    csr = make()
+    order = I.greedy_colour_order(csr) if order_kind == "colour" else np.arange(csr.n, dtype=np.int32)
+    inst = ctx.add_csr(*csr, order=order)
+    R = 13  # not a multiple of any tile width: ragged last tile
+    m0, t0 = I.replica_inputs(R, csr.n, 0.0, tmax, 17)
+    g = ctx.solve(inst, R, 0.0, tmax, fixed_sweeps=3, m0=m0, t0=t0,
+                  outputs=("m_final", "energies", "sweeps", "levels", "spins"))
+    o = O.mars_solve(O.Instance.csr(csr), m0, t0, fixed_sweeps=3, order=order)
+    assert np.abs(g.m_final - o["m"]).max() <= M_TOL
+    assert np.array_equal(g.replica_sweeps, o["sweeps"])
+    assert np.array_equal(g.replica_levels, o["levels"])
+    # the GPU's spins and energies are consistent with its own m
+    assert np.array_equal(g.spins, np.where(g.m_final >= 0, 1, -1).astype(np.int8))
+    assert np.array_equal(g.energies, O.energies(O.Instance.csr(csr), g.spins))
+    ctx.free(inst)
+
+
+def test_library_default_order_is_greedy_colouring(ctx):
+    csr = I.er_graph(400, 7, 9, "pm1")
+    inst = ctx.add_csr(*csr)
+    assert np.array_equal(ctx.order(inst), I.greedy_colour_order(csr))
+    info = ctx.info(inst)
+    assert 2 <= info["levels"] <= 12
+    lat = ctx.add_csr(*I.ea_lattice(10, 2, 0))
+    assert ctx.info(lat)["levels"] == 2
+    ctx.free(inst)
+    ctx.free(lat)
+
+
+@pytest.mark.parametrize("case", ["sk64_pm1", "sk200_gauss_field", "sk97_order"])
+def test_dense_fixed_sweep_trajectories(ctx, case):
+    rng = np.random.default_rng(7)
+    order = None
+    h = None
+    if case == "sk64_pm1":
+        J, tmax, c = I.sk_pm1(64, 0), 16.0, 1.0
+    elif case == "sk200_gauss_field":
+        J, tmax, c = I.sk_gauss(200, 1), 2.0, 0.25
+        h = rng.normal(size=200) * 0.05
+    else:
+        J, tmax, c = I.sk_pm1(97, 2), 20.0, 1.0
+        order = rng.permutation(97).astype(np.int32)
+    inst = ctx.add_dense(J, h=h, order=order)
+    R = 9
+    m0, t0 = I.replica_inputs(R, J.shape[0], 0.0, tmax, 23)
+    g = ctx.solve(inst, R, 0.0, tmax, c_step=c, fixed_sweeps=2, m0=m0, t0=t0,
+                  outputs=("m_final", "sweeps", "levels"))
+    o = O.mars_solve(O.Instance.dense(J, h), m0, t0, c_step=c, fixed_sweeps=2, order=order)
+    assert np.abs(g.m_final - o["m"]).max() <= M_TOL
+    assert np.array_equal(g.replica_sweeps, o["sweeps"])
+    ctx.free(inst)
+
+
+@pytest.mark.parametrize("kind", ["dense", "sparse"])
+def test_jacobi_fixed_sweep_trajectories(ctx, kind):
+    if kind == "dense":
+        J, csr, tmax = I.sk_pm1(48, 3), None, 12.0
+        n = 48
+    else:
+        J, csr, tmax = None, I.ea_lattice(10, 2, 4), 4.0
+        n = csr.n
+    inst = _add(ctx, J, csr)
+    m0, t0 = I.replica_inputs(6, n, 0.0, tmax, 29)
+    g = ctx.solve(inst, 6, 0.0, tmax, fixed_sweeps=2, update="jacobi", m0=m0, t0=t0,
+                  outputs=("m_final",))
+    o = O.mars_solve(_oracle_inst(J, csr), m0, t0, fixed_sweeps=2, update=O.UPDATE_JACOBI)
+    assert np.abs(g.m_final - o["m"]).max() <= M_TOL
+    ctx.free(inst)
+
+
+# --------------------------------------------------------------------------
+# the stopping rule: per-replica agreement and distributions
+# --------------------------------------------------------------------------
+
+def test_convergence_rule_sparse_agrees_with_oracle(ctx):
+    from scipy import stats
+    csr = I.ea_lattice(24, 2, 5)
+    order = I.greedy_colour_order(csr)
+    inst = ctx.add_csr(*csr, order=order)
+    R = 96
+    m0, t0 = I.replica_inputs(R, csr.n, 0.0, 4.0, 31)
+    g = ctx.solve(inst, R, 0.0, 4.0, m0=m0, t0=t0, outputs=("energies", "sweeps"))
+    o = O.mars_solve(O.Instance.csr(csr), m0, t0, order=order, nthreads=8, want_m=False)
+    same = np.mean(g.energies == o["energy"])
+    assert same >= 0.85, same
+    assert stats.ks_2samp(g.energies, o["energy"]).pvalue > 0.01
+    assert g.best_energy == o["energy"].min() or abs(g.best_energy - o["energy"].min()) <= 8
+    ctx.free(inst)
+
+
+def test_sk64_config_best_matches_oracle(ctx):
+    """Dense SK +-1, N = 64, R = 256, T0 ~ U(0, 16), c_step 1, d_min 1e-4."""
+    J = I.sk_pm1(64, 0)
+    inst = ctx.add_dense(J)
+    m0, t0 = I.replica_inputs(256, 64, 0.0, 16.0, 0)
+    g = ctx.solve(inst, 256, 0.0, 16.0, m0=m0, t0=t0, outputs=("energies",))
+    o = O.mars_solve(O.Instance.dense(J), m0, t0, nthreads=8, want_m=False)
+    assert np.mean(g.energies == o["energy"]) >= 0.9
+    assert g.best_energy == o["energy"].min()
+    assert g.best_energy == O.energy(O.Instance.dense(J), g.best_spins)
+    ctx.free(inst)
+
+
+def test_n20_never_below_ground_state_and_hits_it(ctx):
+    J = I.sk_pm1(20, 0)
+    e_gs, _, _ = O.bruteforce(O.Instance.dense(J))
+    inst = ctx.add_dense(J)
+    g = ctx.solve(inst, 256, 0.0, 16.0, seed=0, outputs=("energies",))
+    assert np.all(g.energies >= e_gs)
+    assert g.best_energy == e_gs
+    assert g.hits == int(np.sum(g.energies == e_gs))
+    ctx.free(inst)
+
+
+# --------------------------------------------------------------------------
+# best-replica bookkeeping and edge cases
+# --------------------------------------------------------------------------
+
+def test_best_replica_lowest_index_hits_mean(ctx):
+    csr = I.ea_lattice(8, 2, 0, "antiferro")
+    inst = ctx.add_csr(*csr)
+    g = ctx.solve(inst, 64, 0.0, 4.0, seed=3, outputs=("energies", "spins"))
+    e = g.energies
+    assert g.best_energy == e.min()
+    assert g.best_replica == int(np.flatnonzero(e == e.min())[0])
+    assert g.hits == int(np.sum(e == e.min()))
+    assert g.mean_energy == pytest.approx(e.mean(), rel=1e-12)
+    assert np.array_equal(g.best_spins, g.spins[g.best_replica])
+    assert g.best_cut == (csr.val[csr.col > np.repeat(np.arange(csr.n), np.diff(csr.row_ptr))].sum()
+                          - g.best_energy) / 2
+    ctx.free(inst)
+
+
+def test_zero_levels_return_sign_of_start(ctx):
+    csr = I.ea_lattice(6, 2, 0)
+    inst = ctx.add_csr(*csr)
+    m0, _ = I.replica_inputs(5, csr.n, 0, 1, 2)
+    m0[0, :3] = 0.0  # sign(0) = +1
+    t0 = np.array([0.0, 0.5, 1.0, 0.999, 1.0], np.float32)  # T0 - 1 <= 0 for all
+    g = ctx.solve(inst, 5, 0.0, 1.0, m0=m0, t0=t0, outputs=("spins", "sweeps", "levels"))
+    assert np.all(g.replica_sweeps == 0) and np.all(g.replica_levels == 0)
+    assert np.array_equal(g.spins, np.where(m0 >= 0, 1, -1).astype(np.int8))
+    ctx.free(inst)
+
+
+def test_single_spin_with_field(ctx):
+    row_ptr = np.array([0, 0], np.int32)
+    inst = ctx.add_csr(row_ptr, np.zeros(0, np.int32), np.zeros(0), h=np.array([0.75]))
+    g = ctx.solve(inst, 3, 2.0, 6.0, seed=1, outputs=("m_final", "spins", "t0"))
+    o = O.mars_solve(O.Instance.csr((row_ptr, np.zeros(0, np.int32), np.zeros(0)),
+                                    np.array([0.75])),
+                     np.zeros((3, 1), np.float32) + 0.3, g.t0)
+    assert np.all(g.spins == -1) and g.best_energy == -0.75
+    ctx.free(inst)
+
+
+def test_field_sparse_trajectory(ctx):
+    csr = I.er_graph(200, 6, 8, "pm1")
+    h = np.random.default_rng(4).normal(size=200)
+    order = I.greedy_colour_order(csr)
+    inst = ctx.add_csr(*csr, h=h, order=order)
+    m0, t0 = I.replica_inputs(7, 200, 0.5, 5.0, 3)
+    g = ctx.solve(inst, 7, 0.5, 5.0, fixed_sweeps=4, m0=m0, t0=t0, outputs=("m_final", "spins"))
+    o = O.mars_solve(O.Instance.csr(csr, h), m0, t0, fixed_sweeps=4, order=order)
+    assert np.abs(g.m_final - o["m"]).max() <= M_TOL
+    e, _ = ctx.energy(inst, g.spins)
+    np.testing.assert_allclose(e, O.energies(O.Instance.csr(csr, h), g.spins), rtol=0, atol=1e-9)
+    ctx.free(inst)
+
+
+def test_large_n_streaming_path(ctx):
+    """n too large for shared memory: magnetisations live in global memory."""
+    csr = I.er_graph(70000, 4, 6, "pm1")
+    order = I.greedy_colour_order(csr)
+    inst = ctx.add_csr(*csr, order=order)
+    m0, t0 = I.replica_inputs(3, csr.n, 0.0, 4.0, 8)
+    g = ctx.solve(inst, 3, 0.0, 4.0, fixed_sweeps=2, m0=m0, t0=t0, outputs=("m_final",))
+    o = O.mars_solve(O.Instance.csr(csr), m0, t0, fixed_sweeps=2, order=order)
+    assert np.abs(g.m_final - o["m"]).max() <= M_TOL
+    ctx.free(inst)
+
+
+def test_device_pointer_inputs_and_outputs(ctx):
+    import torch
+    csr = I.ea_lattice(16, 2, 2)
+    order = I.greedy_colour_order(csr)
+    rp = torch.from_numpy(csr.row_ptr).cuda()
+    col = torch.from_numpy(csr.col).cuda()
+    val = torch.from_numpy(csr.val.astype(np.float32)).cuda()
+    inst = ctx.add_csr(rp, col, val, order=order)
+    m0, t0 = I.replica_inputs(8, csr.n, 0.0, 4.0, 9)
+    g = ctx.solve(inst, 8, 0.0, 4.0, fixed_sweeps=2, m0=torch.from_numpy(m0).cuda(),
+                  t0=torch.from_numpy(t0).cuda(), outputs=("m_final", "energies"),
+                  device_outputs=True)
+    o = O.mars_solve(O.Instance.csr(csr), m0, t0, fixed_sweeps=2, order=order)
+    assert g.m_final.is_cuda
+    assert np.abs(g.m_final.cpu().numpy() - o["m"]).max() <= M_TOL
+    ctx.free(inst)
+
+
+def test_invalid_inputs_rejected(ctx):
+    from paper_1907_05124_gb300.mars import MarsError, MARS_EINVAL
+    J = I.sk_pm1(8, 0)
+    bad = J.copy()
+    bad[0, 1] = 5.0
+    with pytest.raises(MarsError) as e:
+        ctx.add_dense(bad)
+    assert e.value.code == MARS_EINVAL
+    diag = J.copy()
+    diag[2, 2] = 1.0
+    with pytest.raises(MarsError):
+        ctx.add_dense(diag)
+    csr = I.ea_lattice(4, 2, 0)
+    rp, col, val = csr
+    val2 = val.copy()
+    val2[0] = -val2[0]  # breaks symmetry
+    with pytest.raises(MarsError):
+        ctx.add_csr(rp, col, val2)
+    with pytest.raises(MarsError):
+        ctx.add_csr(rp, col, val, order=np.zeros(16, np.int32))
+    inst = ctx.add_csr(rp, col, val)
+    with pytest.raises(MarsError):
+        ctx.solve(inst, 4, 3.0, 1.0)
+    with pytest.raises(MarsError):
+        ctx.solve(inst, 4, 0.0, 1.0, c_step=0.0)
+    with pytest.raises(MarsError):
+        ctx.solve(inst, 0, 0.0, 1.0)
+    with pytest.raises(MarsError):
+        ctx.energy(inst, np.zeros((1, 16), np.int8))
+    ctx.free(inst)
+    with pytest.raises(MarsError):
+        ctx.free(inst)
+
+
+def test_hbm_budget_enforced():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_05124_gb300 import mars
+    from paper_1907_05124_gb300.mars import MarsError, MARS_ENOMEM
+    c = mars.Context(0, hbm_budget_bytes=4096)
+    with pytest.raises(MarsError) as e:
+        c.add_dense(I.sk_pm1(64, 0))
+    assert e.value.code == MARS_ENOMEM
+    c.close()
+
+
+# --------------------------------------------------------------------------
+# the benchmark's workload at full size: 2-D EA L = 100, R = 1024
+# --------------------------------------------------------------------------
+
+def test_full_size_ea2d_sampled_replicas(ctx):
+    csr = I.ea_lattice(100, 2, 0)
+    inst = ctx.add_csr(*csr)  # library colour order, as the benchmark uses
+    order = I.greedy_colour_order(csr)
+    R, tmax = 1024, 4.0
+    # fixed sweeps with the library's own start-state draw; the oracle draws the
+    # same replicas from the published generator definition
+    g = ctx.solve(inst, R, 0.0, tmax, seed=0, fixed_sweeps=2, outputs=("m_final", "t0"))
+    sample = [0, 1, 511, 1023]
+    for r in sample:
+        m0, t0 = O.draw_replicas(0, 1, csr.n, 0.0, tmax, r0=r)
+        assert t0[0] == g.t0[r]
+        o = O.mars_solve(O.Instance.csr(csr), m0, t0, fixed_sweeps=2, order=order)
+        assert np.abs(g.m_final[r] - o["m"][0]).max() <= M_TOL
+    # the stopping rule at full size: energies are exact for the returned spins
+    g = ctx.solve(inst, R, 0.0, tmax, seed=0, outputs=("energies", "spins", "sweeps"))
+    assert g.best_energy == O.energy(O.Instance.csr(csr), g.best_spins)
+    for r in (3, 700):
+        assert g.energies[r] == O.energy(O.Instance.csr(csr), g.spins[r])
+    assert g.spin_updates == int(g.replica_sweeps.sum()) * csr.n
+    assert g.best_energy >= -csr.nnz // 2
+    ctx.free(inst)
