@@ -1,0 +1,357 @@
+// Sparse MARS descent, fast path: sliced-ELL couplings and on-chip replicas.
+//
+// Same method and same schedule as kernels_sparse.cu (Section 3, Algorithm 1:
+// sequential sweeps reproduced level by level), with a layout built for the
+// SM instead of a plain CSR walk:
+//
+//  * Within a level the runtime sorts spins by degree and cuts them into
+//    slices of 32 consecutive new labels (any order inside a level gives the
+//    sequential sweep's values, since those spins share no coupling). A
+//    slice's couplings are stored slot-major, padded to the slice's largest
+//    degree: entry d of row q sits at off + 32*d + q. A warp walks one slice,
+//    lane q owns row q, and each of its loads is one coalesced 128-byte line.
+//    Padding points at a dummy spin whose magnetisation is held at 0.
+//  * +-1 couplings are one 32-bit word: column | sign bit. General weights
+//    are a (column, value) pair.
+//  * A thread owns one spin for all RT replicas of the tile: one coupling
+//    load, one RT-wide shared-memory gather, RT multiply-adds.
+//
+// The tile's magnetisations m[i*RT + k] live in shared memory for the whole
+// descent; the dummy row n is zero. Only the sweeps' parallel steps need a
+// block barrier.
+#include "device_common.cuh"
+#include "mars_internal.h"
+
+#include <algorithm>
+
+namespace mars {
+namespace {
+
+constexpr int kThreads = 1024;
+constexpr int kWarps = kThreads / 32;
+
+template <int RT>
+struct Vec;
+template <>
+struct Vec<1> {
+    using T = float;
+    __device__ static T load(const float* p) { return *p; }
+    __device__ static void store(float* p, T v) { *p = v; }
+    __device__ static float get(const T& v, int) { return v; }
+    __device__ static void set(T& v, int, float x) { v = x; }
+};
+template <>
+struct Vec<2> {
+    using T = float2;
+    __device__ static T load(const float* p) { return *reinterpret_cast<const float2*>(p); }
+    __device__ static void store(float* p, T v) { *reinterpret_cast<float2*>(p) = v; }
+    __device__ static float get(const T& v, int k) { return k == 0 ? v.x : v.y; }
+    __device__ static void set(T& v, int k, float x) { if (k == 0) v.x = x; else v.y = x; }
+};
+template <>
+struct Vec<4> {
+    using T = float4;
+    __device__ static T load(const float* p) { return *reinterpret_cast<const float4*>(p); }
+    __device__ static void store(float* p, T v) { *reinterpret_cast<float4*>(p) = v; }
+    __device__ static float get(const T& v, int k)
+    {
+        return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+    }
+    __device__ static void set(T& v, int k, float x)
+    {
+        if (k == 0) v.x = x; else if (k == 1) v.y = x; else if (k == 2) v.z = x; else v.w = x;
+    }
+};
+
+// One coupling: (column, weight). PM1 entries pack the sign in bit 31.
+template <bool PM1>
+struct Entry;
+template <>
+struct Entry<true> {
+    const uint32_t* e;
+    __device__ void get(int idx, int& col, float& w) const
+    {
+        const uint32_t v = __ldg(e + idx);
+        col = (int)(v & 0x7fffffffu);
+        w = (v >> 31) ? -1.f : 1.f;
+    }
+};
+template <>
+struct Entry<false> {
+    const int2* e;
+    __device__ void get(int idx, int& col, float& w) const
+    {
+        const int2 v = __ldg(e + idx);
+        col = v.x;
+        w = __int_as_float(v.y);
+    }
+};
+
+template <int RT, bool PM1>
+__global__ void __launch_bounds__(kThreads, 1) sparse_sell_kernel(DevInstance in, DevSolve s)
+{
+    using V = Vec<RT>;
+    extern __shared__ __align__(16) float m[];  // (n+1)*RT
+    __shared__ double s_T[RT];
+    __shared__ float s_invT[RT];
+    __shared__ int s_lvl_sweeps[RT], s_sweeps[RT], s_levels[RT], s_capped[RT], s_active[RT];
+    __shared__ float s_dred[kWarps][RT];
+    __shared__ long long s_ei[kWarps][RT];
+    __shared__ double s_ef[kWarps][RT];
+    __shared__ int s_tile, s_any;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = in.n;
+    Entry<PM1> ent;
+    if constexpr (PM1) ent.e = in.sell_pm1; else ent.e = in.sell_gen;
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(s.work_counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= s.ntiles) break;
+
+        // ---- start states: caller m0 or the counter-based draw ------------------
+        for (int idx = tid; idx < (n + 1) * RT; idx += kThreads) {
+            const int i = idx / RT, k = idx % RT;
+            const int r = s.tile_rep[tile * RT + k];
+            float v = 0.f;
+            if (i < n && r >= 0) {
+                const int o = __ldg(in.new2old + i);
+                v = s.m0 ? __ldg(s.m0 + (size_t)r * n + o) : draw_m0(s.seed, s.stream, r, o);
+            }
+            m[idx] = v;
+        }
+        if (tid < RT) {
+            const int r = s.tile_rep[tile * RT + tid];
+            const double T = (r >= 0 ? (double)s.t0[r] : 0.0) - s.c_step;
+            const bool act = r >= 0 && T > 0.0;
+            s_T[tid] = T;
+            s_invT[tid] = act ? (float)(1.0 / T) : 0.f;
+            s_active[tid] = act;
+            s_levels[tid] = act ? 1 : 0;
+            s_lvl_sweeps[tid] = 0;
+            s_sweeps[tid] = 0;
+            s_capped[tid] = 0;
+        }
+        __syncthreads();
+
+        // ---- temperature levels and sweeps -------------------------------------
+        for (;;) {
+            if (tid == 0) {
+                int any = 0;
+#pragma unroll
+                for (int q = 0; q < RT; ++q) any |= s_active[q];
+                s_any = any;
+            }
+            __syncthreads();
+            if (!s_any) break;
+            float invT[RT];
+            bool act[RT];
+            float dloc[RT];
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                invT[k] = s_invT[k];
+                act[k] = s_active[k] != 0;
+                dloc[k] = 0.f;
+            }
+            for (int l = 0; l < in.nlev; ++l) {
+                const int s0 = __ldg(in.lvl_slice + l), s1 = __ldg(in.lvl_slice + l + 1);
+                for (int sl = s0 + warp; sl < s1; sl += kWarps) {
+                    const int4 d = __ldg(in.slices + sl);  // row0, rows, degree, offset
+                    if (lane < d.y) {
+                        const int i = d.x + lane;
+                        typename V::T acc;
+#pragma unroll
+                        for (int k = 0; k < RT; ++k) V::set(acc, k, 0.f);
+#pragma unroll 4
+                        for (int q = 0; q < d.z; ++q) {
+                            int c;
+                            float w;
+                            ent.get(d.w + 32 * q + lane, c, w);
+                            const typename V::T mv = V::load(m + c * RT);
+#pragma unroll
+                            for (int k = 0; k < RT; ++k)
+                                V::set(acc, k, fmaf(w, V::get(mv, k), V::get(acc, k)));
+                        }
+                        const float hv = in.h ? __ldg(in.h + i) : 0.f;
+                        const typename V::T old = V::load(m + i * RT);
+                        typename V::T nv = old;
+#pragma unroll
+                        for (int k = 0; k < RT; ++k) {
+                            if (act[k]) {
+                                const float sn = -tanhf((V::get(acc, k) + hv) * invT[k]);
+                                dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(old, k)));
+                                V::set(nv, k, sn);
+                            }
+                        }
+                        V::store(m + i * RT, nv);
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                const float v = warp_reduce_strided<1>(dloc[k], MaxOp());
+                if (lane == 0) s_dred[warp][k] = v;
+            }
+            __syncthreads();
+            if (tid < RT && s_active[tid]) {
+                float dd = 0.f;
+#pragma unroll 8
+                for (int w = 0; w < kWarps; ++w) dd = fmaxf(dd, s_dred[w][tid]);
+                int ls = s_lvl_sweeps[tid] + 1;
+                s_sweeps[tid] += 1;
+                const bool level_done = s.fixed_sweeps > 0 ? ls >= s.fixed_sweeps
+                                                           : (dd <= s.d_min || ls >= s.k_max);
+                if (level_done) {
+                    if (s.fixed_sweeps == 0 && !(dd <= s.d_min)) s_capped[tid] += 1;
+                    const double T = s_T[tid] - s.c_step;
+                    s_T[tid] = T;
+                    ls = 0;
+                    if (T > 0.0) {
+                        s_levels[tid] += 1;
+                        s_invT[tid] = (float)(1.0 / T);
+                    } else {
+                        s_active[tid] = 0;
+                    }
+                }
+                s_lvl_sweeps[tid] = ls;
+            }
+            __syncthreads();
+        }
+
+        // ---- sign-round, outputs and exact energy --------------------------------
+        long long ei[RT];
+        double ef[RT];
+        int rep[RT];
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            ei[k] = 0;
+            ef[k] = 0.0;
+            rep[k] = s.tile_rep[tile * RT + k];
+        }
+        for (int i = tid; i < n; i += kThreads) {
+            const int o = __ldg(in.new2old + i);
+            const int e0 = __ldg(in.row_ptr + i), e1 = __ldg(in.row_ptr + i + 1);
+            const typename V::T mi = V::load(m + i * RT);
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                const int r = rep[k];
+                if (r < 0) continue;
+                const float mv = V::get(mi, k);
+                const int si = mv >= 0.f ? 1 : -1;
+                s.sigma[(size_t)r * n + o] = (int8_t)si;
+                if (s.m_final) s.m_final[(size_t)r * n + o] = mv;
+            }
+            for (int e = e0; e < e1; ++e) {
+                const int j = __ldg(in.col + e);
+                if (j <= i) continue;
+                const typename V::T mj = V::load(m + j * RT);
+                if (in.integer) {
+                    const int w = (int)__ldg(in.val_i8 + e);
+#pragma unroll
+                    for (int k = 0; k < RT; ++k)
+                        ei[k] += (long long)(w * (V::get(mi, k) >= 0.f ? 1 : -1) *
+                                             (V::get(mj, k) >= 0.f ? 1 : -1));
+                } else {
+                    const double w = __ldg(in.val_f64 + e);
+#pragma unroll
+                    for (int k = 0; k < RT; ++k)
+                        ef[k] += w * ((V::get(mi, k) >= 0.f) == (V::get(mj, k) >= 0.f) ? 1.0 : -1.0);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                const int si = V::get(mi, k) >= 0.f ? 1 : -1;
+                if (in.integer) {
+                    if (in.h) ei[k] += (long long)__ldg(in.h + i) * si;
+                } else if (in.h_f64) {
+                    ef[k] += __ldg(in.h_f64 + i) * si;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const long long a = warp_reduce_strided<1>(ei[k], SumOp());
+            const double b = warp_reduce_strided<1>(ef[k], SumOp());
+            if (lane == 0) { s_ei[warp][k] = a; s_ef[warp][k] = b; }
+        }
+        __syncthreads();
+        if (tid < RT) {
+            const int r = rep[tid];
+            if (r >= 0) {
+                long long ti = 0;
+                double tf = 0.0;
+                for (int w = 0; w < kWarps; ++w) { ti += s_ei[w][tid]; tf += s_ef[w][tid]; }
+                s.energy[r] = in.integer ? (double)ti : tf;
+                s.energy_i64[r] = in.integer ? ti : 0;
+                s.sweeps[r] = s_sweeps[tid];
+                s.levels[r] = s_levels[tid];
+                s.capped[r] = s_capped[tid];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+const void* pick(int rt, bool pm1)
+{
+    switch (rt) {
+    case 1: return pm1 ? (const void*)sparse_sell_kernel<1, true> : (const void*)sparse_sell_kernel<1, false>;
+    case 2: return pm1 ? (const void*)sparse_sell_kernel<2, true> : (const void*)sparse_sell_kernel<2, false>;
+    case 4: return pm1 ? (const void*)sparse_sell_kernel<4, true> : (const void*)sparse_sell_kernel<4, false>;
+    default: return nullptr;
+    }
+}
+
+}  // namespace
+
+bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p)
+{
+    if (!in.slices || (!in.sell_pm1 && !in.sell_gen)) return false;
+    int sms = 1, optin = 48 * 1024;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    const size_t budget = (size_t)optin - 12 * 1024;  // static shared memory and slack
+    int rt = 0;
+    for (int c : {4, 2, 1}) {
+        if ((size_t)(in.n + 1) * c * sizeof(float) <= budget && (R + c - 1) / c >= std::min(R, sms)) {
+            rt = c;
+            break;
+        }
+    }
+    if (rt == 0) {
+        if ((size_t)(in.n + 1) * sizeof(float) > budget) return false;
+        rt = 1;
+    }
+    p->rt = rt;
+    p->onchip = 1;
+    p->threads = kThreads;
+    p->smem = (size_t)(in.n + 1) * rt * sizeof(float);
+    p->sell = 1;
+    const void* k = pick(rt, in.sell_pm1 != nullptr);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, p->smem);
+    if (per_sm < 1) per_sm = 1;
+    const int ntiles = (R + rt - 1) / rt;
+    p->grid = std::max(1, std::min(ntiles, sms * per_sm));
+    p->scratch_floats = 0;
+    return true;
+}
+
+cudaError_t launch_sparse_sell(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
+                               cudaStream_t st)
+{
+    const void* k = pick(p.rt, in.sell_pm1 != nullptr);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    DevInstance a = in;
+    DevSolve b = s;
+    void* args[] = {&a, &b};
+    return cudaLaunchKernel(k, dim3(p.grid), dim3(kThreads), args, p.smem, st);
+}
+
+}  // namespace mars

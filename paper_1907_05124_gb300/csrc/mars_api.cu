@@ -479,10 +479,16 @@ int mars_instance_csr(mars_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
         level[v] = lv;
         nlev = std::max(nlev, lv + 1);
     }
+    // New labels: by level, then by degree (descending) so that the 32-row
+    // slices of the ELL copy are nearly uniform, then by visiting position.
+    // Spins of one level share no coupling, so their relative order is free.
     std::vector<int32_t> new2old(n), old2new(n), lvl_start(nlev + 1, 0);
     std::iota(new2old.begin(), new2old.end(), 0);
     std::stable_sort(new2old.begin(), new2old.end(), [&](int32_t a, int32_t b) {
-        return level[a] != level[b] ? level[a] < level[b] : pos[a] < pos[b];
+        if (level[a] != level[b]) return level[a] < level[b];
+        const int32_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];
+        if (da != db) return da > db;
+        return pos[a] < pos[b];
     });
     for (int32_t a = 0; a < n; ++a) { old2new[new2old[a]] = a; lvl_start[level[new2old[a]] + 1]++; }
     for (int32_t l = 0; l < nlev; ++l) lvl_start[l + 1] += lvl_start[l];
@@ -506,6 +512,45 @@ int mars_instance_csr(mars_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
             if (integer) nval_i8[e] = (int8_t)row[q].second;
         }
     }
+    // Sliced-ELL copy: per level, 32 consecutive new labels per slice, entries
+    // slot-major and padded to the slice's largest degree with the dummy spin n.
+    bool pm1 = integer;
+    for (int64_t e = 0; e < nnz && pm1; ++e) pm1 = nval_f64[e] == 1.0 || nval_f64[e] == -1.0;
+    std::vector<int32_t> lvl_slice(nlev + 1, 0);
+    std::vector<int32_t> slice_words;  // row0, rows, degree, offset per slice
+    std::vector<uint32_t> sell_pm1;
+    std::vector<int32_t> sell_gen;     // (column, float bits) pairs
+    int64_t sell_len = 0;
+    for (int32_t l = 0; l < nlev; ++l) {
+        for (int32_t r0 = lvl_start[l]; r0 < lvl_start[l + 1]; r0 += 32) {
+            const int32_t rows = std::min(32, lvl_start[l + 1] - r0);
+            int32_t deg = 0;
+            for (int32_t q = 0; q < rows; ++q) deg = std::max(deg, nrp[r0 + q + 1] - nrp[r0 + q]);
+            slice_words.insert(slice_words.end(), {r0, rows, deg, (int32_t)sell_len});
+            for (int32_t t = 0; t < deg; ++t) {
+                for (int32_t q = 0; q < 32; ++q) {
+                    int32_t cidx = n;
+                    double w = 0.0;
+                    if (q < rows && t < nrp[r0 + q + 1] - nrp[r0 + q]) {
+                        cidx = ncol[nrp[r0 + q] + t];
+                        w = nval_f64[nrp[r0 + q] + t];
+                    }
+                    if (pm1) {
+                        sell_pm1.push_back((uint32_t)cidx | (w < 0 ? 0x80000000u : 0u));
+                    } else {
+                        const float wf = (float)w;
+                        int32_t bits;
+                        std::memcpy(&bits, &wf, sizeof bits);
+                        sell_gen.push_back(cidx);
+                        sell_gen.push_back(bits);
+                    }
+                }
+            }
+            sell_len += (int64_t)deg * 32;
+            if (sell_len > INT32_MAX) return fail(c, MARS_EINVAL, "padded coupling table too large");
+        }
+        lvl_slice[l + 1] = (int32_t)(slice_words.size() / 4);
+    }
     std::vector<float> hf;
     std::vector<double> hd;
     if (!hh.empty()) {
@@ -514,6 +559,16 @@ int mars_instance_csr(mars_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
         for (int32_t a = 0; a < n; ++a) { hf[a] = (float)hh[new2old[a]]; hd[a] = hh[new2old[a]]; }
     }
     DevInstance& d = in->dev;
+    {
+        const int32_t* sw = nullptr;
+        if ((rc = upload(c, in.get(), slice_words, &sw))) return rc;
+        d.slices = (const int4*)sw;
+        if ((rc = upload(c, in.get(), lvl_slice, &d.lvl_slice))) return rc;
+        if ((rc = upload(c, in.get(), sell_pm1, &d.sell_pm1))) return rc;
+        const int32_t* sg = nullptr;
+        if ((rc = upload(c, in.get(), sell_gen, &sg))) return rc;
+        d.sell_gen = (const int2*)sg;
+    }
     d.n = n;
     d.dense = 0;
     d.nnz = nnz;
@@ -666,7 +721,8 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
         dp = plan_dense(in->dev, R, s.jacobi, c->device);
         if (dp.scratch_floats && (rc = S.get(dp.scratch_floats, &s.m_scratch))) return rc;
     } else {
-        sp = plan_sparse(in->dev, R, s.jacobi, c->device);
+        if (s.jacobi || !plan_sparse_sell(in->dev, R, c->device, &sp))
+            sp = plan_sparse(in->dev, R, s.jacobi, c->device);
         rt = sp.rt;
         const size_t per = (size_t)sp.grid * n * rt;
         float* scr = nullptr;
@@ -691,7 +747,10 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     if (in->dev.dense) {
         MARS_CUDA(c, launch_dense(in->dev, s, dp, st));
     } else {
-        MARS_CUDA(c, launch_sparse(in->dev, s, sp, st));
+        if (sp.sell)
+            MARS_CUDA(c, launch_sparse_sell(in->dev, s, sp, st));
+        else
+            MARS_CUDA(c, launch_sparse(in->dev, s, sp, st));
     }
     MARS_CUDA(c, cudaEventRecord(c->ev2, st));
     MARS_CUDA(c, launch_best(s, n, in->dev.integer, dbest, dres, st));

@@ -24,6 +24,11 @@ struct DevInstance {
     const int8_t* val_i8 = nullptr;    // integer instances
     const double* val_f64 = nullptr;   // every instance: exact values for energies
     const int32_t* lvl_start = nullptr;  // nlev+1 offsets into new labels
+    // sliced-ELL copy of the couplings: 32-row slices {row0, rows, degree, offset}
+    const int4* slices = nullptr;
+    const int32_t* lvl_slice = nullptr;  // nlev+1 offsets into slices
+    const uint32_t* sell_pm1 = nullptr;  // +-1 couplings: column | sign << 31
+    const int2* sell_gen = nullptr;      // general couplings: (column, float bits)
     // dense (n*n, new labels: Jn[a][b] = J[new2old[a]][new2old[b]])
     const float* Jf = nullptr;
     const int8_t* J_i8 = nullptr;
@@ -82,7 +87,11 @@ struct SparsePlan {
     size_t smem = 0;    // dynamic shared memory
     int grid = 0;
     size_t scratch_floats = 0;  // m_scratch (+ m_next) floats needed
+    int sell = 0;       // the sliced-ELL kernel
 };
+bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p);
+cudaError_t launch_sparse_sell(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
+                               cudaStream_t st);
 SparsePlan plan_sparse(const DevInstance& in, int R, int jacobi, int device);
 cudaError_t launch_sparse(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
                           cudaStream_t st);
