@@ -4,7 +4,7 @@
 // spins one after another (Gauss-Seidel: every spin shares a coupling with
 // every other, so there is no parallelism inside one replica's sweep); the
 // warp spreads each local field Phi_a = sum_b J_ab s_b over its 32 lanes and
-// reduces it with shuffles. The replica's magnetisations stay in shared memory
+// reduces it with shuffles, in compensated arithmetic (see Dot2). The replica's magnetisations stay in shared memory
 // when they fit, J is read through the read-only cache and shared by every
 // warp on the SM. This is the plain FP32 path the tensor-core path is checked
 // against; it is exact in its arithmetic order, not fast for large n.
@@ -18,12 +18,40 @@ namespace {
 
 constexpr int kDenseWarps = 4;
 
-__device__ __forceinline__ float warp_sum(float v)
-{
+// Compensated dot product (Ogita, Rump, Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005, algorithm Dot2): every product's
+// rounding error comes from an FMA, every sum's from TwoSum, and the errors
+// are carried in a second float. The result is as accurate as a dot product
+// evaluated in twice the working precision and then rounded, so the local
+// field of a dense row does not lose ulps to a 32-lane tree of n terms.
+// Explicit-rounding intrinsics keep the compiler from fusing the error terms.
+struct Dot2 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add_product(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);
+        add_pair(p, pe);
+    }
+    __device__ __forceinline__ void add_pair(float v, float err)
+    {
+        const float t = __fadd_rn(s, v);
+        const float z = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(v, z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(e, err));
+    }
+    __device__ __forceinline__ float warp_total()
+    {
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-    return v;
-}
+        for (int m = 16; m >= 1; m >>= 1) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, s, m);
+            const float c2 = __shfl_xor_sync(0xffffffffu, c, m);
+            add_pair(s2, c2);
+        }
+        return __fadd_rn(s, c);
+    }
+};
 
 template <bool ONCHIP, bool JACOBI>
 __global__ void __launch_bounds__(kDenseWarps * 32) dense_descent_kernel(DevInstance in, DevSolve s)
@@ -52,10 +80,10 @@ __global__ void __launch_bounds__(kDenseWarps * 32) dense_descent_kernel(DevInst
         float d = 0.f;
         for (int a = 0; a < n; ++a) {
             const float* Jrow = in.Jf + (size_t)a * n;
-            float p = 0.f;
-            for (int b = lane; b < n; b += 32) p = fmaf(__ldg(Jrow + b), m[b], p);
-            p = warp_sum(p);
-            if (in.h) p += __ldg(in.h + a);
+            Dot2 acc;
+            for (int b = lane; b < n; b += 32) acc.add_product(__ldg(Jrow + b), m[b]);
+            if (in.h && lane == 0) acc.add_pair(__ldg(in.h + a), 0.f);
+            const float p = acc.warp_total();
             const float sn = -tanhf(p * invT);
             d = fmaxf(d, fabsf(sn - m[a]));
             __syncwarp();

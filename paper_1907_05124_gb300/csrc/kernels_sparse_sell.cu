@@ -94,193 +94,126 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_sell_kernel(DevInstance in
     extern __shared__ __align__(16) float m[];  // (n+1)*RT
     __shared__ double s_T[RT];
     __shared__ float s_invT[RT];
+    __shared__ int s_rep[RT], s_fresh[RT], s_done[RT];
     __shared__ int s_lvl_sweeps[RT], s_sweeps[RT], s_levels[RT], s_capped[RT], s_active[RT];
     __shared__ float s_dred[kWarps][RT];
     __shared__ long long s_ei[kWarps][RT];
     __shared__ double s_ef[kWarps][RT];
-    __shared__ int s_tile, s_any;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = in.n;
     Entry<PM1> ent;
     if constexpr (PM1) ent.e = in.sell_pm1; else ent.e = in.sell_gen;
 
+    // Each of the RT slots takes replicas from the queue s.tile_rep[0..R) (longest
+    // start temperatures first) until it is empty: when a slot's replica ends,
+    // the slot is finalised and refilled at once, so no slot idles while work
+    // remains.
+    if (tid == 0) {
+        for (int k = 0; k < RT; ++k) {
+            const int q = atomicAdd(s.work_counter, 1);
+            const int r = q < s.R ? s.tile_rep[q] : -1;
+            s_rep[k] = r;
+            s_fresh[k] = r >= 0;
+            s_done[k] = 0;
+            s_active[k] = 0;
+        }
+    }
+    __syncthreads();
+
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(s.work_counter, 1);
-        __syncthreads();
-        const int tile = s_tile;
-        if (tile >= s.ntiles) break;
+        // ---- fresh slots: start state (caller m0 or the draw) and first level --
+        bool fresh[RT], any_fresh = false;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) { fresh[k] = s_fresh[k] != 0; any_fresh |= fresh[k]; }
+        if (any_fresh) {
+            for (int idx = tid; idx < (n + 1) * RT; idx += kThreads) {
+                const int i = idx / RT, k = idx % RT;
+                if (!fresh[k]) continue;
+                const int r = s_rep[k];
+                float v = 0.f;
+                if (i < n) {
+                    const int o = __ldg(in.new2old + i);
+                    v = s.m0 ? __ldg(s.m0 + (size_t)r * n + o) : draw_m0(s.seed, s.stream, r, o);
+                }
+                m[idx] = v;
+            }
+            __syncthreads();
+            if (tid < RT && fresh[tid]) {
+                const double T = (double)s.t0[s_rep[tid]] - s.c_step;
+                const bool act = T > 0.0;
+                s_T[tid] = T;
+                s_invT[tid] = act ? (float)(1.0 / T) : 0.f;
+                s_active[tid] = act;
+                s_done[tid] = !act;  // no level with T > 0: the result is sign(m0)
+                s_levels[tid] = act ? 1 : 0;
+                s_lvl_sweeps[tid] = 0;
+                s_sweeps[tid] = 0;
+                s_capped[tid] = 0;
+                s_fresh[tid] = 0;
+            }
+            __syncthreads();
+        }
 
-        // ---- start states: caller m0 or the counter-based draw ------------------
-        for (int idx = tid; idx < (n + 1) * RT; idx += kThreads) {
-            const int i = idx / RT, k = idx % RT;
-            const int r = s.tile_rep[tile * RT + k];
-            float v = 0.f;
-            if (i < n && r >= 0) {
+        // ---- finished slots: sign-round, outputs, exact energy; then refill ----
+        bool done[RT], any_done = false;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) { done[k] = s_done[k] != 0; any_done |= done[k]; }
+        if (any_done) {
+            long long ei[RT];
+            double ef[RT];
+            int rep[RT];
+#pragma unroll
+            for (int k = 0; k < RT; ++k) { ei[k] = 0; ef[k] = 0.0; rep[k] = s_rep[k]; }
+            for (int i = tid; i < n; i += kThreads) {
                 const int o = __ldg(in.new2old + i);
-                v = s.m0 ? __ldg(s.m0 + (size_t)r * n + o) : draw_m0(s.seed, s.stream, r, o);
-            }
-            m[idx] = v;
-        }
-        if (tid < RT) {
-            const int r = s.tile_rep[tile * RT + tid];
-            const double T = (r >= 0 ? (double)s.t0[r] : 0.0) - s.c_step;
-            const bool act = r >= 0 && T > 0.0;
-            s_T[tid] = T;
-            s_invT[tid] = act ? (float)(1.0 / T) : 0.f;
-            s_active[tid] = act;
-            s_levels[tid] = act ? 1 : 0;
-            s_lvl_sweeps[tid] = 0;
-            s_sweeps[tid] = 0;
-            s_capped[tid] = 0;
-        }
-        __syncthreads();
-
-        // ---- temperature levels and sweeps -------------------------------------
-        for (;;) {
-            if (tid == 0) {
-                int any = 0;
+                const typename V::T mi = V::load(m + i * RT);
 #pragma unroll
-                for (int q = 0; q < RT; ++q) any |= s_active[q];
-                s_any = any;
-            }
-            __syncthreads();
-            if (!s_any) break;
-            float invT[RT];
-            bool act[RT];
-            float dloc[RT];
-#pragma unroll
-            for (int k = 0; k < RT; ++k) {
-                invT[k] = s_invT[k];
-                act[k] = s_active[k] != 0;
-                dloc[k] = 0.f;
-            }
-            for (int l = 0; l < in.nlev; ++l) {
-                const int s0 = __ldg(in.lvl_slice + l), s1 = __ldg(in.lvl_slice + l + 1);
-                for (int sl = s0 + warp; sl < s1; sl += kWarps) {
-                    const int4 d = __ldg(in.slices + sl);  // row0, rows, degree, offset
-                    if (lane < d.y) {
-                        const int i = d.x + lane;
-                        typename V::T acc;
-#pragma unroll
-                        for (int k = 0; k < RT; ++k) V::set(acc, k, 0.f);
-#pragma unroll 4
-                        for (int q = 0; q < d.z; ++q) {
-                            int c;
-                            float w;
-                            ent.get(d.w + 32 * q + lane, c, w);
-                            const typename V::T mv = V::load(m + c * RT);
-#pragma unroll
-                            for (int k = 0; k < RT; ++k)
-                                V::set(acc, k, fmaf(w, V::get(mv, k), V::get(acc, k)));
-                        }
-                        const float hv = in.h ? __ldg(in.h + i) : 0.f;
-                        const typename V::T old = V::load(m + i * RT);
-                        typename V::T nv = old;
-#pragma unroll
-                        for (int k = 0; k < RT; ++k) {
-                            if (act[k]) {
-                                const float sn = -tanhf((V::get(acc, k) + hv) * invT[k]);
-                                dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(old, k)));
-                                V::set(nv, k, sn);
-                            }
-                        }
-                        V::store(m + i * RT, nv);
-                    }
+                for (int k = 0; k < RT; ++k) {
+                    if (!done[k]) continue;
+                    const float mv = V::get(mi, k);
+                    s.sigma[(size_t)rep[k] * n + o] = (int8_t)(mv >= 0.f ? 1 : -1);
+                    if (s.m_final) s.m_final[(size_t)rep[k] * n + o] = mv;
                 }
-                __syncthreads();
-            }
+                const int e0 = __ldg(in.row_ptr + i), e1 = __ldg(in.row_ptr + i + 1);
+                for (int e = e0; e < e1; ++e) {
+                    const int j = __ldg(in.col + e);
+                    if (j <= i) continue;
+                    const typename V::T mj = V::load(m + j * RT);
+                    if (in.integer) {
+                        const int w = (int)__ldg(in.val_i8 + e);
 #pragma unroll
-            for (int k = 0; k < RT; ++k) {
-                const float v = warp_reduce_strided<1>(dloc[k], MaxOp());
-                if (lane == 0) s_dred[warp][k] = v;
-            }
-            __syncthreads();
-            if (tid < RT && s_active[tid]) {
-                float dd = 0.f;
-#pragma unroll 8
-                for (int w = 0; w < kWarps; ++w) dd = fmaxf(dd, s_dred[w][tid]);
-                int ls = s_lvl_sweeps[tid] + 1;
-                s_sweeps[tid] += 1;
-                const bool level_done = s.fixed_sweeps > 0 ? ls >= s.fixed_sweeps
-                                                           : (dd <= s.d_min || ls >= s.k_max);
-                if (level_done) {
-                    if (s.fixed_sweeps == 0 && !(dd <= s.d_min)) s_capped[tid] += 1;
-                    const double T = s_T[tid] - s.c_step;
-                    s_T[tid] = T;
-                    ls = 0;
-                    if (T > 0.0) {
-                        s_levels[tid] += 1;
-                        s_invT[tid] = (float)(1.0 / T);
+                        for (int k = 0; k < RT; ++k)
+                            if (done[k])
+                                ei[k] += (V::get(mi, k) >= 0.f) == (V::get(mj, k) >= 0.f) ? w : -w;
                     } else {
-                        s_active[tid] = 0;
+                        const double w = __ldg(in.val_f64 + e);
+#pragma unroll
+                        for (int k = 0; k < RT; ++k)
+                            if (done[k])
+                                ef[k] += (V::get(mi, k) >= 0.f) == (V::get(mj, k) >= 0.f) ? w : -w;
                     }
                 }
-                s_lvl_sweeps[tid] = ls;
+#pragma unroll
+                for (int k = 0; k < RT; ++k) {
+                    if (!done[k]) continue;
+                    const int si = V::get(mi, k) >= 0.f ? 1 : -1;
+                    if (in.integer) {
+                        if (in.h) ei[k] += (long long)__ldg(in.h + i) * si;
+                    } else if (in.h_f64) {
+                        ef[k] += __ldg(in.h_f64 + i) * si;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                const long long a = warp_reduce_strided<1>(ei[k], SumOp());
+                const double b = warp_reduce_strided<1>(ef[k], SumOp());
+                if (lane == 0) { s_ei[warp][k] = a; s_ef[warp][k] = b; }
             }
             __syncthreads();
-        }
-
-        // ---- sign-round, outputs and exact energy --------------------------------
-        long long ei[RT];
-        double ef[RT];
-        int rep[RT];
-#pragma unroll
-        for (int k = 0; k < RT; ++k) {
-            ei[k] = 0;
-            ef[k] = 0.0;
-            rep[k] = s.tile_rep[tile * RT + k];
-        }
-        for (int i = tid; i < n; i += kThreads) {
-            const int o = __ldg(in.new2old + i);
-            const int e0 = __ldg(in.row_ptr + i), e1 = __ldg(in.row_ptr + i + 1);
-            const typename V::T mi = V::load(m + i * RT);
-#pragma unroll
-            for (int k = 0; k < RT; ++k) {
-                const int r = rep[k];
-                if (r < 0) continue;
-                const float mv = V::get(mi, k);
-                const int si = mv >= 0.f ? 1 : -1;
-                s.sigma[(size_t)r * n + o] = (int8_t)si;
-                if (s.m_final) s.m_final[(size_t)r * n + o] = mv;
-            }
-            for (int e = e0; e < e1; ++e) {
-                const int j = __ldg(in.col + e);
-                if (j <= i) continue;
-                const typename V::T mj = V::load(m + j * RT);
-                if (in.integer) {
-                    const int w = (int)__ldg(in.val_i8 + e);
-#pragma unroll
-                    for (int k = 0; k < RT; ++k)
-                        ei[k] += (long long)(w * (V::get(mi, k) >= 0.f ? 1 : -1) *
-                                             (V::get(mj, k) >= 0.f ? 1 : -1));
-                } else {
-                    const double w = __ldg(in.val_f64 + e);
-#pragma unroll
-                    for (int k = 0; k < RT; ++k)
-                        ef[k] += w * ((V::get(mi, k) >= 0.f) == (V::get(mj, k) >= 0.f) ? 1.0 : -1.0);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < RT; ++k) {
-                const int si = V::get(mi, k) >= 0.f ? 1 : -1;
-                if (in.integer) {
-                    if (in.h) ei[k] += (long long)__ldg(in.h + i) * si;
-                } else if (in.h_f64) {
-                    ef[k] += __ldg(in.h_f64 + i) * si;
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < RT; ++k) {
-            const long long a = warp_reduce_strided<1>(ei[k], SumOp());
-            const double b = warp_reduce_strided<1>(ef[k], SumOp());
-            if (lane == 0) { s_ei[warp][k] = a; s_ef[warp][k] = b; }
-        }
-        __syncthreads();
-        if (tid < RT) {
-            const int r = rep[tid];
-            if (r >= 0) {
+            if (tid < RT && done[tid]) {
+                const int r = rep[tid];
                 long long ti = 0;
                 double tf = 0.0;
                 for (int w = 0; w < kWarps; ++w) { ti += s_ei[w][tid]; tf += s_ef[w][tid]; }
@@ -290,6 +223,93 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_sell_kernel(DevInstance in
                 s.levels[r] = s_levels[tid];
                 s.capped[r] = s_capped[tid];
             }
+            __syncthreads();
+            if (tid == 0) {
+                for (int k = 0; k < RT; ++k) {
+                    if (!done[k]) continue;
+                    const int q = atomicAdd(s.work_counter, 1);
+                    const int r = q < s.R ? s.tile_rep[q] : -1;
+                    s_rep[k] = r;
+                    s_fresh[k] = r >= 0;
+                    s_done[k] = 0;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        bool act[RT], any_act = false;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) { act[k] = s_active[k] != 0; any_act |= act[k]; }
+        if (!any_act) break;  // every slot is empty: the queue ran dry
+
+        // ---- one sweep: the levels in order, each a parallel step -------------
+        float invT[RT], dloc[RT];
+#pragma unroll
+        for (int k = 0; k < RT; ++k) { invT[k] = s_invT[k]; dloc[k] = 0.f; }
+        for (int l = 0; l < in.nlev; ++l) {
+            const int s0 = __ldg(in.lvl_slice + l), s1 = __ldg(in.lvl_slice + l + 1);
+            for (int sl = s0 + warp; sl < s1; sl += kWarps) {
+                const int4 d = __ldg(in.slices + sl);  // row0, rows, degree, offset
+                if (lane < d.y) {
+                    const int i = d.x + lane;
+                    typename V::T acc;
+#pragma unroll
+                    for (int k = 0; k < RT; ++k) V::set(acc, k, 0.f);
+#pragma unroll 4
+                    for (int q = 0; q < d.z; ++q) {
+                        int c;
+                        float w;
+                        ent.get(d.w + 32 * q + lane, c, w);
+                        const typename V::T mv = V::load(m + c * RT);
+#pragma unroll
+                        for (int k = 0; k < RT; ++k)
+                            V::set(acc, k, fmaf(w, V::get(mv, k), V::get(acc, k)));
+                    }
+                    const float hv = in.h ? __ldg(in.h + i) : 0.f;
+                    const typename V::T old = V::load(m + i * RT);
+                    typename V::T nv = old;
+#pragma unroll
+                    for (int k = 0; k < RT; ++k) {
+                        if (act[k]) {
+                            const float sn = -tanhf((V::get(acc, k) + hv) * invT[k]);
+                            dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(old, k)));
+                            V::set(nv, k, sn);
+                        }
+                    }
+                    V::store(m + i * RT, nv);
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float v = warp_reduce_strided<1>(dloc[k], MaxOp());
+            if (lane == 0) s_dred[warp][k] = v;
+        }
+        __syncthreads();
+        if (tid < RT && s_active[tid]) {
+            float dd = 0.f;
+#pragma unroll 8
+            for (int w = 0; w < kWarps; ++w) dd = fmaxf(dd, s_dred[w][tid]);
+            int ls = s_lvl_sweeps[tid] + 1;
+            s_sweeps[tid] += 1;
+            const bool level_done = s.fixed_sweeps > 0 ? ls >= s.fixed_sweeps
+                                                       : (dd <= s.d_min || ls >= s.k_max);
+            if (level_done) {
+                if (s.fixed_sweeps == 0 && !(dd <= s.d_min)) s_capped[tid] += 1;
+                const double T = s_T[tid] - s.c_step;
+                s_T[tid] = T;
+                ls = 0;
+                if (T > 0.0) {
+                    s_levels[tid] += 1;
+                    s_invT[tid] = (float)(1.0 / T);
+                } else {
+                    s_active[tid] = 0;
+                    s_done[tid] = 1;
+                }
+            }
+            s_lvl_sweeps[tid] = ls;
         }
         __syncthreads();
     }

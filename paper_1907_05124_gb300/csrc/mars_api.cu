@@ -733,6 +733,8 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     std::vector<int32_t> reps(R);
     std::iota(reps.begin(), reps.end(), 0);
     std::stable_sort(reps.begin(), reps.end(), [&](int32_t a, int32_t b) { return t0h[a] > t0h[b]; });
+    // Tiles of rt replicas in that order; the sliced-ELL kernel instead treats
+    // the list as one queue that its replica slots draw from.
     const int32_t ntiles = (R + rt - 1) / rt;
     std::vector<int32_t> tile_rep((size_t)ntiles * rt, -1);
     for (int32_t q = 0; q < R; ++q) tile_rep[q] = reps[q];
