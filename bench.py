@@ -280,7 +280,7 @@ def run_mars(args, world, rank, local):
     peak = 152 * 128 * 2 * sm_clock_ghz / 1e3  # FP32 FMA lanes x 2 flop x clock, TFLOP/s
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "sparse_sell_kernel<4, +-1 couplings>",
+                "kernel": "sparse_sell_kernel<RT=2, 1024 threads, +-1 couplings>",
                 "descent_ms_mean": 1e3 * d_mean,
                 "spin_updates_per_s_descent": upd_per_launch / d_mean}
 

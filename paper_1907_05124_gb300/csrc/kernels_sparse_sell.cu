@@ -23,12 +23,28 @@
 #include "mars_internal.h"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace mars {
 namespace {
 
-constexpr int kThreads = 1024;
-constexpr int kWarps = kThreads / 32;
+// tanh(x) = sign(x) (1 - 2 / (1 + e^{2|x|})), with e^{2|x|} = 2^{2|x| log2 e}
+// from the SFU's ex2.approx and the quotient from its rcp.approx. Absolute
+// error below 2.5e-7 over all of R (checked against FP64 tanh through the C
+// ABI by the fields-only test); saturates to +-1 when 2|x| log2 e overflows.
+__device__ __forceinline__ float tanh_sfu(float x)
+{
+    // tanh(x) = sign(x) (1 - 2 / (1 + 2^{2|x| log2 e})), SFU ex2 and rcp; below
+    // |x| = 1e-3 the odd series x - x^3/3 (error < 2e-16) keeps tiny fields'
+    // signs, which the difference 1 - 2/(1+e) would round away.
+    const float a = fabsf(x) * 2.8853900817779268f;
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(a));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
+    const float big = copysignf(fmaf(-2.0f, r, 1.0f), x);
+    const float small = fmaf(x * x, x * -0.333333343f, x);
+    return fabsf(x) < 1e-3f ? small : big;
+}
 
 template <int RT>
 struct Vec;
@@ -87,9 +103,11 @@ struct Entry<false> {
     }
 };
 
-template <int RT, bool PM1>
-__global__ void __launch_bounds__(kThreads, 1) sparse_sell_kernel(DevInstance in, DevSolve s)
+template <int RT, int NT, bool PM1>
+__global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance in, DevSolve s)
 {
+    constexpr int kThreads = NT;
+    constexpr int kWarps = NT / 32;
     using V = Vec<RT>;
     extern __shared__ __align__(16) float m[];  // (n+1)*RT
     __shared__ double s_T[RT];
@@ -272,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_sell_kernel(DevInstance in
 #pragma unroll
                     for (int k = 0; k < RT; ++k) {
                         if (act[k]) {
-                            const float sn = -tanhf((V::get(acc, k) + hv) * invT[k]);
+                            const float sn = -tanh_sfu((V::get(acc, k) + hv) * invT[k]);
                             dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(old, k)));
                             V::set(nv, k, sn);
                         }
@@ -315,18 +333,44 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_sell_kernel(DevInstance in
     }
 }
 
-const void* pick(int rt, bool pm1)
+template <int RT, int NT>
+const void* pick_nt(bool pm1)
 {
-    switch (rt) {
-    case 1: return pm1 ? (const void*)sparse_sell_kernel<1, true> : (const void*)sparse_sell_kernel<1, false>;
-    case 2: return pm1 ? (const void*)sparse_sell_kernel<2, true> : (const void*)sparse_sell_kernel<2, false>;
-    case 4: return pm1 ? (const void*)sparse_sell_kernel<4, true> : (const void*)sparse_sell_kernel<4, false>;
-    default: return nullptr;
+    return pm1 ? (const void*)sparse_sell_kernel<RT, NT, true> : (const void*)sparse_sell_kernel<RT, NT, false>;
+}
+
+const void* pick(int rt, int nt, bool pm1)
+{
+    if (nt == 512) {
+        switch (rt) {
+        case 1: return pick_nt<1, 512>(pm1);
+        case 2: return pick_nt<2, 512>(pm1);
+        case 4: return pick_nt<4, 512>(pm1);
+        }
+    } else if (nt == 1024) {
+        switch (rt) {
+        case 1: return pick_nt<1, 1024>(pm1);
+        case 2: return pick_nt<2, 1024>(pm1);
+        case 4: return pick_nt<4, 1024>(pm1);
+        }
     }
+    return nullptr;
+}
+
+int env_int(const char* name, int dflt)
+{
+    const char* v = std::getenv(name);
+    return v && *v ? std::atoi(v) : dflt;
 }
 
 }  // namespace
 
+// Launch shape: replica slots per CTA (RT) and threads per CTA. A GB300
+// sweep of the six shapes on the 2-D L=100 lattice, R=1024 (spin-updates/s):
+// RT=2 with 1024 threads 3.46e11; RT=1/1024 2.63e11; RT=4/1024 2.64e11;
+// the 512-thread shapes 2.0-2.2e11. Wider CTAs give a lone replica's sweep
+// more threads; two slots amortise the coupling loads without the 4-wide
+// tail. MARS_SELL_RT / MARS_SELL_THREADS override the choice for tuning.
 bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p)
 {
     if (!in.slices || (!in.sell_pm1 && !in.sell_gen)) return false;
@@ -334,26 +378,22 @@ bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     const size_t budget = (size_t)optin - 12 * 1024;  // static shared memory and slack
-    int rt = 0;
-    for (int c : {4, 2, 1}) {
-        if ((size_t)(in.n + 1) * c * sizeof(float) <= budget && (R + c - 1) / c >= std::min(R, sms)) {
-            rt = c;
-            break;
-        }
-    }
-    if (rt == 0) {
-        if ((size_t)(in.n + 1) * sizeof(float) > budget) return false;
-        rt = 1;
-    }
+    int rt = env_int("MARS_SELL_RT", 2);
+    int nt = env_int("MARS_SELL_THREADS", 1024);
+    if (rt != 1 && rt != 2 && rt != 4) rt = 1;
+    if (nt != 512 && nt != 1024) nt = 512;
+    while (rt > 1 && (size_t)(in.n + 1) * rt * sizeof(float) > budget) rt /= 2;
+    if ((size_t)(in.n + 1) * rt * sizeof(float) > budget) return false;
     p->rt = rt;
     p->onchip = 1;
-    p->threads = kThreads;
+    p->threads = nt;
     p->smem = (size_t)(in.n + 1) * rt * sizeof(float);
     p->sell = 1;
-    const void* k = pick(rt, in.sell_pm1 != nullptr);
+    const void* k = pick(rt, nt, in.sell_pm1 != nullptr);
+    if (!k) return false;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, p->smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, p->smem);
     if (per_sm < 1) per_sm = 1;
     const int ntiles = (R + rt - 1) / rt;
     p->grid = std::max(1, std::min(ntiles, sms * per_sm));
@@ -364,14 +404,14 @@ bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p)
 cudaError_t launch_sparse_sell(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
                                cudaStream_t st)
 {
-    const void* k = pick(p.rt, in.sell_pm1 != nullptr);
+    const void* k = pick(p.rt, p.threads, in.sell_pm1 != nullptr);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     DevInstance a = in;
     DevSolve b = s;
     void* args[] = {&a, &b};
-    return cudaLaunchKernel(k, dim3(p.grid), dim3(kThreads), args, p.smem, st);
+    return cudaLaunchKernel(k, dim3(p.grid), dim3(p.threads), args, p.smem, st);
 }
 
 }  // namespace mars

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace mars {
@@ -30,6 +32,9 @@ struct DevInstance {
     const uint32_t* sell_pm1 = nullptr;  // +-1 couplings: column | sign << 31
     const int2* sell_gen = nullptr;      // general couplings: (column, float bits)
     // dense (n*n, new labels: Jn[a][b] = J[new2old[a]][new2old[b]])
+    int32_t n_pad = 0;                   // n rounded up to the 128-spin panel
+    const __nv_bfloat16* Jbf = nullptr;  // n_pad*n_pad BF16, zero padded (tensor-core operand)
+    const float* Jdiag = nullptr;        // (n_pad/128) FP32 128x128 diagonal blocks
     const float* Jf = nullptr;
     const int8_t* J_i8 = nullptr;
     const double* J_f64 = nullptr;
@@ -95,6 +100,51 @@ cudaError_t launch_sparse_sell(const DevInstance& in, const DevSolve& s, const S
 SparsePlan plan_sparse(const DevInstance& in, int R, int jacobi, int device);
 cudaError_t launch_sparse(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
                           cudaStream_t st);
+
+// Tensor-core dense path (kernels_dense_tc.cu).
+struct TcPanel {
+    int32_t p0 = 0;          // first row of the panel
+    int32_t kblocks = 0;     // 64-wide K blocks per split
+    int32_t R_pad = 0;
+    float* G = nullptr;      // [split][R_pad][128]
+    const int32_t* active_prefix = nullptr;
+    int32_t* err = nullptr;
+};
+struct TcState {
+    int32_t R = 0, R_pad = 0, n = 0, n_pad = 0, splitk = 1;
+    float* G = nullptr;
+    float* S = nullptr;            // [R][n_pad] FP32 magnetisations, slot order
+    __nv_bfloat16* Sb = nullptr;   // [R_pad][n_pad] BF16 shadow (tensor-core operand)
+    const float* Jdiag = nullptr;
+    const float* h = nullptr;
+    const int32_t* rep = nullptr;      // slot -> replica
+    const int32_t* new2old = nullptr;
+    const float* m0 = nullptr;
+    const float* t0 = nullptr;
+    uint64_t seed = 0;
+    uint32_t stream = 0;
+    double c_step = 1.0;
+    float d_min = 1e-4f;
+    int32_t k_max = 1000, fixed_sweeps = 0;
+    double* T = nullptr;
+    float* invT = nullptr;
+    float* d = nullptr;
+    int32_t* active = nullptr;
+    int32_t* levels = nullptr;
+    int32_t* lvl_sweeps = nullptr;
+    int32_t* sweeps = nullptr;
+    int32_t* capped = nullptr;
+    int32_t* counters = nullptr;       // [0] active prefix, [1] active count, [2] error
+};
+size_t tc_gemm_smem(int bn);
+cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g,
+                                 int bn, int n_tiles, int splitk, cudaStream_t st);
+cudaError_t launch_tc_chain(const TcState& t, int p, cudaStream_t st);
+cudaError_t launch_tc_init(const TcState& t, cudaStream_t st);
+cudaError_t launch_tc_advance(const TcState& t, cudaStream_t st);
+cudaError_t launch_tc_prefix(const TcState& t, cudaStream_t st);
+cudaError_t launch_tc_finalize(const TcState& t, const DevInstance& in, const DevSolve& s,
+                               cudaStream_t st);
 
 struct DensePlan {
     int warps_per_block = 4;

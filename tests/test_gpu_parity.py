@@ -434,3 +434,49 @@ def test_full_size_ea2d_sampled_replicas(ctx):
     assert g.spin_updates == int(g.replica_sweeps.sum()) * csr.n
     assert g.best_energy >= -csr.nnz // 2
     ctx.free(inst)
+
+
+# --------------------------------------------------------------------------
+# the sliced-ELL kernel's tanh and launch shapes
+# --------------------------------------------------------------------------
+
+def test_sfu_tanh_absolute_error_bound(ctx):
+    """Couplings present but zero: Phi_i = h_i exactly, and one sweep at T = 1
+    returns -tanh(h_i) as the kernel evaluates it; compare with FP64 tanh."""
+    n = 8192
+    i = np.arange(n)
+    row_ptr = np.arange(0, 2 * n + 1, 2, dtype=np.int32)
+    col = np.stack([(i - 1) % n, (i + 1) % n], axis=1).astype(np.int32)
+    col.sort(axis=1)
+    h = np.concatenate([np.linspace(-20, 20, n - 16),
+                        [0.0, 1e-30, -1e-30, 1e-7, -1e-7, 1e-3, -1e-3, 0.5, -0.5, 88.0, -88.0,
+                         1e4, -1e4, 3e-5, 0.125, -0.125]])
+    inst = ctx.add_csr(row_ptr, col.ravel(), np.zeros(2 * n), h=h)
+    t0 = np.full(2, 2.0, np.float32)  # one level at T = 1: 1/T = 1 exactly
+    m0 = np.zeros((2, n), np.float32)
+    g = ctx.solve(inst, 2, 2.0, 2.0, fixed_sweeps=1, m0=m0, t0=t0, outputs=("m_final",))
+    ref = -np.tanh(h.astype(np.float32).astype(np.float64))
+    err = np.abs(g.m_final[0] - ref).max()
+    assert err <= 2.5e-7, err
+    assert np.all(np.abs(g.m_final[0]) <= 1.0)
+    assert np.all(np.sign(g.m_final[0][h != 0]) == -np.sign(h[h != 0]))
+    ctx.free(inst)
+
+
+@pytest.mark.parametrize("rt,threads", [(1, 512), (1, 1024), (2, 512), (4, 1024)])
+def test_sell_launch_shapes_agree(ctx, monkeypatch, rt, threads):
+    """Every replica-slot width and CTA size gives the oracle's trajectory."""
+    monkeypatch.setenv("MARS_SELL_RT", str(rt))
+    monkeypatch.setenv("MARS_SELL_THREADS", str(threads))
+    csr = I.er_graph(3000, 9, 12, "pm1")
+    order = I.greedy_colour_order(csr)
+    inst = ctx.add_csr(*csr, order=order)
+    R = 11
+    m0, t0 = I.replica_inputs(R, csr.n, 0.0, 6.0, 41)
+    t0 = floored_t0(t0, max_levels=STRICT_LEVELS)
+    g = ctx.solve(inst, R, 0.0, 6.0, fixed_sweeps=1, m0=m0, t0=t0, outputs=("m_final", "energies"))
+    o = O.mars_solve(O.Instance.csr(csr), m0, t0, fixed_sweeps=1, order=order)
+    check_trajectory(g.m_final, o["m"], "strict")
+    g2 = ctx.solve(inst, 40, 0.0, 6.0, seed=5, outputs=("energies", "spins"))
+    assert np.array_equal(g2.energies, O.energies(O.Instance.csr(csr), g2.spins))
+    ctx.free(inst)
