@@ -238,6 +238,47 @@ int mars_draw_replicas(mars_ctx* ctx, uint64_t seed, uint32_t stream, int32_t r0
                        int32_t n, double t_min, double t_max, float* m0, float* t0,
                        uint32_t flags);
 
+/*
+ * Bytes of the static device array behind mars_solve_noalloc (16 MiB).
+ */
+#define MARS_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * mars_solve_noalloc: the solve of mars_solve without allocating any device
+ * memory. The paper has no counterpart to this entry point. It is for
+ * callers that cannot allocate device memory while they run: a program whose
+ * device memory is already reserved in full by another framework's allocator,
+ * or a latency-bound loop that must not call an allocator (or handle its
+ * failure) once it has started. Such a caller registers its instances at
+ * start-up, when allocation is still allowed, and solves them with this call.
+ *
+ * Every per-solve buffer (start temperatures, the replica queue, per-replica
+ * spins and energies, counters, the result) lives in one file-scope static
+ * device array of MARS_NOALLOC_SCRATCH_BYTES. Each GPU that loads the library
+ * holds that array until the process exits. The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ *  - Inputs: an instance registered earlier, and params as for mars_solve
+ *    with update MARS_UPDATE_GS, precision MARS_FP32 and t0 = NULL (the
+ *    start temperatures are always drawn); m0 may be a device pointer
+ *    (MARS_DEVICE_PTR) or NULL.
+ *  - Outputs: best_spins (n int8, device pointer, required), energies
+ *    (R doubles, device pointer, or NULL) and result (host, or NULL). Replicas
+ *    run in index order instead of longest-first; each replica's result is
+ *    the same as mars_solve's for the same seed.
+ *  - Limit: the replica count and n must fit the array (about R*n + 40*R
+ *    bytes); larger requests, and instances too large for the on-chip kernels,
+ *    return MARS_EINVAL with a message naming the limit.
+ *  - Set-up: the first call on a device looks up the array's device address
+ *    with cudaGetSymbolAddress (with that device current) and caches it; make
+ *    that first call before any stream capture on the device.
+ *  - Sharing: all calls share the one array and each starts by clearing the
+ *    counters it needs at zero. Calls whose work overlaps on the GPU (other
+ *    streams, other contexts, other threads) race on the array: serialise
+ *    them.
+ */
+int mars_solve_noalloc(mars_ctx* ctx, int32_t inst, const mars_params* params, int8_t* best_spins,
+                       double* energies, mars_result* result);
+
 #ifdef __cplusplus
 }
 #endif

@@ -241,6 +241,32 @@ Instance* find(mars_ctx* c, int32_t id)
 
 }  // namespace
 
+// Accessors for mars_noalloc.cu.
+int noalloc_view(mars_ctx* c, int32_t id, NoallocView* v)
+{
+    if (!c || !v) return MARS_EINVAL;
+    Instance* in = find(c, id);
+    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    v->device = c->device;
+    v->stream = c->stream;
+    v->inst = &in->dev;
+    v->total_weight = in->info.total_weight;
+    v->energy_err_bound =
+        in->dev.integer ? 0.0 : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + in->dev.n);
+    return MARS_OK;
+}
+
+int noalloc_fail(mars_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
 extern "C" {
 
 int mars_create(mars_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream)

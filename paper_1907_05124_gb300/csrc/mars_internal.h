@@ -166,4 +166,18 @@ cudaError_t launch_best(const DevSolve& s, int32_t n, int32_t integer, int8_t* b
 cudaError_t launch_energy(const DevInstance& in, const int8_t* spins, int32_t count,
                           double* e, long long* e_i64, int32_t* status, cudaStream_t st);
 
+// Read-only view of a context and one of its instances, for entry points that
+// live outside mars_api.cu (mars_noalloc.cu).
+struct NoallocView {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    const DevInstance* inst = nullptr;
+    double total_weight = 0.0;
+    double energy_err_bound = 0.0;
+};
+
 }  // namespace mars
+
+struct mars_ctx;
+int noalloc_view(mars_ctx* c, int32_t inst, mars::NoallocView* v);
+int noalloc_fail(mars_ctx* c, int code, const char* fmt, ...);

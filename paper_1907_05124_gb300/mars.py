@@ -20,6 +20,7 @@ MARS_OK, MARS_EINVAL, MARS_ENOMEM, MARS_EAGAIN, MARS_ETIMEOUT, MARS_EDEVICE, MAR
     0, -1, -2, -3, -4, -5, -6
 MARS_I8, MARS_F32, MARS_F64 = 1, 2, 3
 MARS_DEVICE_PTR = 1
+NOALLOC_SCRATCH_BYTES = 16 << 20  # MARS_NOALLOC_SCRATCH_BYTES
 UPDATE = {"gs": 0, "jacobi": 1}
 PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
 
@@ -87,6 +88,7 @@ SIGNATURES = {
     "mars_draw_replicas": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                           ctypes.c_double, P, P, ctypes.c_uint32]),
+    "mars_solve_noalloc": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P]),
 }
 
 _lib = None
