@@ -209,6 +209,12 @@ typedef struct {
     double energy_err_bound;  /* 0 when energies are exact */
     int32_t status;           /* MARS_OK or the device-side error */
     int32_t integer;          /* 1 if energies are exact integers */
+    /* Tensor-core path only (precision BF16): CUDA-event time, count and
+     * algorithmic flops (2 x 128 x n per active replica) of the panel GEMM
+     * launches of one sampled sweep per batch of sweeps; 0 elsewhere. */
+    double gemm_seconds;
+    int64_t gemm_launches;
+    double gemm_flops;
 } mars_result;
 
 /*

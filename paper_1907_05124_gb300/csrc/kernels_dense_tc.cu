@@ -135,6 +135,21 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) tc::tmem_dealloc(tmem, BN);
 }
 
+// Compensated accumulate: (s, c) += a * b with the product's and the sum's
+// rounding errors carried in c (TwoProduct by FMA, TwoSum; Ogita, Rump,
+// Oishi 2005). Keeps each field within a few FP32 ulps of exact after the
+// up to 127 in-panel corrections a spin receives.
+__device__ __forceinline__ void acc2(float& s, float& c, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+
 // One warp per replica slot: the panel's 128 spins in sequence.
 __global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t, int p)
 {
@@ -148,14 +163,16 @@ __global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t
     if (slot >= t.R || !t.active[slot]) return;
     const int p0 = p * kBM;
     const float invT = t.invT[slot];
-    float g[4], sf[4], so_f[4], so_b[4];
+    float g[4], gc[4], sf[4], so_f[4], so_b[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int a = lane + 32 * q;
-        float acc = 0.f;
-        for (int sp = 0; sp < t.splitk; ++sp) acc += t.G[((size_t)sp * t.R_pad + slot) * kBM + a];
-        if (t.h && p0 + a < t.n) acc += __ldg(t.h + p0 + a);
+        float acc = 0.f, accc = 0.f;
+        for (int sp = 0; sp < t.splitk; ++sp)
+            acc2(acc, accc, t.G[((size_t)sp * t.R_pad + slot) * kBM + a], 1.0f);
+        if (t.h && p0 + a < t.n) acc2(acc, accc, __ldg(t.h + p0 + a), 1.0f);
         g[q] = acc;
+        gc[q] = accc;
         const size_t idx = (size_t)slot * t.n_pad + p0 + a;
         so_f[q] = t.S[idx];
         so_b[q] = __bfloat162float(t.Sb[idx]);
@@ -169,7 +186,7 @@ __global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t
             const int a = qa * 32 + l;
             float delta = 0.f;
             if (lane == l) {
-                const float sn = -tanh_sfu(g[qa] * invT);
+                const float sn = -tanh_sfu(__fadd_rn(g[qa], gc[qa]) * invT);
                 dloc = fmaxf(dloc, fabsf(sn - so_f[qa]));
                 delta = sn - so_b[qa];
                 sf[qa] = sn;
@@ -179,7 +196,7 @@ __global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t
 #pragma unroll
             for (int q = qa; q < 4; ++q) {
                 const int k = lane + 32 * q;
-                if (k > a) g[q] = fmaf(Jrow[k], delta, g[q]);
+                if (k > a) acc2(g[q], gc[q], Jrow[k], delta);
             }
         }
     }

@@ -262,15 +262,27 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance 
         if (!any_act) break;  // every slot is empty: the queue ran dry
 
         // ---- one sweep: the levels in order, each a parallel step -------------
+        // A thread updates its spin for all RT replicas from one coupling load
+        // and RT-wide gathers (dead slots skip only their tanh). When a single
+        // slot is left (the queue ran dry) it takes a one-replica path, so a
+        // straggler replica's sweep costs what a one-replica sweep costs.
         float invT[RT], dloc[RT];
+        int live = 0;
 #pragma unroll
-        for (int k = 0; k < RT; ++k) { invT[k] = s_invT[k]; dloc[k] = 0.f; }
+        for (int k = 0; k < RT; ++k) {
+            invT[k] = s_invT[k];
+            dloc[k] = 0.f;
+            live |= act[k] ? 1 << k : 0;
+        }
+        const bool all_live = RT == 1 || __popc(live) > 1;
         for (int l = 0; l < in.nlev; ++l) {
             const int s0 = __ldg(in.lvl_slice + l), s1 = __ldg(in.lvl_slice + l + 1);
             for (int sl = s0 + warp; sl < s1; sl += kWarps) {
                 const int4 d = __ldg(in.slices + sl);  // row0, rows, degree, offset
-                if (lane < d.y) {
-                    const int i = d.x + lane;
+                if (lane >= d.y) continue;
+                const int i = d.x + lane;
+                const float hv = in.h ? __ldg(in.h + i) : 0.f;
+                if (all_live) {
                     typename V::T acc;
 #pragma unroll
                     for (int k = 0; k < RT; ++k) V::set(acc, k, 0.f);
@@ -284,18 +296,36 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance 
                         for (int k = 0; k < RT; ++k)
                             V::set(acc, k, fmaf(w, V::get(mv, k), V::get(acc, k)));
                     }
-                    const float hv = in.h ? __ldg(in.h + i) : 0.f;
                     const typename V::T old = V::load(m + i * RT);
-                    typename V::T nv = old;
+                    typename V::T nv;
 #pragma unroll
                     for (int k = 0; k < RT; ++k) {
-                        if (act[k]) {
+                        if ((live >> k) & 1) {
                             const float sn = -tanh_sfu((V::get(acc, k) + hv) * invT[k]);
                             dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(old, k)));
                             V::set(nv, k, sn);
+                        } else {
+                            V::set(nv, k, V::get(old, k));
                         }
                     }
                     V::store(m + i * RT, nv);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < RT; ++k) {
+                        if (!((live >> k) & 1)) continue;
+                        float acc = 0.f;
+#pragma unroll 4
+                        for (int q = 0; q < d.z; ++q) {
+                            int c;
+                            float w;
+                            ent.get(d.w + 32 * q + lane, c, w);
+                            acc = fmaf(w, m[c * RT + k], acc);
+                        }
+                        const float old = m[i * RT + k];
+                        const float sn = -tanh_sfu((acc + hv) * invT[k]);
+                        dloc[k] = fmaxf(dloc[k], fabsf(sn - old));
+                        m[i * RT + k] = sn;
+                    }
                 }
             }
             __syncthreads();

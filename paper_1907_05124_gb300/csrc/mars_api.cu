@@ -5,6 +5,8 @@
 #include "../../include/mars.h"
 #include "mars_internal.h"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -50,6 +52,11 @@ struct mars_ctx {
     std::map<int32_t, std::unique_ptr<Instance>> insts;
     int32_t next_id = 1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    std::vector<cudaEvent_t> prof;  // event pairs around sampled panel GEMM launches
+    ~mars_ctx()
+    {
+        for (cudaEvent_t e : prof) cudaEventDestroy(e);
+    }
 };
 
 namespace {
@@ -241,6 +248,164 @@ Instance* find(mars_ctx* c, int32_t id)
 
 }  // namespace
 
+// Round-to-nearest-even FP32 -> BF16 bits (host side, for uploads).
+uint16_t float_to_bf16_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;  // NaN
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Row-major [outer][inner] BF16 matrix, boxes of box_inner x box_outer with the
+// 128-byte swizzle (box_inner = 64 BF16 = 128 bytes).
+bool encode_bf16_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
+                    uint32_t box_inner, uint32_t box_outer)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {inner * 2};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The dense descent on tensor cores: slots in start-temperature order, a
+// sweep = for each 128-spin panel {BF16 panel GEMM, in-panel sequential
+// chain}, then the level step; the host checks the active count between
+// batches of sweeps. Writes the same per-replica outputs as the other paths.
+struct TcProfile {
+    double gemm_seconds = 0.0, gemm_flops = 0.0;
+    int64_t gemm_launches = 0;
+};
+
+int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve& s,
+                 const std::vector<int32_t>& reps, float t0_max, Scratch& S, TcProfile* prof)
+{
+    cudaStream_t st = c->stream;
+    const DevInstance& d = in->dev;
+    const int32_t R = s.R, n = d.n, n_pad = d.n_pad, P = n_pad / 128;
+    constexpr int BN = 128;
+    const int32_t R_pad = (R + BN - 1) / BN * BN;
+    const int ntiles = R_pad / BN;
+    // Split K until the panel GEMM fills the SMs in one wave (one CTA per SM).
+    int splitk = 1;
+    while (splitk < 8 && ntiles * splitk * 2 <= c->sms && (n_pad / 64) % (splitk * 2) == 0)
+        splitk *= 2;
+    int rc;
+    TcState t;
+    t.R = R;
+    t.R_pad = R_pad;
+    t.n = n;
+    t.n_pad = n_pad;
+    t.splitk = splitk;
+    t.Jdiag = d.Jdiag;
+    t.h = d.h;
+    t.new2old = d.new2old;
+    t.m0 = s.m0;
+    t.t0 = s.t0;
+    t.seed = s.seed;
+    t.stream = s.stream;
+    t.c_step = s.c_step;
+    t.d_min = s.d_min;
+    t.k_max = s.k_max;
+    t.fixed_sweeps = s.fixed_sweeps;
+    int32_t* rep = nullptr;
+    if ((rc = S.get((size_t)R * n_pad, &t.S))) return rc;
+    if ((rc = S.get((size_t)R_pad * n_pad, &t.Sb))) return rc;
+    if ((rc = S.get((size_t)splitk * R_pad * 128, &t.G))) return rc;
+    if ((rc = S.get(R, &t.T))) return rc;
+    if ((rc = S.get(R, &t.invT))) return rc;
+    if ((rc = S.get(R, &t.d))) return rc;
+    if ((rc = S.get(R, &t.active))) return rc;
+    if ((rc = S.get(R, &t.levels))) return rc;
+    if ((rc = S.get(R, &t.lvl_sweeps))) return rc;
+    if ((rc = S.get(R, &t.sweeps))) return rc;
+    if ((rc = S.get(R, &t.capped))) return rc;
+    if ((rc = S.get(4, &t.counters))) return rc;
+    if ((rc = S.get(R, &rep))) return rc;
+    t.rep = rep;
+    MARS_CUDA(c, cudaMemcpyAsync(rep, reps.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    MARS_CUDA(c, cudaMemsetAsync(t.Sb, 0, (size_t)R_pad * n_pad * sizeof(__nv_bfloat16), st));
+    MARS_CUDA(c, cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), st));
+    CUtensorMap tmJ, tmS;
+    if (!encode_bf16_2d(&tmJ, d.Jbf, n_pad, n_pad, 64, 128) ||
+        !encode_bf16_2d(&tmS, t.Sb, n_pad, R_pad, 64, BN))
+        return fail(c, MARS_EDEVICE, "tensor map encoding failed");
+    MARS_CUDA(c, launch_tc_init(t, st));
+    MARS_CUDA(c, launch_tc_prefix(t, st));
+    TcPanel g;
+    g.kblocks = n_pad / 64 / splitk;
+    g.R_pad = R_pad;
+    g.G = t.G;
+    g.active_prefix = t.counters;
+    g.err = t.counters + 2;
+    // Every replica ends within (levels + 1) x (sweeps per level) sweeps.
+    const double levels_max = std::ceil((double)t0_max / s.c_step) + 1.0;
+    const int64_t sweep_cap =
+        (int64_t)(levels_max * (double)(s.fixed_sweeps > 0 ? s.fixed_sweeps : s.k_max)) + 1;
+    int64_t done_sweeps = 0;
+    int batch = 1;
+    int32_t hc[4] = {0, 0, 0, 0};
+    MARS_CUDA(c, cudaMemcpyAsync(hc, t.counters, sizeof hc, cudaMemcpyDeviceToHost, st));
+    MARS_CUDA(c, cudaStreamSynchronize(st));
+    // Event pairs around the panel GEMMs of the first sweep of every batch.
+    while ((int)c->prof.size() < 2 * P) {
+        cudaEvent_t e;
+        MARS_CUDA(c, cudaEventCreate(&e));
+        c->prof.push_back(e);
+    }
+    for (;;) {
+        const int32_t active_now = hc[1];
+        for (int b = 0; b < batch; ++b) {
+            for (int pp = 0; pp < P; ++pp) {
+                g.p0 = pp * 128;
+                if (b == 0) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp], st));
+                MARS_CUDA(c, launch_tc_panel_gemm(tmJ, tmS, g, BN, ntiles, splitk, st));
+                if (b == 0) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp + 1], st));
+                MARS_CUDA(c, launch_tc_chain(t, pp, st));
+            }
+            MARS_CUDA(c, launch_tc_advance(t, st));
+        }
+        done_sweeps += batch;
+        MARS_CUDA(c, cudaMemcpyAsync(hc, t.counters, sizeof hc, cudaMemcpyDeviceToHost, st));
+        MARS_CUDA(c, cudaStreamSynchronize(st));
+        for (int pp = 0; pp < P; ++pp) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, c->prof[2 * pp], c->prof[2 * pp + 1]);
+            prof->gemm_seconds += ms * 1e-3;
+            prof->gemm_launches += 1;
+            prof->gemm_flops += 2.0 * 128.0 * (double)n * (double)active_now;
+        }
+        if (hc[2] != 0) return fail(c, MARS_ETIMEOUT, "a tensor-core pipeline wait gave up");
+        if (hc[1] == 0) break;
+        if (done_sweeps > sweep_cap)
+            return fail(c, MARS_EDEVICE, "descent exceeded its sweep bound");
+        batch = std::min(batch * 2, 32);
+    }
+    MARS_CUDA(c, launch_tc_finalize(t, d, s, st));
+    return MARS_OK;
+}
+
 // Accessors for mars_noalloc.cu.
 int noalloc_view(mars_ctx* c, int32_t id, NoallocView* v)
 {
@@ -385,12 +550,31 @@ int mars_instance_dense(mars_ctx* c, int32_t n, const void* J, int32_t jt, const
         hd.resize(n);
         for (int32_t a = 0; a < n; ++a) { hf[a] = (float)hh[o[a]]; hd[a] = hh[o[a]]; }
     }
+    // Tensor-core operands: BF16 J padded to whole 128-spin panels, and the
+    // panels' FP32 diagonal blocks for the in-panel sequential updates.
+    const int32_t n_pad = (n + 127) / 128 * 128;
+    std::vector<uint16_t> Jb((size_t)n_pad * n_pad, 0);
+    std::vector<float> Jdiag((size_t)n_pad * 128, 0.f);
+    for (int32_t a = 0; a < n; ++a)
+        for (int32_t b = 0; b < n; ++b) {
+            const float v = Jf[(size_t)a * n + b];
+            Jb[(size_t)a * n_pad + b] = float_to_bf16_bits(v);
+            if (a / 128 == b / 128)
+                Jdiag[((size_t)(a / 128) * 128 + a % 128) * 128 + b % 128] = v;
+        }
     DevInstance& d = in->dev;
     d.n = n;
     d.dense = 1;
     d.nnz = (int64_t)n * (n - 1);
     d.nlev = n;
     d.integer = integer;
+    d.n_pad = n_pad;
+    {
+        const uint16_t* jb = nullptr;
+        if ((rc = upload(c, in.get(), Jb, &jb))) return rc;
+        d.Jbf = (const __nv_bfloat16*)jb;
+        if ((rc = upload(c, in.get(), Jdiag, &d.Jdiag))) return rc;
+    }
     if ((rc = upload(c, in.get(), Jf, &d.Jf))) return rc;
     if ((rc = upload(c, in.get(), Ji, &d.J_i8))) return rc;
     if ((rc = upload(c, in.get(), Jd, &d.J_f64))) return rc;
@@ -667,8 +851,10 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     if (p->k_max < 1 || p->fixed_sweeps < 0) return fail(c, MARS_EINVAL, "k_max >= 1, fixed_sweeps >= 0");
     if (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI)
         return fail(c, MARS_EINVAL, "unknown update rule %d", p->update);
-    if (p->precision != MARS_FP32)
-        return fail(c, MARS_EINVAL, "precision %d is not available for this instance", p->precision);
+    const bool tc = p->precision == MARS_BF16;
+    if (p->precision != MARS_FP32 && !(tc && in->dev.dense && p->update == MARS_UPDATE_GS))
+        return fail(c, MARS_EINVAL, "precision %d is not available for this instance and update rule",
+                    p->precision);
     if ((size_t)R * n > ((size_t)1 << 40)) return fail(c, MARS_EINVAL, "R*n too large");
     DeviceGuard g(c->device);
     cudaStream_t st = c->stream;
@@ -743,9 +929,11 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     SparsePlan sp;
     DensePlan dp;
     int rt = 1;
-    if (in->dev.dense) {
+    if (in->dev.dense && !tc) {
         dp = plan_dense(in->dev, R, s.jacobi, c->device);
         if (dp.scratch_floats && (rc = S.get(dp.scratch_floats, &s.m_scratch))) return rc;
+    } else if (tc) {
+        rt = 1;
     } else {
         if (s.jacobi || !plan_sparse_sell(in->dev, R, c->device, &sp))
             sp = plan_sparse(in->dev, R, s.jacobi, c->device);
@@ -771,8 +959,12 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     s.tile_rep = dtile;
     s.ntiles = ntiles;
     s.rt = rt;
+    TcProfile tcprof;
     MARS_CUDA(c, cudaEventRecord(c->ev0, st));
-    if (in->dev.dense) {
+    if (tc) {
+        const float t0_max = *std::max_element(t0h.begin(), t0h.end());
+        if ((rc = run_dense_tc(c, in, p, s, reps, t0_max, S, &tcprof))) return rc;
+    } else if (in->dev.dense) {
         MARS_CUDA(c, launch_dense(in->dev, s, dp, st));
     } else {
         if (sp.sell)
@@ -819,6 +1011,9 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
         result->capped_levels = hres.capped;
         result->gpu_seconds = ms * 1e-3;
         result->descent_seconds = ms_descent * 1e-3;
+        result->gemm_seconds = tcprof.gemm_seconds;
+        result->gemm_launches = tcprof.gemm_launches;
+        result->gemm_flops = tcprof.gemm_flops;
         result->integer = in->dev.integer;
         result->energy_err_bound =
             in->dev.integer ? 0.0 : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + n);

@@ -59,7 +59,9 @@ class Result(ctypes.Structure):
                 ("levels", ctypes.c_int64), ("capped_levels", ctypes.c_int64),
                 ("gpu_seconds", ctypes.c_double), ("descent_seconds", ctypes.c_double),
                 ("energy_err_bound", ctypes.c_double),
-                ("status", ctypes.c_int32), ("integer", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("integer", ctypes.c_int32),
+                ("gemm_seconds", ctypes.c_double), ("gemm_launches", ctypes.c_int64),
+                ("gemm_flops", ctypes.c_double)]
 
 
 class InstanceInfo(ctypes.Structure):
@@ -159,6 +161,9 @@ class SolveResult:
     energy_err_bound: float
     integer: bool
     best_spins: np.ndarray
+    gemm_seconds: float = 0.0
+    gemm_launches: int = 0
+    gemm_flops: float = 0.0
     energies: np.ndarray | None = None
     spins: np.ndarray | None = None
     m_final: np.ndarray | None = None
@@ -319,6 +324,8 @@ class Context:
             levels=res.levels, capped_levels=res.capped_levels, gpu_seconds=res.gpu_seconds,
             descent_seconds=res.descent_seconds,
             energy_err_bound=res.energy_err_bound, integer=bool(res.integer), best_spins=best,
+            gemm_seconds=res.gemm_seconds, gemm_launches=res.gemm_launches,
+            gemm_flops=res.gemm_flops,
             energies=keep.get("energies"), spins=keep.get("spins"), m_final=keep.get("m_final"),
             t0=keep.get("t0"), replica_sweeps=keep.get("sweeps"),
             replica_levels=keep.get("levels"), replica_capped=keep.get("capped"))

@@ -1,0 +1,142 @@
+"""Dense tensor-core path (precision BF16) against the FP64 oracle.
+
+The BF16 path computes each 128-spin panel's fields with a tcgen05 GEMM over
+BF16 copies of J and of the magnetisations, then updates the panel's spins in
+sequence in FP32. Two kinds of checks:
+
+* exact structure: with J block-diagonal in 128-spin blocks (+-1 inside) and
+  start states exactly representable in BF16, every panel's GEMM sees only
+  BF16-exact inputs, so one sweep must equal the sequential FP64 sweep to FP32
+  rounding (max-abs 1e-5). A wrong TMA coordinate, descriptor, swizzle or
+  split-K reduction breaks this.
+* full instances: BF16 rounding of updated spins moves trajectories, so the
+  bar is the method's outcome: every returned energy is the exact energy of
+  the returned spins, and the energy distribution matches the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1907_05124_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_05124_gb300 import build, mars
+    build.build()
+    c = mars.Context(0)
+    yield c
+    c.close()
+
+
+def block_diagonal_pm1(n, seed, block=128):
+    rng = np.random.default_rng(seed)
+    J = np.zeros((n, n))
+    for b0 in range(0, n, block):
+        b1 = min(n, b0 + block)
+        k = b1 - b0
+        u = np.triu(rng.choice(np.array([-1.0, 1.0]), size=(k, k)), 1)
+        J[b0:b1, b0:b1] = u + u.T
+    return J
+
+
+def bf16_exact_m0(R, n, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.integers(-128, 129, size=(R, n)) / 128.0).astype(np.float32)
+
+
+def _sensitivity(inst, m0, t0, **kw):
+    rng = np.random.default_rng(99)
+    bumped = np.nextafter(m0, np.where(rng.random(m0.shape) < 0.5, -2.0, 2.0).astype(np.float32))
+    a = O.mars_solve(inst, m0, t0, **kw)["m"]
+    b = O.mars_solve(inst, bumped, t0, **kw)["m"]
+    return float(np.abs(a - b).max())
+
+
+@pytest.mark.parametrize("regime", ["contracting", "saturated"])
+@pytest.mark.parametrize("n,R,with_h", [(512, 200, False), (320, 130, True), (128, 64, False),
+                                         (1024, 300, False)])
+def test_block_diagonal_sweep(ctx, n, R, with_h, regime):
+    """One sweep over block-diagonal +-1 J with BF16-exact start states.
+
+    contracting: one level at T in [24, 28), above the blocks' spectral edge
+    (about 2 sqrt(128) = 22.6), where the sequential map contracts and an ideal
+    FP32 sweep stays within 1e-7 of FP64: the bar is the strict 1e-5.
+    saturated: T in [0.5, 1), where rounding is amplified along the 128-spin
+    chain (an ideal FP32 sweep already differs by ~5e-5); the bar is 1e-5 plus
+    50 times the oracle's own change under a one-ulp perturbation of m0.
+    """
+    J = block_diagonal_pm1(n, n)
+    h = np.random.default_rng(1).integers(-2, 3, size=n).astype(np.float64) if with_h else None
+    inst = ctx.add_dense(J, h=h)
+    m0 = bf16_exact_m0(R, n, 3)
+    rng = np.random.default_rng(4)
+    if regime == "contracting":
+        c, t0 = 30.0, rng.uniform(54.0, 58.0, size=R).astype(np.float32)
+    else:
+        c, t0 = 1.0, rng.uniform(1.5, 2.0, size=R).astype(np.float32)
+    g = ctx.solve(inst, R, float(t0.min()), float(t0.max()), c_step=c, fixed_sweeps=1, m0=m0,
+                  t0=t0, precision="bf16", outputs=("m_final", "energies", "spins", "sweeps"))
+    oi = O.Instance.dense(J, h)
+    o = O.mars_solve(oi, m0, t0, c_step=c, fixed_sweeps=1)
+    err = np.abs(g.m_final - o["m"]).max()
+    if regime == "contracting":
+        assert err <= 1e-5, err
+    else:
+        delta = _sensitivity(oi, m0, t0, c_step=c, fixed_sweeps=1)
+        assert err <= 1e-5 + 50 * delta, (err, delta)
+    assert np.array_equal(g.replica_sweeps, o["sweeps"])
+    assert np.array_equal(g.energies, O.energies(oi, g.spins))
+    ctx.free(inst)
+
+
+def test_sk_pm1_energies_exact_and_distribution(ctx):
+    from scipy import stats
+    n, R = 256, 384
+    J = I.sk_pm1(n, 7)
+    inst = ctx.add_dense(J)
+    m0, t0 = I.replica_inputs(R, n, 0.0, 32.0, 8)
+    g = ctx.solve(inst, R, 0.0, 32.0, m0=m0, t0=t0, precision="bf16",
+                  outputs=("energies", "spins", "sweeps"))
+    oi = O.Instance.dense(J)
+    assert np.array_equal(g.energies, O.energies(oi, g.spins))
+    assert g.best_energy == O.energy(oi, g.best_spins)
+    o = O.mars_solve(oi, m0, t0, nthreads=8, want_m=False)
+    assert stats.ks_2samp(g.energies, o["energy"]).pvalue > 0.01
+    # same quality: best energies within 1 % of each other
+    assert abs(g.best_energy - o["energy"].min()) <= 0.01 * abs(o["energy"].min())
+    ctx.free(inst)
+
+
+def test_sk_gaussian_energies(ctx):
+    n, R = 384, 96
+    J = I.sk_gauss(n, 5)
+    inst = ctx.add_dense(J)
+    c = float(1.0 / np.sqrt(n))
+    m0, t0 = I.replica_inputs(R, n, 0.0, 2.0, 6)
+    g = ctx.solve(inst, R, 0.0, 2.0, c_step=c, fixed_sweeps=2, m0=m0, t0=t0, precision="bf16",
+                  outputs=("energies", "spins", "levels"))
+    oi = O.Instance.dense(J)
+    ref = O.energies(oi, g.spins)
+    np.testing.assert_allclose(g.energies, ref, rtol=0, atol=1e-12 * np.abs(J).sum())
+    o = O.mars_solve(oi, m0, t0, c_step=c, fixed_sweeps=2, nthreads=8, want_m=False)
+    assert np.array_equal(g.replica_levels, o["levels"])
+    assert abs(g.best_energy - o["energy"].min()) <= 0.02 * abs(o["energy"].min())
+    ctx.free(inst)
+
+
+def test_bf16_rejected_where_not_available(ctx):
+    from paper_1907_05124_gb300.mars import MarsError
+    inst = ctx.add_csr(*I.ea_lattice(8, 2, 0))
+    with pytest.raises(MarsError):
+        ctx.solve(inst, 4, 0.0, 4.0, precision="bf16")
+    ctx.free(inst)
+    dinst = ctx.add_dense(I.sk_pm1(64, 0))
+    with pytest.raises(MarsError):
+        ctx.solve(dinst, 4, 0.0, 4.0, precision="bf16", update="jacobi")
+    ctx.free(dinst)
