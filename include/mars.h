@@ -227,6 +227,50 @@ int mars_solve(mars_ctx* ctx, int32_t inst, const mars_params* params, int8_t* b
                const mars_outputs* outputs, mars_result* result);
 
 /*
+ * Several solves in one persistent launch (the batch of Section 3's
+ * independent simulations, across instances). Job j solves CSR instance
+ * insts[j] with params[j] (sequential FP32 sweeps); results[j] and, when
+ * best_spins and best_spins[j] are non-NULL, best_spins[j] (n_j int8, host)
+ * receive what mars_solve would return: every replica's result is the same
+ * as in a separate mars_solve with the same parameters. Instances of uneven
+ * size and replica count share the SMs: CTAs drain one instance's replica
+ * queue after another. gpu_seconds and descent_seconds of every result time
+ * the whole batch. Errors: as mars_solve, plus MARS_EINVAL for a dense
+ * instance or one too large for the on-chip kernel.
+ */
+int mars_solve_batch(mars_ctx* ctx, int32_t count, const int32_t* insts, const mars_params* params,
+                     int8_t* const* best_spins, mars_result* results);
+
+/*
+ * Serving. Requests are solves queued with mars_submit and collected with
+ * mars_poll; each mars_submit / mars_poll call advances the engine. Queued
+ * requests are admitted in arrival order whenever an in-flight slot is free
+ * (mars_serve_limits, default 8) and the context's HBM budget holds the
+ * request's buffers; each admitted request runs on its own CUDA stream, so
+ * requests that arrive while others are on the GPU start as soon as slots
+ * and memory free up and their kernels overlap on the device. A request's
+ * result is the same as mars_solve's with the same parameters, except that
+ * replicas run in index order (the per-replica results are identical).
+ * m0/t0 must be device pointers (MARS_DEVICE_PTR) or NULL; the instance must
+ * stay registered until the request is collected.
+ */
+int mars_serve_limits(mars_ctx* ctx, int32_t max_inflight);
+
+/* Queue a solve; *req receives its id. Errors: as mars_solve's parameter checks. */
+int mars_submit(mars_ctx* ctx, int32_t inst, const mars_params* params, int64_t* req);
+
+/*
+ * MARS_OK with the request's best spins (n int8, host, nullable) and result
+ * (nullable) once it is done (the request is then forgotten); MARS_EAGAIN
+ * while it is queued or running; the request's error if it failed;
+ * MARS_ENOTFOUND for an unknown id.
+ */
+int mars_poll(mars_ctx* ctx, int64_t req, int8_t* best_spins, mars_result* result);
+
+/* Numbers of queued and running requests (after advancing the engine). */
+int mars_serve_status(mars_ctx* ctx, int32_t* queued, int32_t* running);
+
+/*
  * Exact energies (Section 2, Eq. 2, pairs once) of count spin vectors
  * (count*n int8, entries +-1, caller labels). e (count doubles) receives the
  * energy rounded once to the nearest double; e_i64 (nullable) receives it as

@@ -137,8 +137,9 @@ __global__ void __launch_bounds__(128, 1)
 
 // Compensated accumulate: (s, c) += a * b with the product's and the sum's
 // rounding errors carried in c (TwoProduct by FMA, TwoSum; Ogita, Rump,
-// Oishi 2005). Keeps each field within a few FP32 ulps of exact after the
-// up to 127 in-panel corrections a spin receives.
+// Oishi 2005). Used where a panel's field is assembled from its split-K
+// partial sums and the field h. The in-panel corrections use plain FMAs:
+// beside a BF16 GEMM their FP32 rounding is immaterial.
 __device__ __forceinline__ void acc2(float& s, float& c, float a, float b)
 {
     const float p = __fmul_rn(a, b);
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t
             const int a = qa * 32 + l;
             float delta = 0.f;
             if (lane == l) {
-                const float sn = -tanh_sfu(__fadd_rn(g[qa], gc[qa]) * invT);
+                const float sn = -tanh_sfu((g[qa] + gc[qa]) * invT);
                 dloc = fmaxf(dloc, fabsf(sn - so_f[qa]));
                 delta = sn - so_b[qa];
                 sf[qa] = sn;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t
 #pragma unroll
             for (int q = qa; q < 4; ++q) {
                 const int k = lane + 32 * q;
-                if (k > a) acc2(g[q], gc[q], Jrow[k], delta);
+                if (k > a) g[q] = fmaf(Jrow[k], delta, g[q]);
             }
         }
     }

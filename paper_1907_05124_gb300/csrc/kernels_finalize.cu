@@ -5,6 +5,7 @@
 // replicas that reach it, as the paper's success probability P does
 // (Section 4.2). Energies are Eq. 2 with each pair counted once.
 #include "device_common.cuh"
+#include "exact_sum.cuh"
 #include "mars_internal.h"
 
 #include <cfloat>
@@ -108,17 +109,23 @@ __global__ void __launch_bounds__(kBestThreads) best_kernel(DevSolve s, int32_t 
 
 constexpr int kEnergyThreads = 256;
 
+// Energies of spin vectors, one CTA per vector. Integer couplings sum exactly
+// in int64; other couplings sum exactly in an ExactAcc and are rounded once.
 __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(DevInstance in, const int8_t* spins,
                                                                 double* e, long long* e_i64,
                                                                 int32_t* status)
 {
     __shared__ long long s_i[kEnergyThreads / 32];
     __shared__ double s_f[kEnergyThreads / 32];
+    __shared__ long long s_x[kEnergyThreads / 32][kExactLimbs];
     const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = in.n;
     const int8_t* sp = spins + (size_t)c * n;
     long long ei = 0;
-    double ef = 0.0;
+    double ef = 0.0;  // plain FP64 sum when the instance's span exceeds the accumulator
+    const bool exact = in.exact_ok != 0;
+    ExactAcc ex;
+    ex.clear();
     for (int a = tid; a < n; a += kEnergyThreads) {
         const int sa = sp[__ldg(in.new2old + a)];
         if (sa != 1 && sa != -1) { atomicExch(status, (int)kDevBadIndex); continue; }
@@ -130,9 +137,10 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(DevInstance in, 
                 ei += acc * sa;
             } else {
                 const double* row = in.J_f64 + (size_t)a * n;
-                double acc = 0.0;
-                for (int b = a + 1; b < n; ++b) acc += row[b] * (double)sp[__ldg(in.new2old + b)];
-                ef += acc * sa;
+                for (int b = a + 1; b < n; ++b) {
+                    const double w = sa * sp[__ldg(in.new2old + b)] > 0 ? row[b] : -row[b];
+                    if (exact) ex.add(w, in.exact_e0); else ef += w;
+                }
             }
         } else {
             const int e0 = __ldg(in.row_ptr + a), e1 = __ldg(in.row_ptr + a + 1);
@@ -144,34 +152,69 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(DevInstance in, 
                 }
                 ei += acc * sa;
             } else {
-                double acc = 0.0;
                 for (int q = e0; q < e1; ++q) {
                     const int b = __ldg(in.col + q);
-                    if (b > a) acc += __ldg(in.val_f64 + q) * (double)sp[__ldg(in.new2old + b)];
+                    if (b <= a) continue;
+                    const double v = __ldg(in.val_f64 + q);
+                    const double w = sa * sp[__ldg(in.new2old + b)] > 0 ? v : -v;
+                    if (exact) ex.add(w, in.exact_e0); else ef += w;
                 }
-                ef += acc * sa;
             }
         }
         if (in.integer) {
             if (in.h) ei += (long long)__ldg(in.h + a) * sa;
         } else if (in.h_f64) {
-            ef += __ldg(in.h_f64 + a) * sa;
+            const double hv = sa > 0 ? __ldg(in.h_f64 + a) : -__ldg(in.h_f64 + a);
+            if (exact) ex.add(hv, in.exact_e0); else ef += hv;
         }
     }
     ei = warp_reduce_strided<1>(ei, SumOp());
     ef = warp_reduce_strided<1>(ef, SumOp());
-    if (lane == 0) { s_i[warp] = ei; s_f[warp] = ef; }
+    ex.normalize();  // limbs small enough that 256 of them sum without overflow
+#pragma unroll
+    for (int l = 0; l < kExactLimbs; ++l) ex.d[l] = warp_reduce_strided<1>(ex.d[l], SumOp());
+    if (lane == 0) {
+        s_i[warp] = ei;
+        s_f[warp] = ef;
+#pragma unroll
+        for (int l = 0; l < kExactLimbs; ++l) s_x[warp][l] = ex.d[l];
+    }
     __syncthreads();
     if (tid == 0) {
         long long ti = 0;
         double tf = 0.0;
-        for (int w = 0; w < kEnergyThreads / 32; ++w) { ti += s_i[w]; tf += s_f[w]; }
-        e[c] = in.integer ? (double)ti : tf;
+        ExactAcc tot;
+        tot.clear();
+        for (int w = 0; w < kEnergyThreads / 32; ++w) {
+            ti += s_i[w];
+            tf += s_f[w];
+#pragma unroll
+            for (int l = 0; l < kExactLimbs; ++l) tot.d[l] += s_x[w][l];
+        }
+        e[c] = in.integer ? (double)ti : exact ? tot.round(in.exact_e0) : tf;
         if (e_i64) e_i64[c] = in.integer ? ti : 0;
     }
 }
 
+// Replica queue in index order (entries past R empty), counters at zero.
+__global__ void queue_identity_kernel(int32_t* q, int32_t total, int32_t R, int32_t* counters)
+{
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+        q[i] = i < R ? i : -1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        counters[0] = 0;
+        counters[1] = 0;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_queue_identity(int32_t* q, int32_t total, int32_t R, int32_t* counters,
+                                  cudaStream_t st)
+{
+    queue_identity_kernel<<<(total + 255) / 256, 256, 0, st>>>(q, total, R, counters);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_draw(uint64_t seed, uint32_t stream, int32_t r0, int32_t R, int32_t n,
                         double t_min, double t_max, float* m0, float* t0, cudaStream_t st)

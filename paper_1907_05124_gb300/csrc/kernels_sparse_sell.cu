@@ -79,11 +79,13 @@ struct Vec<4> {
     }
 };
 
-// One coupling: (column, weight). PM1 entries pack the sign in bit 31.
-template <bool PM1>
+// One coupling: (column, weight). Format 0: (column, float bits) pairs;
+// format 1: +-1 words, column | sign << 31; format 2: +-1 halfwords,
+// column | sign << 15, staged in shared memory for the whole kernel.
+template <int FMT>
 struct Entry;
 template <>
-struct Entry<true> {
+struct Entry<1> {
     const uint32_t* e;
     __device__ void get(int idx, int& col, float& w) const
     {
@@ -93,7 +95,7 @@ struct Entry<true> {
     }
 };
 template <>
-struct Entry<false> {
+struct Entry<0> {
     const int2* e;
     __device__ void get(int idx, int& col, float& w) const
     {
@@ -102,26 +104,71 @@ struct Entry<false> {
         w = __int_as_float(v.y);
     }
 };
+template <>
+struct Entry<2> {
+    const uint16_t* e;  // shared memory
+    __device__ void get(int idx, int& col, float& w) const
+    {
+        const uint32_t v = e[idx];
+        col = (int)(v & 0x7fffu);
+        w = (v >> 15) ? -1.f : 1.f;
+    }
+};
 
-template <int RT, int NT, bool PM1>
-__global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance in, DevSolve s)
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Per-CTA bookkeeping of the RT replica slots, in shared memory.
+template <int RT, int NW>
+struct SlotState {
+    double T[RT];
+    float invT[RT];
+    int rep[RT], fresh[RT], done[RT];
+    int lvl_sweeps[RT], sweeps[RT], levels[RT], capped[RT], active[RT];
+    float dred[NW][RT];
+    long long ei[NW][RT];
+    double ef[NW][RT];
+};
+
+// Run one instance's replica queue on this CTA until the queue is empty and
+// every slot has drained. Called by the whole CTA (it contains barriers).
+template <int RT, int NT, int FMT, int DEG = 0>
+__device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, SlotState<RT, NT / 32>& S)
 {
     constexpr int kThreads = NT;
     constexpr int kWarps = NT / 32;
     using V = Vec<RT>;
-    extern __shared__ __align__(16) float m[];  // (n+1)*RT
-    __shared__ double s_T[RT];
-    __shared__ float s_invT[RT];
-    __shared__ int s_rep[RT], s_fresh[RT], s_done[RT];
-    __shared__ int s_lvl_sweeps[RT], s_sweeps[RT], s_levels[RT], s_capped[RT], s_active[RT];
-    __shared__ float s_dred[kWarps][RT];
-    __shared__ long long s_ei[kWarps][RT];
-    __shared__ double s_ef[kWarps][RT];
+    double* const s_T = S.T;
+    float* const s_invT = S.invT;
+    int* const s_rep = S.rep;
+    int* const s_fresh = S.fresh;
+    int* const s_done = S.done;
+    int* const s_lvl_sweeps = S.lvl_sweeps;
+    int* const s_sweeps = S.sweeps;
+    int* const s_levels = S.levels;
+    int* const s_capped = S.capped;
+    int* const s_active = S.active;
+    auto& s_dred = S.dred;
+    auto& s_ei = S.ei;
+    auto& s_ef = S.ef;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = in.n;
-    Entry<PM1> ent;
-    if constexpr (PM1) ent.e = in.sell_pm1; else ent.e = in.sell_gen;
+    Entry<FMT> ent;
+    const int4* slices = in.slices;
+    if constexpr (FMT == 0) ent.e = in.sell_gen;
+    if constexpr (FMT == 1) ent.e = in.sell_pm1;
+    if constexpr (FMT == 2) {
+        // Stage the slice table and the halfword couplings in shared memory,
+        // after the magnetisations; they serve every replica this CTA runs.
+        unsigned char* base = reinterpret_cast<unsigned char*>(m);
+        int4* ss = reinterpret_cast<int4*>(base + align16((size_t)(n + 1) * RT * sizeof(float)));
+        uint16_t* se = reinterpret_cast<uint16_t*>(ss + in.nslices);
+        for (int q = tid; q < in.nslices; q += kThreads) ss[q] = __ldg(in.slices + q);
+        for (int64_t q = tid; q < in.sell_len; q += kThreads) se[q] = __ldg(in.sell16 + q);
+        slices = ss;
+        ent.e = se;
+        __syncthreads();
+    }
 
     // Each of the RT slots takes replicas from the queue s.tile_rep[0..R) (longest
     // start temperatures first) until it is empty: when a slot's replica ends,
@@ -278,7 +325,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance 
         for (int l = 0; l < in.nlev; ++l) {
             const int s0 = __ldg(in.lvl_slice + l), s1 = __ldg(in.lvl_slice + l + 1);
             for (int sl = s0 + warp; sl < s1; sl += kWarps) {
-                const int4 d = __ldg(in.slices + sl);  // row0, rows, degree, offset
+                const int4 d = FMT == 2 ? slices[sl] : __ldg(in.slices + sl);  // row0, rows, degree, offset
                 if (lane >= d.y) continue;
                 const int i = d.x + lane;
                 const float hv = in.h ? __ldg(in.h + i) : 0.f;
@@ -286,8 +333,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance 
                     typename V::T acc;
 #pragma unroll
                     for (int k = 0; k < RT; ++k) V::set(acc, k, 0.f);
+                    const int deg = DEG > 0 ? DEG : d.z;  // a regular instance's degree is known
 #pragma unroll 4
-                    for (int q = 0; q < d.z; ++q) {
+                    for (int q = 0; q < deg; ++q) {
                         int c;
                         float w;
                         ent.get(d.w + 32 * q + lane, c, w);
@@ -314,8 +362,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance 
                     for (int k = 0; k < RT; ++k) {
                         if (!((live >> k) & 1)) continue;
                         float acc = 0.f;
+                        const int deg = DEG > 0 ? DEG : d.z;
 #pragma unroll 4
-                        for (int q = 0; q < d.z; ++q) {
+                        for (int q = 0; q < deg; ++q) {
                             int c;
                             float w;
                             ent.get(d.w + 32 * q + lane, c, w);
@@ -363,25 +412,85 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance 
     }
 }
 
-template <int RT, int NT>
-const void* pick_nt(bool pm1)
+template <int RT, int NT, int FMT, int DEG>
+__global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance in, DevSolve s)
 {
-    return pm1 ? (const void*)sparse_sell_kernel<RT, NT, true> : (const void*)sparse_sell_kernel<RT, NT, false>;
+    extern __shared__ __align__(16) float m[];  // (n+1)*RT, then the staged table (FMT 2)
+    __shared__ SlotState<RT, NT / 32> S;
+    run_job<RT, NT, FMT, DEG>(in, s, m, S);
 }
 
-const void* pick(int rt, int nt, bool pm1)
+// Several instances in one persistent launch: CTAs work through the job list
+// in order, each draining one instance's replica queue before it moves on, so
+// instances of uneven size and replica count share the SMs without a launch
+// per instance. The coupling format is chosen per job.
+template <int RT, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_batch_kernel(const BatchJob* jobs, int njobs,
+                                                                       int* cursor)
 {
+    extern __shared__ __align__(16) float m[];
+    __shared__ SlotState<RT, NT / 32> S;
+    __shared__ BatchJob s_jobcopy;  // the current job's descriptors, read from shared memory
+    __shared__ int s_job;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int j = *((volatile int*)cursor);
+            while (j < njobs && *((volatile int*)jobs[j].s.work_counter) >= jobs[j].s.R) {
+                atomicMax(cursor, j + 1);
+                ++j;
+            }
+            s_job = j < njobs ? j : -1;
+        }
+        __syncthreads();
+        const int j = s_job;
+        if (j < 0) break;
+        {
+            const int* src = reinterpret_cast<const int*>(jobs + j);
+            int* dst = reinterpret_cast<int*>(&s_jobcopy);
+            for (int w = threadIdx.x; w < (int)(sizeof(BatchJob) / sizeof(int)); w += blockDim.x)
+                dst[w] = src[w];
+        }
+        __syncthreads();
+        const BatchJob& job = s_jobcopy;
+        switch (job.fmt) {
+        case 2: run_job<RT, NT, 2>(job.in, job.s, m, S); break;
+        case 1: run_job<RT, NT, 1>(job.in, job.s, m, S); break;
+        default: run_job<RT, NT, 0>(job.in, job.s, m, S); break;
+        }
+        __syncthreads();
+    }
+}
+
+template <int RT, int NT, int DEG>
+const void* pick_nt(int fmt)
+{
+    return fmt == 2 ? (const void*)sparse_sell_kernel<RT, NT, 2, DEG>
+         : fmt == 1 ? (const void*)sparse_sell_kernel<RT, NT, 1, DEG>
+                    : (const void*)sparse_sell_kernel<RT, NT, 0, DEG>;
+}
+
+// Regular instances of degree 4 or 6 (square and cubic lattices) get a fully
+// unrolled coupling loop in the default 1024-thread shapes.
+const void* pick(int rt, int nt, int fmt, int deg)
+{
+    if (nt == 1024 && (deg == 4 || deg == 6) && fmt != 0) {
+        switch (rt) {
+        case 1: return deg == 4 ? pick_nt<1, 1024, 4>(fmt) : pick_nt<1, 1024, 6>(fmt);
+        case 2: return deg == 4 ? pick_nt<2, 1024, 4>(fmt) : pick_nt<2, 1024, 6>(fmt);
+        case 4: return deg == 4 ? pick_nt<4, 1024, 4>(fmt) : pick_nt<4, 1024, 6>(fmt);
+        }
+    }
     if (nt == 512) {
         switch (rt) {
-        case 1: return pick_nt<1, 512>(pm1);
-        case 2: return pick_nt<2, 512>(pm1);
-        case 4: return pick_nt<4, 512>(pm1);
+        case 1: return pick_nt<1, 512, 0>(fmt);
+        case 2: return pick_nt<2, 512, 0>(fmt);
+        case 4: return pick_nt<4, 512, 0>(fmt);
         }
     } else if (nt == 1024) {
         switch (rt) {
-        case 1: return pick_nt<1, 1024>(pm1);
-        case 2: return pick_nt<2, 1024>(pm1);
-        case 4: return pick_nt<4, 1024>(pm1);
+        case 1: return pick_nt<1, 1024, 0>(fmt);
+        case 2: return pick_nt<2, 1024, 0>(fmt);
+        case 4: return pick_nt<4, 1024, 0>(fmt);
         }
     }
     return nullptr;
@@ -412,14 +521,31 @@ bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p)
     int nt = env_int("MARS_SELL_THREADS", 1024);
     if (rt != 1 && rt != 2 && rt != 4) rt = 1;
     if (nt != 512 && nt != 1024) nt = 512;
-    while (rt > 1 && (size_t)(in.n + 1) * rt * sizeof(float) > budget) rt /= 2;
-    if ((size_t)(in.n + 1) * rt * sizeof(float) > budget) return false;
+    auto m_bytes = [&](int c) { return align16((size_t)(in.n + 1) * c * sizeof(float)); };
+    const size_t table = (size_t)in.nslices * 16 + (size_t)in.sell_len * 2;
+    // Halfword couplings staged on chip when they fit beside the magnetisations.
+    int fmt = in.sell_pm1 ? 1 : 0;
+    if (in.sell16 && env_int("MARS_SELL_SMEM_TABLE", 1)) {
+        int c = rt;
+        while (c > 1 && m_bytes(c) + table > budget) c /= 2;
+        if (m_bytes(c) + table <= budget) {
+            fmt = 2;
+            rt = c;
+        }
+    }
+    if (fmt != 2) {
+        while (rt > 1 && m_bytes(rt) > budget) rt /= 2;
+        if (m_bytes(rt) > budget) return false;
+    }
     p->rt = rt;
     p->onchip = 1;
     p->threads = nt;
-    p->smem = (size_t)(in.n + 1) * rt * sizeof(float);
+    p->entry = fmt;
+    p->smem = m_bytes(rt) + (fmt == 2 ? table : 0);
     p->sell = 1;
-    const void* k = pick(rt, nt, in.sell_pm1 != nullptr);
+    const int deg = env_int("MARS_SELL_UNROLL", 1) ? in.regular_deg : 0;
+    p->deg = deg;
+    const void* k = pick(rt, nt, fmt, deg);
     if (!k) return false;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     int per_sm = 1;
@@ -434,13 +560,74 @@ bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p)
 cudaError_t launch_sparse_sell(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
                                cudaStream_t st)
 {
-    const void* k = pick(p.rt, p.threads, in.sell_pm1 != nullptr);
+    const void* k = pick(p.rt, p.threads, p.entry, p.deg);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     DevInstance a = in;
     DevSolve b = s;
     void* args[] = {&a, &b};
+    return cudaLaunchKernel(k, dim3(p.grid), dim3(p.threads), args, p.smem, st);
+}
+
+namespace {
+template <int RT>
+const void* pick_batch(int nt)
+{
+    return nt == 1024 ? (const void*)sparse_sell_batch_kernel<RT, 1024>
+                      : (const void*)sparse_sell_batch_kernel<RT, 512>;
+}
+}  // namespace
+
+// Shared launch shape of a batch: one slot width for every job (the widest
+// that fits the largest instance), per-job coupling format, and the shared
+// memory of the most demanding job.
+bool plan_sparse_batch(const DevInstance* ins, int count, int device, BatchPlan* p, int* fmts)
+{
+    int sms = 1, optin = 48 * 1024;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    const size_t budget = (size_t)optin - 16 * 1024;
+    int nmax = 0;
+    for (int j = 0; j < count; ++j) {
+        if (ins[j].dense || !ins[j].slices || (!ins[j].sell_pm1 && !ins[j].sell_gen)) return false;
+        nmax = std::max(nmax, ins[j].n);
+    }
+    int rt = env_int("MARS_SELL_RT", 2);
+    int nt = env_int("MARS_SELL_THREADS", 1024);
+    if (rt != 1 && rt != 2) rt = 1;
+    if (nt != 512 && nt != 1024) nt = 1024;
+    auto m_bytes = [&](int n, int c) { return align16((size_t)(n + 1) * c * sizeof(float)); };
+    while (rt > 1 && m_bytes(nmax, rt) > budget) rt /= 2;
+    if (m_bytes(nmax, rt) > budget) return false;
+    size_t smem = 0;
+    for (int j = 0; j < count; ++j) {
+        const DevInstance& in = ins[j];
+        const size_t table = (size_t)in.nslices * 16 + (size_t)in.sell_len * 2;
+        int fmt = in.sell_pm1 ? 1 : 0;
+        if (in.sell16 && env_int("MARS_SELL_SMEM_TABLE", 1) && m_bytes(in.n, rt) + table <= budget) fmt = 2;
+        fmts[j] = fmt;
+        smem = std::max(smem, m_bytes(in.n, rt) + (fmt == 2 ? table : 0));
+    }
+    p->rt = rt;
+    p->threads = nt;
+    p->smem = smem;
+    const void* k = pick_batch<1>(nt);
+    if (rt == 2) k = pick_batch<2>(nt);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem);
+    p->grid = sms * std::max(per_sm, 1);
+    return true;
+}
+
+cudaError_t launch_sparse_batch(const BatchJob* jobs, int count, int* cursor, const BatchPlan& p,
+                                cudaStream_t st)
+{
+    const void* k = p.rt == 2 ? pick_batch<2>(p.threads) : pick_batch<1>(p.threads);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&jobs, (void*)&count, (void*)&cursor};
     return cudaLaunchKernel(k, dim3(p.grid), dim3(p.threads), args, p.smem, st);
 }
 

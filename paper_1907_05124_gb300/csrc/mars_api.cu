@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <numeric>
@@ -41,7 +42,11 @@ struct Instance {
 
 }  // namespace
 
+struct Serve;  // the serving engine's request table (below)
+void serve_release(mars_ctx* c);
+
 struct mars_ctx {
+    std::unique_ptr<Serve, void (*)(Serve*)> serve{nullptr, nullptr};
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -111,6 +116,35 @@ int dev_alloc(mars_ctx* c, size_t bytes, DevMem* out)
     out->bytes = bytes;
     c->used += bytes;
     return MARS_OK;
+}
+
+int dev_alloc_on(mars_ctx* c, size_t bytes, DevMem* out, cudaStream_t st)
+{
+    out->p = nullptr;
+    out->bytes = 0;
+    if (bytes == 0) return MARS_OK;
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(c, MARS_ENOMEM, "HBM budget exceeded: %zu + %zu > %zu bytes", c->used, bytes,
+                    c->budget);
+    cudaError_t e = cudaMallocAsync(&out->p, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MARS_ENOMEM, "device allocation of %zu bytes failed: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    out->bytes = bytes;
+    c->used += bytes;
+    return MARS_OK;
+}
+
+void dev_free_on(mars_ctx* c, DevMem* m, cudaStream_t st)
+{
+    if (m->p) {
+        cudaFreeAsync(m->p, st);
+        c->used -= m->bytes;
+    }
+    m->p = nullptr;
+    m->bytes = 0;
 }
 
 void dev_free(mars_ctx* c, DevMem* m)
@@ -218,6 +252,29 @@ int check_order(mars_ctx* c, const int32_t* order, int32_t n, std::vector<int32_
 
 bool is_small_int(double v, double lim) { return v == std::floor(v) && std::fabs(v) <= lim; }
 
+// Span of the exact energy accumulator (exact_sum.cuh): e0 is the weight of
+// the last mantissa bit of the smallest non-zero term; the sum of `terms`
+// terms of at most max|v| must stay below 2^(e0 + 220).
+void exact_span(const std::vector<double>& vals, const std::vector<double>& h, int64_t terms,
+                DevInstance* d)
+{
+    int lo = INT32_MAX, hi = INT32_MIN;
+    auto visit = [&](double v) {
+        if (v == 0.0) return;
+        int e;
+        std::frexp(std::fabs(v), &e);   // |v| = f 2^e, 0.5 <= f < 1
+        lo = std::min(lo, e - 53);       // weight of the last mantissa bit
+        hi = std::max(hi, e);            // |v| < 2^e
+    };
+    for (double v : vals) visit(v);
+    for (double v : h) visit(v);
+    if (lo == INT32_MAX) { d->exact_ok = 1; d->exact_e0 = 0; return; }
+    int grow = 0;
+    while ((int64_t)1 << grow < terms + 1 && grow < 62) ++grow;
+    d->exact_e0 = lo;
+    d->exact_ok = (hi + grow - lo) <= 220 && lo >= -1126;
+}
+
 int finish_register(mars_ctx* c, std::unique_ptr<Instance> in, int32_t* inst)
 {
     in->info.device_bytes = 0;
@@ -298,21 +355,48 @@ struct TcProfile {
     int64_t gemm_launches = 0;
 };
 
-int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve& s,
-                 const std::vector<int32_t>& reps, float t0_max, Scratch& S, TcProfile* prof)
+// One dense tensor-core descent in flight: its device state, tensor maps and
+// the host's view of progress. run_dense_tc drives it to the end; the serving
+// engine steps it one batch of sweeps at a time.
+struct TcRun {
+    TcState t;
+    TcPanel g;
+    CUtensorMap tmJ, tmS;
+    int P = 0, ntiles = 0, splitk = 1, batch = 1;
+    int64_t done_sweeps = 0, sweep_cap = 0;
+    int32_t* h_counters = nullptr;  // pinned: active prefix, active count, error
+    int32_t active_at_batch = 0;
+    bool profile = false;
+    // One sweep (128-spin panels x {GEMM, chain}, then the level step) captured
+    // as a CUDA graph and replayed: 2P+2 launches become one graph launch.
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~TcRun()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+constexpr int kTcBN = 128;
+
+// Device state of a tensor-core descent; buffers come from `get` so that the
+// blocking path (Scratch) and the serving engine (per-request lists) can own them.
+template <typename Get>
+int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t* rep_dev,
+             float t0_max, cudaStream_t st, Get&& get, TcRun* run)
 {
-    cudaStream_t st = c->stream;
-    const DevInstance& d = in->dev;
-    const int32_t R = s.R, n = d.n, n_pad = d.n_pad, P = n_pad / 128;
-    constexpr int BN = 128;
-    const int32_t R_pad = (R + BN - 1) / BN * BN;
-    const int ntiles = R_pad / BN;
+    int rc;
+    TcState& t = run->t;
+    const int32_t R = s.R, n = d.n, n_pad = d.n_pad;
+    const int32_t R_pad = (R + kTcBN - 1) / kTcBN * kTcBN;
+    run->P = n_pad / 128;
+    run->ntiles = R_pad / kTcBN;
     // Split K until the panel GEMM fills the SMs in one wave (one CTA per SM).
     int splitk = 1;
-    while (splitk < 8 && ntiles * splitk * 2 <= c->sms && (n_pad / 64) % (splitk * 2) == 0)
+    while (splitk < 8 && run->ntiles * splitk * 2 <= c->sms && (n_pad / 64) % (splitk * 2) == 0)
         splitk *= 2;
-    int rc;
-    TcState t;
+    run->splitk = splitk;
     t.R = R;
     t.R_pad = R_pad;
     t.n = n;
@@ -329,81 +413,473 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     t.d_min = s.d_min;
     t.k_max = s.k_max;
     t.fixed_sweeps = s.fixed_sweeps;
-    int32_t* rep = nullptr;
-    if ((rc = S.get((size_t)R * n_pad, &t.S))) return rc;
-    if ((rc = S.get((size_t)R_pad * n_pad, &t.Sb))) return rc;
-    if ((rc = S.get((size_t)splitk * R_pad * 128, &t.G))) return rc;
-    if ((rc = S.get(R, &t.T))) return rc;
-    if ((rc = S.get(R, &t.invT))) return rc;
-    if ((rc = S.get(R, &t.d))) return rc;
-    if ((rc = S.get(R, &t.active))) return rc;
-    if ((rc = S.get(R, &t.levels))) return rc;
-    if ((rc = S.get(R, &t.lvl_sweeps))) return rc;
-    if ((rc = S.get(R, &t.sweeps))) return rc;
-    if ((rc = S.get(R, &t.capped))) return rc;
-    if ((rc = S.get(4, &t.counters))) return rc;
-    if ((rc = S.get(R, &rep))) return rc;
-    t.rep = rep;
-    MARS_CUDA(c, cudaMemcpyAsync(rep, reps.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    t.rep = rep_dev;
+    if ((rc = get((size_t)R * n_pad * sizeof(float), (void**)&t.S))) return rc;
+    if ((rc = get((size_t)R_pad * n_pad * sizeof(__nv_bfloat16), (void**)&t.Sb))) return rc;
+    if ((rc = get((size_t)splitk * R_pad * 128 * sizeof(float), (void**)&t.G))) return rc;
+    if ((rc = get((size_t)R * sizeof(double), (void**)&t.T))) return rc;
+    if ((rc = get((size_t)R * sizeof(float), (void**)&t.invT))) return rc;
+    if ((rc = get((size_t)R * sizeof(float), (void**)&t.d))) return rc;
+    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.active))) return rc;
+    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.levels))) return rc;
+    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.lvl_sweeps))) return rc;
+    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.sweeps))) return rc;
+    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.capped))) return rc;
+    if ((rc = get(4 * sizeof(int32_t), (void**)&t.counters))) return rc;
     MARS_CUDA(c, cudaMemsetAsync(t.Sb, 0, (size_t)R_pad * n_pad * sizeof(__nv_bfloat16), st));
     MARS_CUDA(c, cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), st));
-    CUtensorMap tmJ, tmS;
-    if (!encode_bf16_2d(&tmJ, d.Jbf, n_pad, n_pad, 64, 128) ||
-        !encode_bf16_2d(&tmS, t.Sb, n_pad, R_pad, 64, BN))
+    if (!encode_bf16_2d(&run->tmJ, d.Jbf, n_pad, n_pad, 64, 128) ||
+        !encode_bf16_2d(&run->tmS, t.Sb, n_pad, R_pad, 64, kTcBN))
         return fail(c, MARS_EDEVICE, "tensor map encoding failed");
     MARS_CUDA(c, launch_tc_init(t, st));
     MARS_CUDA(c, launch_tc_prefix(t, st));
-    TcPanel g;
-    g.kblocks = n_pad / 64 / splitk;
-    g.R_pad = R_pad;
-    g.G = t.G;
-    g.active_prefix = t.counters;
-    g.err = t.counters + 2;
+    run->g.kblocks = n_pad / 64 / splitk;
+    run->g.R_pad = R_pad;
+    run->g.G = t.G;
+    run->g.active_prefix = t.counters;
+    run->g.err = t.counters + 2;
     // Every replica ends within (levels + 1) x (sweeps per level) sweeps.
     const double levels_max = std::ceil((double)t0_max / s.c_step) + 1.0;
-    const int64_t sweep_cap =
-        (int64_t)(levels_max * (double)(s.fixed_sweeps > 0 ? s.fixed_sweeps : s.k_max)) + 1;
-    int64_t done_sweeps = 0;
-    int batch = 1;
-    int32_t hc[4] = {0, 0, 0, 0};
-    MARS_CUDA(c, cudaMemcpyAsync(hc, t.counters, sizeof hc, cudaMemcpyDeviceToHost, st));
-    MARS_CUDA(c, cudaStreamSynchronize(st));
-    // Event pairs around the panel GEMMs of the first sweep of every batch.
-    while ((int)c->prof.size() < 2 * P) {
-        cudaEvent_t e;
-        MARS_CUDA(c, cudaEventCreate(&e));
-        c->prof.push_back(e);
+    run->sweep_cap = (int64_t)(levels_max * (double)(s.fixed_sweeps > 0 ? s.fixed_sweeps : s.k_max)) + 1;
+    run->batch = 1;
+    run->done_sweeps = 0;
+    return MARS_OK;
+}
+
+// One sweep as direct launches; with `timed`, event pairs bracket each GEMM.
+int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
+{
+    for (int pp = 0; pp < run->P; ++pp) {
+        run->g.p0 = pp * 128;
+        if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp], st));
+        MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, run->g, kTcBN, run->ntiles, run->splitk, st));
+        if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp + 1], st));
+        MARS_CUDA(c, launch_tc_chain(run->t, pp, st));
     }
-    for (;;) {
-        const int32_t active_now = hc[1];
-        for (int b = 0; b < batch; ++b) {
-            for (int pp = 0; pp < P; ++pp) {
-                g.p0 = pp * 128;
-                if (b == 0) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp], st));
-                MARS_CUDA(c, launch_tc_panel_gemm(tmJ, tmS, g, BN, ntiles, splitk, st));
-                if (b == 0) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp + 1], st));
-                MARS_CUDA(c, launch_tc_chain(t, pp, st));
-            }
-            MARS_CUDA(c, launch_tc_advance(t, st));
+    MARS_CUDA(c, launch_tc_advance(run->t, st));
+    return MARS_OK;
+}
+
+// Enqueue run->batch sweeps (the first one with timed GEMMs when profiling,
+// the rest as replays of the captured sweep), then the copy of the counters
+// to pinned memory.
+int tc_enqueue_batch(mars_ctx* c, TcRun* run, cudaStream_t st)
+{
+    int rc;
+    if (run->profile) {
+        while ((int)c->prof.size() < 2 * run->P) {
+            cudaEvent_t e;
+            MARS_CUDA(c, cudaEventCreate(&e));
+            c->prof.push_back(e);
         }
-        done_sweeps += batch;
-        MARS_CUDA(c, cudaMemcpyAsync(hc, t.counters, sizeof hc, cudaMemcpyDeviceToHost, st));
-        MARS_CUDA(c, cudaStreamSynchronize(st));
-        for (int pp = 0; pp < P; ++pp) {
+    }
+    for (int b = 0; b < run->batch; ++b) {
+        if (b == 0 && run->profile) {
+            if ((rc = tc_enqueue_sweep(c, run, st, true))) return rc;
+            continue;
+        }
+        if (!run->exec) {
+            MARS_CUDA(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+            rc = tc_enqueue_sweep(c, run, st, false);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(st, &graph);
+            if (rc) return rc;
+            if (e != cudaSuccess) return fail(c, MARS_EDEVICE, "sweep capture failed: %s", cudaGetErrorString(e));
+            run->graph = graph;
+            MARS_CUDA(c, cudaGraphInstantiate(&run->exec, run->graph, 0));
+        }
+        MARS_CUDA(c, cudaGraphLaunch(run->exec, st));
+    }
+    run->done_sweeps += run->batch;
+    MARS_CUDA(c, cudaMemcpyAsync(run->h_counters, run->t.counters, 4 * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, st));
+    return MARS_OK;
+}
+
+// After a batch's counters arrived: 1 = more sweeps needed, 0 = done, < 0 = error.
+int tc_after_batch(mars_ctx* c, TcRun* run)
+{
+    if (run->h_counters[2] != 0) return fail(c, MARS_ETIMEOUT, "a tensor-core pipeline wait gave up");
+    if (run->h_counters[1] == 0) return 0;
+    if (run->done_sweeps > run->sweep_cap) return fail(c, MARS_EDEVICE, "descent exceeded its sweep bound");
+    run->active_at_batch = run->h_counters[1];
+    run->batch = std::min(run->batch * 2, 32);
+    return 1;
+}
+
+// The dense descent on tensor cores, blocking: slots in start-temperature
+// order, a sweep = for each 128-spin panel {BF16 panel GEMM, in-panel
+// sequential chain}, then the level step; the host checks the active count
+// between batches of sweeps.
+int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve& s,
+                 const std::vector<int32_t>& reps, float t0_max, Scratch& S, TcProfile* prof)
+{
+    (void)p;
+    cudaStream_t st = c->stream;
+    int rc;
+    int32_t* rep = nullptr;
+    if ((rc = S.get(s.R, &rep))) return rc;
+    MARS_CUDA(c, cudaMemcpyAsync(rep, reps.data(), s.R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    TcRun run;
+    auto get = [&](size_t bytes, void** out) -> int {
+        unsigned char* q = nullptr;
+        int r = S.get(bytes, &q);
+        *out = q;
+        return r;
+    };
+    if ((rc = tc_setup(c, in->dev, s, rep, t0_max, st, get, &run))) return rc;
+    int32_t* pinned = nullptr;
+    MARS_CUDA(c, cudaMallocHost((void**)&pinned, 4 * sizeof(int32_t)));
+    run.h_counters = pinned;
+    run.profile = true;
+    MARS_CUDA(c, cudaMemcpyAsync(run.h_counters, run.t.counters, 4 * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, st));
+    cudaError_t se = cudaStreamSynchronize(st);
+    run.active_at_batch = run.h_counters[1];
+    int state = se == cudaSuccess ? (run.h_counters[1] > 0 ? 1 : 0) : -1;
+    while (state == 1) {
+        const int32_t active_now = run.active_at_batch;
+        if ((rc = tc_enqueue_batch(c, &run, st))) { cudaFreeHost(pinned); return rc; }
+        se = cudaStreamSynchronize(st);
+        if (se != cudaSuccess) break;
+        for (int pp = 0; pp < run.P; ++pp) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, c->prof[2 * pp], c->prof[2 * pp + 1]);
             prof->gemm_seconds += ms * 1e-3;
             prof->gemm_launches += 1;
-            prof->gemm_flops += 2.0 * 128.0 * (double)n * (double)active_now;
+            prof->gemm_flops += 2.0 * 128.0 * (double)in->dev.n * (double)active_now;
         }
-        if (hc[2] != 0) return fail(c, MARS_ETIMEOUT, "a tensor-core pipeline wait gave up");
-        if (hc[1] == 0) break;
-        if (done_sweeps > sweep_cap)
-            return fail(c, MARS_EDEVICE, "descent exceeded its sweep bound");
-        batch = std::min(batch * 2, 32);
+        state = tc_after_batch(c, &run);
     }
-    MARS_CUDA(c, launch_tc_finalize(t, d, s, st));
+    cudaFreeHost(pinned);
+    if (se != cudaSuccess) return fail(c, MARS_EDEVICE, "CUDA error: %s", cudaGetErrorString(se));
+    if (state < 0) return state;
+    MARS_CUDA(c, launch_tc_finalize(run.t, in->dev, s, st));
     return MARS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: requests admitted while others run (continuous batching).
+//
+// mars_submit queues a request; every mars_submit / mars_poll call advances
+// the engine: finished requests are collected (their events have fired), and
+// queued requests are admitted in arrival order while an in-flight slot is
+// free and the HBM budget holds their buffers. Each admitted request runs on
+// its own stream, so its kernels overlap with the others' on the device; a
+// dense tensor-core request advances one batch of sweeps per event.
+// ---------------------------------------------------------------------------
+enum class ReqState { Queued, Running, TcRunning, Finishing, Done, Failed };
+
+struct ServeReq {
+    int64_t id = 0;
+    int32_t inst = 0;
+    mars_params p{};
+    ReqState state = ReqState::Queued;
+    int rc = MARS_OK;
+    std::string err;
+    int slot = -1;
+    cudaStream_t st = nullptr;
+    std::vector<DevMem> bufs;
+    DevSolve s;
+    DevInstance dev;
+    DevResult* dres = nullptr;
+    int8_t* dbest = nullptr;
+    unsigned char* pinned = nullptr;  // DevResult | status | counters[4] | best spins
+    cudaEvent_t ev = nullptr;
+    std::unique_ptr<TcRun> tc;
+    double total_weight = 0.0, err_bound = 0.0;
+};
+
+struct Serve {
+    std::vector<cudaStream_t> streams;
+    std::vector<int> free_slots;
+    std::deque<int64_t> queue;
+    std::map<int64_t, std::unique_ptr<ServeReq>> reqs;
+    int64_t next_id = 1;
+    int max_inflight = 8;
+    int inflight = 0;
+};
+
+void serve_delete(Serve* sv) { delete sv; }
+
+Serve* serve_get(mars_ctx* c)
+{
+    if (!c->serve) c->serve = std::unique_ptr<Serve, void (*)(Serve*)>(new Serve(), serve_delete);
+    Serve* sv = c->serve.get();
+    while ((int)sv->streams.size() < sv->max_inflight) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) break;
+        sv->free_slots.push_back((int)sv->streams.size());
+        sv->streams.push_back(st);
+    }
+    return sv;
+}
+
+struct PinnedView {
+    DevResult* res;
+    int32_t* status;
+    int32_t* counters;
+    int8_t* best;
+};
+
+PinnedView pinned_view(unsigned char* base)
+{
+    PinnedView v;
+    v.res = (DevResult*)base;
+    v.status = (int32_t*)(base + 128);
+    v.counters = (int32_t*)(base + 192);
+    v.best = (int8_t*)(base + 256);
+    return v;
+}
+
+void serve_free_req(mars_ctx* c, Serve* sv, ServeReq* q)
+{
+    if (q->st) {
+        for (auto& b : q->bufs) dev_free_on(c, &b, q->st);
+        q->bufs.clear();
+    }
+    if (q->pinned) {
+        cudaFreeHost(q->pinned);
+        q->pinned = nullptr;
+    }
+    if (q->ev) {
+        cudaEventDestroy(q->ev);
+        q->ev = nullptr;
+    }
+    if (q->slot >= 0) {
+        sv->free_slots.push_back(q->slot);
+        sv->inflight -= 1;
+        q->slot = -1;
+    }
+    q->tc.reset();
+}
+
+// Device bytes a request holds while it runs (what admission checks).
+size_t serve_footprint(const DevInstance& d, const mars_params& p, int sms)
+{
+    const size_t R = (size_t)p.replicas, n = (size_t)d.n;
+    size_t b = R * n + R * (4 + 8 + 8 + 12 + 4 + 4) + 4096 + n;
+    if (d.dense && p.precision == MARS_BF16) {
+        const size_t np = (size_t)d.n_pad, Rp = (R + 127) / 128 * 128;
+        b += R * np * 4 + Rp * np * 2 + 8 * Rp * 128 * 4 + R * 32;
+    } else if (!d.dense) {
+        b += (size_t)sms * n * 8 * sizeof(float);  // a possible streaming slab
+    }
+    return b;
+}
+
+int serve_finish_enqueue(mars_ctx* c, ServeReq* q)
+{
+    cudaStream_t st = q->st;
+    if (!q->dev.integer && q->dev.exact_ok)
+        MARS_CUDA(c, launch_energy(q->dev, q->s.sigma, q->s.R, q->s.energy, nullptr, q->s.status, st));
+    MARS_CUDA(c, launch_best(q->s, q->dev.n, q->dev.integer, q->dbest, q->dres, st));
+    PinnedView v = pinned_view(q->pinned);
+    MARS_CUDA(c, cudaMemcpyAsync(v.res, q->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, st));
+    MARS_CUDA(c, cudaMemcpyAsync(v.status, q->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MARS_CUDA(c, cudaMemcpyAsync(v.best, q->dbest, q->dev.n, cudaMemcpyDeviceToHost, st));
+    MARS_CUDA(c, cudaEventRecord(q->ev, st));
+    q->state = ReqState::Finishing;
+    return MARS_OK;
+}
+
+// Allocate, enqueue the whole pipeline (or the first batch of a tensor-core
+// descent) on the request's stream, and record its event.
+int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
+{
+    Instance* in = find(c, q->inst);
+    if (!in) return fail(c, MARS_ENOTFOUND, "instance %d was freed before its request ran", q->inst);
+    q->dev = in->dev;
+    q->total_weight = in->info.total_weight;
+    q->err_bound = (in->dev.integer || in->dev.exact_ok)
+                       ? 0.0
+                       : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + in->dev.n);
+    q->slot = sv->free_slots.back();
+    sv->free_slots.pop_back();
+    sv->inflight += 1;
+    q->st = sv->streams[q->slot];
+    cudaStream_t st = q->st;
+    const mars_params& p = q->p;
+    const int32_t R = p.replicas, n = q->dev.n;
+    int rc;
+    auto get = [&](size_t bytes, void** out) -> int {
+        DevMem m;
+        int r = dev_alloc_on(c, bytes, &m, st);
+        if (r) return r;
+        q->bufs.push_back(m);
+        *out = m.p;
+        return MARS_OK;
+    };
+    MARS_CUDA(c, cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming));
+    MARS_CUDA(c, cudaMallocHost((void**)&q->pinned, 256 + (size_t)n));
+    DevSolve& s = q->s;
+    s.R = R;
+    s.seed = p.seed;
+    s.stream = p.stream;
+    s.c_step = p.c_step;
+    s.d_min = (float)p.d_min;
+    s.k_max = p.k_max;
+    s.fixed_sweeps = p.fixed_sweeps;
+    s.jacobi = p.update == MARS_UPDATE_JACOBI;
+    s.m0 = p.m0;
+    float* t0 = nullptr;
+    if ((rc = get((size_t)R * sizeof(float), (void**)&t0))) return rc;
+    if (p.t0) {
+        MARS_CUDA(c, cudaMemcpyAsync(t0, p.t0, R * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    } else {
+        MARS_CUDA(c, launch_draw(p.seed, p.stream, 0, R, 0, p.t_min, p.t_max, nullptr, t0, st));
+    }
+    s.t0 = t0;
+    if ((rc = get((size_t)R * n, (void**)&s.sigma))) return rc;
+    if ((rc = get((size_t)R * sizeof(double), (void**)&s.energy))) return rc;
+    if ((rc = get((size_t)R * sizeof(long long), (void**)&s.energy_i64))) return rc;
+    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&s.sweeps))) return rc;
+    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&s.levels))) return rc;
+    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&s.capped))) return rc;
+    if ((rc = get(2 * sizeof(int32_t), (void**)&s.work_counter))) return rc;
+    s.status = s.work_counter + 1;
+    if ((rc = get(sizeof(DevResult), (void**)&q->dres))) return rc;
+    if ((rc = get((size_t)n, (void**)&q->dbest))) return rc;
+    const bool tc = q->dev.dense && p.precision == MARS_BF16;
+    int rt = 1;
+    SparsePlan sp;
+    DensePlan dp;
+    if (tc) {
+        rt = 1;
+    } else if (q->dev.dense) {
+        dp = plan_dense(q->dev, R, s.jacobi, c->device);
+        if (dp.scratch_floats && (rc = get(dp.scratch_floats * sizeof(float), (void**)&s.m_scratch))) return rc;
+    } else {
+        if (s.jacobi || !plan_sparse_sell(q->dev, R, c->device, &sp))
+            sp = plan_sparse(q->dev, R, s.jacobi, c->device);
+        rt = sp.rt;
+        float* scr = nullptr;
+        if (sp.scratch_floats && (rc = get(sp.scratch_floats * sizeof(float), (void**)&scr))) return rc;
+        const size_t per = (size_t)sp.grid * n * rt;
+        if (!sp.onchip) { s.m_scratch = scr; scr += per; }
+        if (s.jacobi) s.m_next = scr;
+    }
+    const int32_t ntiles = (R + rt - 1) / rt;
+    int32_t* queue = nullptr;
+    if ((rc = get((size_t)ntiles * rt * sizeof(int32_t), (void**)&queue))) return rc;
+    MARS_CUDA(c, launch_queue_identity(queue, ntiles * rt, R, s.work_counter, st));
+    s.tile_rep = queue;
+    s.ntiles = ntiles;
+    s.rt = rt;
+    if (tc) {
+        q->tc.reset(new TcRun());
+        TcRun* run = q->tc.get();
+        const float t0_max = (float)std::max(p.t_max, 0.0);
+        if ((rc = tc_setup(c, q->dev, s, queue, p.t0 ? 1e6f * (float)p.c_step : t0_max, st, get, run)))
+            return rc;
+        run->h_counters = pinned_view(q->pinned).counters;
+        if ((rc = tc_enqueue_batch(c, run, st))) return rc;
+        MARS_CUDA(c, cudaEventRecord(q->ev, st));
+        q->state = ReqState::TcRunning;
+        return MARS_OK;
+    }
+    if (q->dev.dense) {
+        MARS_CUDA(c, launch_dense(q->dev, s, dp, st));
+    } else if (sp.sell) {
+        MARS_CUDA(c, launch_sparse_sell(q->dev, s, sp, st));
+    } else {
+        MARS_CUDA(c, launch_sparse(q->dev, s, sp, st));
+    }
+    return serve_finish_enqueue(c, q);
+}
+
+void serve_mark_failed(mars_ctx* c, Serve* sv, ServeReq* q, int rc)
+{
+    q->rc = rc;
+    q->err = c->err;
+    q->state = ReqState::Failed;
+    serve_free_req(c, sv, q);
+}
+
+void serve_progress(mars_ctx* c)
+{
+    Serve* sv = serve_get(c);
+    // collect
+    for (auto& kv : sv->reqs) {
+        ServeReq* q = kv.second.get();
+        if (q->state != ReqState::TcRunning && q->state != ReqState::Finishing) continue;
+        const cudaError_t e = cudaEventQuery(q->ev);
+        if (e == cudaErrorNotReady) continue;
+        if (e != cudaSuccess) {
+            fail(c, MARS_EDEVICE, "CUDA error: %s", cudaGetErrorString(e));
+            serve_mark_failed(c, sv, q, MARS_EDEVICE);
+            continue;
+        }
+        if (q->state == ReqState::TcRunning) {
+            const int r = tc_after_batch(c, q->tc.get());
+            int rc = MARS_OK;
+            if (r < 0) {
+                rc = r;
+            } else if (r == 1) {
+                rc = tc_enqueue_batch(c, q->tc.get(), q->st);
+                if (!rc && cudaEventRecord(q->ev, q->st) != cudaSuccess) rc = MARS_EDEVICE;
+            } else {
+                rc = launch_tc_finalize(q->tc->t, q->dev, q->s, q->st) == cudaSuccess ? MARS_OK : MARS_EDEVICE;
+                if (!rc) rc = serve_finish_enqueue(c, q);
+            }
+            if (rc) serve_mark_failed(c, sv, q, rc);
+            continue;
+        }
+        // Finishing: results are in pinned memory
+        PinnedView v = pinned_view(q->pinned);
+        if (*v.status != kDevOk) {
+            fail(c, MARS_EDEVICE, "device status %d", *v.status);
+            serve_mark_failed(c, sv, q, MARS_EDEVICE);
+            continue;
+        }
+        q->state = ReqState::Done;
+        for (auto& b : q->bufs) dev_free_on(c, &b, q->st);
+        q->bufs.clear();
+        if (q->slot >= 0) {
+            sv->free_slots.push_back(q->slot);
+            sv->inflight -= 1;
+            q->slot = -1;
+        }
+    }
+    // admit, in arrival order
+    while (!sv->queue.empty() && !sv->free_slots.empty()) {
+        const int64_t id = sv->queue.front();
+        auto it = sv->reqs.find(id);
+        if (it == sv->reqs.end()) { sv->queue.pop_front(); continue; }
+        ServeReq* q = it->second.get();
+        Instance* in = find(c, q->inst);
+        if (!in) {
+            sv->queue.pop_front();
+            fail(c, MARS_ENOTFOUND, "instance %d was freed before its request ran", q->inst);
+            serve_mark_failed(c, sv, q, MARS_ENOTFOUND);
+            continue;
+        }
+        const size_t need = serve_footprint(in->dev, q->p, c->sms);
+        if (c->budget && c->used + need > c->budget) {
+            if (sv->inflight == 0) {  // it will never fit
+                sv->queue.pop_front();
+                fail(c, MARS_ENOMEM, "request needs about %zu bytes; the HBM budget is %zu", need, c->budget);
+                serve_mark_failed(c, sv, q, MARS_ENOMEM);
+                continue;
+            }
+            break;  // wait for memory to free up
+        }
+        sv->queue.pop_front();
+        const int rc = serve_launch(c, sv, q);
+        if (rc) serve_mark_failed(c, sv, q, rc);
+    }
+}
+
+void serve_release(mars_ctx* c)
+{
+    if (!c->serve) return;
+    Serve* sv = c->serve.get();
+    for (cudaStream_t st : sv->streams) cudaStreamSynchronize(st);
+    for (auto& kv : sv->reqs) serve_free_req(c, sv, kv.second.get());
+    sv->reqs.clear();
+    for (cudaStream_t st : sv->streams) cudaStreamDestroy(st);
+    sv->streams.clear();
+    c->serve.reset();
 }
 
 // Accessors for mars_noalloc.cu.
@@ -416,8 +892,9 @@ int noalloc_view(mars_ctx* c, int32_t id, NoallocView* v)
     v->stream = c->stream;
     v->inst = &in->dev;
     v->total_weight = in->info.total_weight;
-    v->energy_err_bound =
-        in->dev.integer ? 0.0 : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + in->dev.n);
+    v->energy_err_bound = (in->dev.integer || in->dev.exact_ok)
+                              ? 0.0
+                              : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + in->dev.n);
     return MARS_OK;
 }
 
@@ -468,6 +945,7 @@ void mars_destroy(mars_ctx* c)
     if (!c) return;
     {
         DeviceGuard g(c->device);
+        serve_release(c);
         for (auto& kv : c->insts)
             for (auto& m : kv.second->mem) dev_free(c, &m);
         c->insts.clear();
@@ -569,6 +1047,7 @@ int mars_instance_dense(mars_ctx* c, int32_t n, const void* J, int32_t jt, const
     d.nlev = n;
     d.integer = integer;
     d.n_pad = n_pad;
+    if (!integer) exact_span(Jh, hh, (int64_t)n * (n - 1) / 2 + n, &d);
     {
         const uint16_t* jb = nullptr;
         if ((rc = upload(c, in.get(), Jb, &jb))) return rc;
@@ -729,6 +1208,8 @@ int mars_instance_csr(mars_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     std::vector<int32_t> lvl_slice(nlev + 1, 0);
     std::vector<int32_t> slice_words;  // row0, rows, degree, offset per slice
     std::vector<uint32_t> sell_pm1;
+    std::vector<uint16_t> sell16;      // the same as halfwords when every column fits 15 bits
+    const bool half = pm1 && n < 32768;
     std::vector<int32_t> sell_gen;     // (column, float bits) pairs
     int64_t sell_len = 0;
     for (int32_t l = 0; l < nlev; ++l) {
@@ -747,6 +1228,7 @@ int mars_instance_csr(mars_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
                     }
                     if (pm1) {
                         sell_pm1.push_back((uint32_t)cidx | (w < 0 ? 0x80000000u : 0u));
+                        if (half) sell16.push_back((uint16_t)((uint32_t)cidx | (w < 0 ? 0x8000u : 0u)));
                     } else {
                         const float wf = (float)w;
                         int32_t bits;
@@ -775,6 +1257,13 @@ int mars_instance_csr(mars_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
         d.slices = (const int4*)sw;
         if ((rc = upload(c, in.get(), lvl_slice, &d.lvl_slice))) return rc;
         if ((rc = upload(c, in.get(), sell_pm1, &d.sell_pm1))) return rc;
+        if ((rc = upload(c, in.get(), sell16, &d.sell16))) return rc;
+        d.nslices = (int32_t)(slice_words.size() / 4);
+        d.sell_len = sell_len;
+        int32_t deg0 = rp[1] - rp[0];
+        for (int32_t i = 1; i < n && deg0 >= 0; ++i)
+            if (rp[i + 1] - rp[i] != deg0) deg0 = -1;
+        d.regular_deg = deg0 > 0 ? deg0 : 0;
         const int32_t* sg = nullptr;
         if ((rc = upload(c, in.get(), sell_gen, &sg))) return rc;
         d.sell_gen = (const int2*)sg;
@@ -782,6 +1271,7 @@ int mars_instance_csr(mars_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     d.n = n;
     d.dense = 0;
     d.nnz = nnz;
+    if (!integer) exact_span(nval_f64, hh, nnz / 2 + n, &d);
     d.nlev = nlev;
     d.integer = integer;
     if ((rc = upload(c, in.get(), nrp, &d.row_ptr))) return rc;
@@ -972,6 +1462,8 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
         else
             MARS_CUDA(c, launch_sparse(in->dev, s, sp, st));
     }
+    if (!in->dev.integer && in->dev.exact_ok)  // replace the kernels' FP64 sums by exact ones
+        MARS_CUDA(c, launch_energy(in->dev, s.sigma, R, s.energy, nullptr, s.status, st));
     MARS_CUDA(c, cudaEventRecord(c->ev2, st));
     MARS_CUDA(c, launch_best(s, n, in->dev.integer, dbest, dres, st));
     MARS_CUDA(c, cudaEventRecord(c->ev1, st));
@@ -1015,10 +1507,246 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
         result->gemm_launches = tcprof.gemm_launches;
         result->gemm_flops = tcprof.gemm_flops;
         result->integer = in->dev.integer;
-        result->energy_err_bound =
-            in->dev.integer ? 0.0 : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + n);
+        result->energy_err_bound = (in->dev.integer || in->dev.exact_ok)
+                                       ? 0.0
+                                       : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + n);
         result->status = MARS_OK;
     }
+    return MARS_OK;
+}
+
+int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mars_params* params,
+                     int8_t* const* best_spins, mars_result* results)
+{
+    if (!c || count < 1 || !insts || !params) return MARS_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    Scratch S(c);
+    int rc;
+    std::vector<Instance*> ins(count);
+    std::vector<DevInstance> dins(count);
+    std::vector<BatchJob> jobs(count);
+    std::vector<DevResult*> dres(count);
+    std::vector<int8_t*> dbest(count);
+    for (int32_t j = 0; j < count; ++j) {
+        const mars_params* p = &params[j];
+        Instance* in = find(c, insts[j]);
+        if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d (job %d)", insts[j], j);
+        const int32_t R = p->replicas, n = in->dev.n;
+        if (in->dev.dense) return fail(c, MARS_EINVAL, "job %d: batched launches take CSR instances", j);
+        if (R < 1 || !std::isfinite(p->t_min) || !std::isfinite(p->t_max) || p->t_min > p->t_max ||
+            !(p->c_step > 0.0) || p->t_max / p->c_step > kMaxLevels || !(p->d_min >= 0.0) ||
+            p->k_max < 1 || p->fixed_sweeps < 0)
+            return fail(c, MARS_EINVAL, "job %d: bad parameters", j);
+        if (p->update != MARS_UPDATE_GS || p->precision != MARS_FP32)
+            return fail(c, MARS_EINVAL, "job %d: batched launches run sequential FP32 sweeps", j);
+        if ((size_t)R * n > ((size_t)1 << 40)) return fail(c, MARS_EINVAL, "job %d: R*n too large", j);
+        ins[j] = in;
+        dins[j] = in->dev;
+        DevSolve& s = jobs[j].s;
+        s.R = R;
+        s.seed = p->seed;
+        s.stream = p->stream;
+        s.c_step = p->c_step;
+        s.d_min = (float)p->d_min;
+        s.k_max = p->k_max;
+        s.fixed_sweeps = p->fixed_sweeps;
+        const bool pdev = p->flags & MARS_DEVICE_PTR;
+        float* t0 = nullptr;
+        if ((rc = S.get(R, &t0))) return rc;
+        std::vector<float> t0h(R);
+        if (p->t0) {
+            MARS_CUDA(c, cudaMemcpyAsync(t0, p->t0, R * sizeof(float),
+                                         pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        } else {
+            MARS_CUDA(c, launch_draw(p->seed, p->stream, 0, R, 0, p->t_min, p->t_max, nullptr, t0, st));
+        }
+        MARS_CUDA(c, cudaMemcpyAsync(t0h.data(), t0, R * sizeof(float), cudaMemcpyDeviceToHost, st));
+        s.t0 = t0;
+        if (p->m0) {
+            if (pdev) {
+                s.m0 = p->m0;
+            } else {
+                float* m0 = nullptr;
+                if ((rc = S.get((size_t)R * n, &m0))) return rc;
+                MARS_CUDA(c, cudaMemcpyAsync(m0, p->m0, (size_t)R * n * sizeof(float),
+                                             cudaMemcpyHostToDevice, st));
+                s.m0 = m0;
+            }
+        }
+        if ((rc = S.get((size_t)R * n, &s.sigma))) return rc;
+        if ((rc = S.get(R, &s.energy))) return rc;
+        if ((rc = S.get(R, &s.energy_i64))) return rc;
+        if ((rc = S.get(R, &s.sweeps))) return rc;
+        if ((rc = S.get(R, &s.levels))) return rc;
+        if ((rc = S.get(R, &s.capped))) return rc;
+        if ((rc = S.get(2, &s.work_counter))) return rc;
+        s.status = s.work_counter + 1;
+        MARS_CUDA(c, cudaMemsetAsync(s.work_counter, 0, 2 * sizeof(int32_t), st));
+        if ((rc = S.get(1, &dres[j]))) return rc;
+        if ((rc = S.get(n, &dbest[j]))) return rc;
+        MARS_CUDA(c, cudaStreamSynchronize(st));
+        for (float v : t0h)
+            if (!std::isfinite(v) || v / p->c_step > kMaxLevels)
+                return fail(c, MARS_EINVAL, "job %d: start temperatures out of range", j);
+        std::vector<int32_t> reps(R);
+        std::iota(reps.begin(), reps.end(), 0);
+        std::stable_sort(reps.begin(), reps.end(), [&](int32_t a, int32_t b) { return t0h[a] > t0h[b]; });
+        int32_t* dq = nullptr;
+        if ((rc = S.get(R, &dq))) return rc;
+        MARS_CUDA(c, cudaMemcpyAsync(dq, reps.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        s.tile_rep = dq;
+        s.ntiles = R;
+        s.rt = 1;
+        jobs[j].in = in->dev;
+    }
+    BatchPlan bp;
+    std::vector<int> fmts(count);
+    if (!plan_sparse_batch(dins.data(), count, c->device, &bp, fmts.data()))
+        return fail(c, MARS_EINVAL, "an instance is too large for the batched on-chip kernel");
+    for (int32_t j = 0; j < count; ++j) jobs[j].fmt = fmts[j];
+    BatchJob* djobs = nullptr;
+    int32_t* cursor = nullptr;
+    if ((rc = S.get(count, &djobs))) return rc;
+    if ((rc = S.get(1, &cursor))) return rc;
+    MARS_CUDA(c, cudaMemcpyAsync(djobs, jobs.data(), count * sizeof(BatchJob), cudaMemcpyHostToDevice, st));
+    MARS_CUDA(c, cudaMemsetAsync(cursor, 0, sizeof(int32_t), st));
+    MARS_CUDA(c, cudaEventRecord(c->ev0, st));
+    MARS_CUDA(c, launch_sparse_batch(djobs, count, cursor, bp, st));
+    MARS_CUDA(c, cudaEventRecord(c->ev2, st));
+    for (int32_t j = 0; j < count; ++j) {
+        const DevSolve& s = jobs[j].s;
+        if (!dins[j].integer && dins[j].exact_ok)
+            MARS_CUDA(c, launch_energy(dins[j], s.sigma, s.R, s.energy, nullptr, s.status, st));
+        MARS_CUDA(c, launch_best(s, dins[j].n, dins[j].integer, dbest[j], dres[j], st));
+    }
+    MARS_CUDA(c, cudaEventRecord(c->ev1, st));
+    std::vector<DevResult> hres(count);
+    std::vector<int32_t> hstatus(count, 0);
+    for (int32_t j = 0; j < count; ++j) {
+        MARS_CUDA(c, cudaMemcpyAsync(&hres[j], dres[j], sizeof(DevResult), cudaMemcpyDeviceToHost, st));
+        MARS_CUDA(c, cudaMemcpyAsync(&hstatus[j], jobs[j].s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if (best_spins && best_spins[j])
+            MARS_CUDA(c, cudaMemcpyAsync(best_spins[j], dbest[j], dins[j].n, cudaMemcpyDeviceToHost, st));
+    }
+    MARS_CUDA(c, cudaStreamSynchronize(st));
+    float ms = 0.f, ms_descent = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    cudaEventElapsedTime(&ms_descent, c->ev0, c->ev2);
+    for (int32_t j = 0; j < count; ++j) {
+        if (hstatus[j] != kDevOk) return fail(c, MARS_EDEVICE, "job %d: device status %d", j, hstatus[j]);
+        if (!results) continue;
+        mars_result* r = &results[j];
+        std::memset(r, 0, sizeof *r);
+        const Instance* in = ins[j];
+        r->best_energy = hres[j].best_energy;
+        r->best_energy_i64 = hres[j].best_energy_i64;
+        r->best_cut = (in->info.total_weight - hres[j].best_energy) / 2.0;
+        r->best_replica = hres[j].best_replica;
+        r->hits = hres[j].hits;
+        r->mean_energy = hres[j].sum_energy / params[j].replicas;
+        r->sweeps = hres[j].sweeps;
+        r->spin_updates = hres[j].sweeps * (int64_t)dins[j].n;
+        r->levels = hres[j].levels;
+        r->capped_levels = hres[j].capped;
+        r->gpu_seconds = ms * 1e-3;          // the whole batch
+        r->descent_seconds = ms_descent * 1e-3;
+        r->integer = dins[j].integer;
+        r->energy_err_bound = (dins[j].integer || dins[j].exact_ok)
+                                  ? 0.0
+                                  : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + dins[j].n);
+        r->status = MARS_OK;
+    }
+    return MARS_OK;
+}
+
+int mars_serve_limits(mars_ctx* c, int32_t max_inflight)
+{
+    if (!c || max_inflight < 1 || max_inflight > 64) return MARS_EINVAL;
+    DeviceGuard g(c->device);
+    Serve* sv = serve_get(c);
+    sv->max_inflight = std::max(max_inflight, (int32_t)sv->inflight);
+    serve_get(c);
+    return MARS_OK;
+}
+
+int mars_submit(mars_ctx* c, int32_t id, const mars_params* p, int64_t* req)
+{
+    if (!c || !p || !req) return MARS_EINVAL;
+    Instance* in = find(c, id);
+    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    if (p->replicas < 1 || !std::isfinite(p->t_min) || !std::isfinite(p->t_max) || p->t_min > p->t_max ||
+        !(p->c_step > 0.0) || p->t_max / p->c_step > kMaxLevels || !(p->d_min >= 0.0) ||
+        p->k_max < 1 || p->fixed_sweeps < 0 ||
+        (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI))
+        return fail(c, MARS_EINVAL, "bad parameters");
+    const bool tc = p->precision == MARS_BF16;
+    if (p->precision != MARS_FP32 && !(tc && in->dev.dense && p->update == MARS_UPDATE_GS))
+        return fail(c, MARS_EINVAL, "precision %d is not available for this instance", p->precision);
+    if ((p->m0 || p->t0) && !(p->flags & MARS_DEVICE_PTR))
+        return fail(c, MARS_EINVAL, "served requests take m0/t0 as device pointers");
+    if (tc && p->t0) return fail(c, MARS_EINVAL, "served tensor-core requests draw t0 themselves");
+    DeviceGuard g(c->device);
+    Serve* sv = serve_get(c);
+    auto q = std::make_unique<ServeReq>();
+    q->id = sv->next_id++;
+    q->inst = id;
+    q->p = *p;
+    *req = q->id;
+    sv->queue.push_back(q->id);
+    sv->reqs[q->id] = std::move(q);
+    serve_progress(c);
+    return MARS_OK;
+}
+
+int mars_poll(mars_ctx* c, int64_t req, int8_t* best_spins, mars_result* result)
+{
+    if (!c) return MARS_EINVAL;
+    DeviceGuard g(c->device);
+    serve_progress(c);
+    Serve* sv = c->serve.get();
+    auto it = sv ? sv->reqs.find(req) : std::map<int64_t, std::unique_ptr<ServeReq>>::iterator();
+    if (!sv || it == sv->reqs.end()) return fail(c, MARS_ENOTFOUND, "unknown request %lld", (long long)req);
+    ServeReq* q = it->second.get();
+    if (q->state == ReqState::Failed) {
+        const int rc = q->rc;
+        c->err = q->err;
+        sv->reqs.erase(it);
+        return rc;
+    }
+    if (q->state != ReqState::Done) return MARS_EAGAIN;
+    PinnedView v = pinned_view(q->pinned);
+    if (best_spins) std::memcpy(best_spins, v.best, q->dev.n);
+    if (result) {
+        const DevResult& h = *v.res;
+        std::memset(result, 0, sizeof *result);
+        result->best_energy = h.best_energy;
+        result->best_energy_i64 = h.best_energy_i64;
+        result->best_cut = (q->total_weight - h.best_energy) / 2.0;
+        result->best_replica = h.best_replica;
+        result->hits = h.hits;
+        result->mean_energy = h.sum_energy / q->p.replicas;
+        result->sweeps = h.sweeps;
+        result->spin_updates = h.sweeps * (int64_t)q->dev.n;
+        result->levels = h.levels;
+        result->capped_levels = h.capped;
+        result->integer = q->dev.integer;
+        result->energy_err_bound = q->err_bound;
+        result->status = MARS_OK;
+    }
+    serve_free_req(c, sv, q);
+    sv->reqs.erase(it);
+    return MARS_OK;
+}
+
+int mars_serve_status(mars_ctx* c, int32_t* queued, int32_t* running)
+{
+    if (!c) return MARS_EINVAL;
+    DeviceGuard g(c->device);
+    serve_progress(c);
+    Serve* sv = c->serve.get();
+    if (queued) *queued = sv ? (int32_t)sv->queue.size() : 0;
+    if (running) *running = sv ? sv->inflight : 0;
     return MARS_OK;
 }
 

@@ -31,6 +31,10 @@ struct DevInstance {
     const int32_t* lvl_slice = nullptr;  // nlev+1 offsets into slices
     const uint32_t* sell_pm1 = nullptr;  // +-1 couplings: column | sign << 31
     const int2* sell_gen = nullptr;      // general couplings: (column, float bits)
+    const uint16_t* sell16 = nullptr;    // +-1 couplings, n < 32768: column | sign << 15
+    int32_t nslices = 0;
+    int64_t sell_len = 0;                // padded entries (32 x degree summed over slices)
+    int32_t regular_deg = 0;             // the common degree when every spin has the same, else 0
     // dense (n*n, new labels: Jn[a][b] = J[new2old[a]][new2old[b]])
     int32_t n_pad = 0;                   // n rounded up to the 128-spin panel
     const __nv_bfloat16* Jbf = nullptr;  // n_pad*n_pad BF16, zero padded (tensor-core operand)
@@ -38,6 +42,10 @@ struct DevInstance {
     const float* Jf = nullptr;
     const int8_t* J_i8 = nullptr;
     const double* J_f64 = nullptr;
+    // exact FP64 energies of non-integer instances (exact_sum.cuh): every
+    // term is a multiple of 2^exact_e0 and every sum fits the accumulator
+    int32_t exact_ok = 0;
+    int32_t exact_e0 = 0;
     // common
     const float* h = nullptr;          // n floats or null
     const double* h_f64 = nullptr;     // n doubles or null
@@ -73,6 +81,23 @@ struct DevSolve {
     int32_t* status = nullptr;         // 1
 };
 
+// One instance of a batched launch (kernels_sparse_sell.cu).
+struct BatchJob {
+    DevInstance in;
+    DevSolve s;
+    int32_t fmt = 0;
+    int32_t pad = 0;
+};
+struct BatchPlan {
+    int rt = 1;
+    int threads = 1024;
+    size_t smem = 0;
+    int grid = 0;
+};
+bool plan_sparse_batch(const DevInstance* ins, int count, int device, BatchPlan* p, int* fmts);
+cudaError_t launch_sparse_batch(const BatchJob* jobs, int count, int* cursor, const BatchPlan& p,
+                                cudaStream_t st);
+
 struct DevResult {
     double best_energy;
     long long best_energy_i64;
@@ -93,6 +118,8 @@ struct SparsePlan {
     int grid = 0;
     size_t scratch_floats = 0;  // m_scratch (+ m_next) floats needed
     int sell = 0;       // the sliced-ELL kernel
+    int entry = 0;      // its coupling format: 0 general, 1 +-1 words, 2 +-1 halfwords in smem
+    int deg = 0;        // compile-time degree of a regular instance (4 or 6), else 0
 };
 bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p);
 cudaError_t launch_sparse_sell(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
@@ -159,6 +186,9 @@ cudaError_t launch_dense(const DevInstance& in, const DevSolve& s, const DensePl
 
 cudaError_t launch_draw(uint64_t seed, uint32_t stream, int32_t r0, int32_t R, int32_t n,
                         double t_min, double t_max, float* m0, float* t0, cudaStream_t st);
+
+cudaError_t launch_queue_identity(int32_t* q, int32_t total, int32_t R, int32_t* counters,
+                                  cudaStream_t st);
 
 cudaError_t launch_best(const DevSolve& s, int32_t n, int32_t integer, int8_t* best_spins,
                         DevResult* res, cudaStream_t st);

@@ -91,6 +91,11 @@ SIGNATURES = {
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                           ctypes.c_double, P, P, ctypes.c_uint32]),
     "mars_solve_noalloc": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P]),
+    "mars_solve_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P]),
+    "mars_serve_limits": (ctypes.c_int, [P, ctypes.c_int32]),
+    "mars_submit": (ctypes.c_int, [P, ctypes.c_int32, P, P]),
+    "mars_poll": (ctypes.c_int, [P, ctypes.c_int64, P, P]),
+    "mars_serve_status": (ctypes.c_int, [P, P, P]),
 }
 
 _lib = None
@@ -329,6 +334,89 @@ class Context:
             energies=keep.get("energies"), spins=keep.get("spins"), m_final=keep.get("m_final"),
             t0=keep.get("t0"), replica_sweeps=keep.get("sweeps"),
             replica_levels=keep.get("levels"), replica_capped=keep.get("capped"))
+
+    def solve_batch(self, jobs):
+        """mars_solve_batch over [(inst, replicas, t_min, t_max, kwargs), ...].
+
+        kwargs may hold c_step, d_min, k_max, fixed_sweeps, seed, stream, m0, t0
+        (host arrays). Returns a list of SolveResult (best spins and summary).
+        """
+        cnt = len(jobs)
+        params = (Params * cnt)()
+        insts = (ctypes.c_int32 * cnt)()
+        keep = []
+        bests = []
+        for j, (inst, R, t_min, t_max, kw) in enumerate(jobs):
+            p = params[j]
+            self._lib.mars_params_default(ctypes.byref(p))
+            p.replicas, p.t_min, p.t_max = int(R), float(t_min), float(t_max)
+            p.c_step = float(kw.get("c_step", 1.0))
+            p.d_min = float(kw.get("d_min", 1e-4))
+            p.k_max = int(kw.get("k_max", 1000))
+            p.fixed_sweeps = int(kw.get("fixed_sweeps", 0))
+            p.seed = int(kw.get("seed", 0))
+            p.stream = int(kw.get("stream", 0))
+            pm, km, _ = _arr(kw.get("m0"), np.float32)
+            pt, kt, _ = _arr(kw.get("t0"), np.float32)
+            p.m0, p.t0 = pm, pt
+            keep += [km, kt]
+            insts[j] = int(inst)
+            bests.append(np.zeros(self._n[inst], dtype=np.int8))
+        ptrs = (ctypes.c_void_p * cnt)(*[b.ctypes.data for b in bests])
+        res = (Result * cnt)()
+        self._check(self._lib.mars_solve_batch(self._ctx, cnt, insts, params, ptrs, res))
+        out = []
+        for j in range(cnt):
+            r = res[j]
+            out.append(SolveResult(
+                best_energy=r.best_energy, best_energy_i64=r.best_energy_i64,
+                best_cut=r.best_cut, best_replica=r.best_replica, hits=r.hits,
+                mean_energy=r.mean_energy, sweeps=r.sweeps, spin_updates=r.spin_updates,
+                levels=r.levels, capped_levels=r.capped_levels, gpu_seconds=r.gpu_seconds,
+                descent_seconds=r.descent_seconds, energy_err_bound=r.energy_err_bound,
+                integer=bool(r.integer), best_spins=bests[j]))
+        return out
+
+    # -- serving ------------------------------------------------------------------
+    def serve_limits(self, max_inflight: int):
+        self._check(self._lib.mars_serve_limits(self._ctx, int(max_inflight)))
+
+    def submit(self, inst: int, replicas: int, t_min: float, t_max: float, *, c_step=1.0,
+               d_min=1e-4, k_max=1000, fixed_sweeps=0, seed=0, stream=0, update="gs",
+               precision="fp32") -> int:
+        """mars_submit: queue a solve and return its request id."""
+        p = Params()
+        self._lib.mars_params_default(ctypes.byref(p))
+        p.replicas, p.t_min, p.t_max, p.c_step, p.d_min = int(replicas), t_min, t_max, c_step, d_min
+        p.k_max, p.fixed_sweeps, p.seed, p.stream = int(k_max), int(fixed_sweeps), int(seed), int(stream)
+        p.update, p.precision = UPDATE[update], PRECISION[precision]
+        req = ctypes.c_int64()
+        self._check(self._lib.mars_submit(self._ctx, int(inst), ctypes.byref(p), ctypes.byref(req)))
+        self._req_n = getattr(self, "_req_n", {})
+        self._req_n[req.value] = self._n[inst]
+        return req.value
+
+    def poll(self, req: int):
+        """mars_poll: None while pending, else a SolveResult (raises if the request failed)."""
+        n = self._req_n[req]
+        best = np.zeros(n, dtype=np.int8)
+        r = Result()
+        rc = self._lib.mars_poll(self._ctx, int(req), best.ctypes.data, ctypes.byref(r))
+        if rc == MARS_EAGAIN:
+            return None
+        self._req_n.pop(req, None)
+        self._check(rc)
+        return SolveResult(
+            best_energy=r.best_energy, best_energy_i64=r.best_energy_i64, best_cut=r.best_cut,
+            best_replica=r.best_replica, hits=r.hits, mean_energy=r.mean_energy, sweeps=r.sweeps,
+            spin_updates=r.spin_updates, levels=r.levels, capped_levels=r.capped_levels,
+            gpu_seconds=r.gpu_seconds, descent_seconds=r.descent_seconds,
+            energy_err_bound=r.energy_err_bound, integer=bool(r.integer), best_spins=best)
+
+    def serve_status(self):
+        q, rn = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.mars_serve_status(self._ctx, ctypes.byref(q), ctypes.byref(rn)))
+        return q.value, rn.value
 
     def energy(self, inst: int, spins):
         """Exact energies of spin vectors (count, n) or (n,) -> (float64[count], int64[count])."""

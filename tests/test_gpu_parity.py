@@ -116,14 +116,27 @@ def test_energy_integer_instances_exact(ctx, kind):
     ctx.free(inst)
 
 
-def test_energy_gaussian_close(ctx):
-    J = I.sk_gauss(150, 4)
-    h = np.random.default_rng(3).normal(size=150) * 0.1
-    inst = ctx.add_dense(J, h=h)
-    spins = np.random.default_rng(5).choice(np.array([-1, 1], np.int8), size=(16, 150))
+@pytest.mark.parametrize("kind", ["dense_field", "sparse_field", "dense_wide"])
+def test_energy_float_couplings_bit_exact(ctx, kind):
+    """Non-integer couplings: the GPU's energy is the exactly rounded sum (FP64 bit-exact)."""
+    rng = np.random.default_rng(3)
+    if kind == "dense_field":
+        J = I.sk_gauss(150, 4)
+        h = rng.normal(size=150) * 0.1
+        inst, oi, n = ctx.add_dense(J, h=h), O.Instance.dense(J, h), 150
+    elif kind == "sparse_field":
+        csr = I.er_graph(700, 9, 5, "pm1")
+        csr = I.Csr(csr.row_ptr, csr.col, csr.val * np.pi / 7)  # non-integer weights
+        h = rng.normal(size=700)
+        inst, oi, n = ctx.add_csr(*csr, h=h), O.Instance.csr(csr, h), 700
+    else:
+        # couplings spanning many binades, with cancellation
+        J = I.sk_gauss(96, 6) * np.exp(rng.uniform(-20, 20, size=(96, 96)))
+        J = np.triu(J, 1) + np.triu(J, 1).T
+        inst, oi, n = ctx.add_dense(J), O.Instance.dense(J), 96
+    spins = rng.choice(np.array([-1, 1], np.int8), size=(24, n))
     e, _ = ctx.energy(inst, spins)
-    ref = O.energies(O.Instance.dense(J, h), spins)
-    np.testing.assert_allclose(e, ref, rtol=0, atol=1e-12 * np.abs(J).sum())
+    assert np.array_equal(e, O.energies(oi, spins))
     ctx.free(inst)
 
 
@@ -318,11 +331,13 @@ def test_field_sparse_trajectory(ctx):
     inst = ctx.add_csr(*csr, h=h, order=order)
     m0, t0 = I.replica_inputs(7, 200, 0.5, 5.0, 3)
     t0 = floored_t0(t0, max_levels=STRICT_LEVELS)
-    g = ctx.solve(inst, 7, 0.5, 5.0, fixed_sweeps=1, m0=m0, t0=t0, outputs=("m_final", "spins"))
+    g = ctx.solve(inst, 7, 0.5, 5.0, fixed_sweeps=1, m0=m0, t0=t0,
+                  outputs=("m_final", "spins", "energies"))
     o = O.mars_solve(O.Instance.csr(csr, h), m0, t0, fixed_sweeps=1, order=order)
     check_trajectory(g.m_final, o["m"], "strict")
     e, _ = ctx.energy(inst, g.spins)
-    np.testing.assert_allclose(e, O.energies(O.Instance.csr(csr, h), g.spins), rtol=0, atol=1e-9)
+    ref = O.energies(O.Instance.csr(csr, h), g.spins)
+    assert np.array_equal(e, ref) and np.array_equal(g.energies, ref)  # FP64 bit-exact
     ctx.free(inst)
 
 

@@ -1,0 +1,105 @@
+"""Serving: requests submitted while others run give the results they give alone.
+
+Every replica of a served request computes exactly what it computes in a
+blocking mars_solve with the same parameters (the replica order differs, the
+arithmetic does not), so each served request's best energy, best replica,
+hits and sweep counts must equal the blocking solve's, whatever else was in
+flight on the GPU at the time.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1907_05124_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_05124_gb300 import build, mars
+    build.build()
+    c = mars.Context(0)
+    yield c
+    c.close()
+
+
+def _wait(ctx, reqs, timeout=300.0):
+    out, t0 = {}, time.time()
+    while len(out) < len(reqs):
+        for r in reqs:
+            if r not in out:
+                res = ctx.poll(r)
+                if res is not None:
+                    out[r] = res
+        assert time.time() - t0 < timeout, "served requests did not finish"
+        time.sleep(0.001)
+    return out
+
+
+def _same(a, b):
+    assert a.best_energy == b.best_energy
+    assert a.best_replica == b.best_replica
+    assert a.hits == b.hits
+    assert a.sweeps == b.sweeps and a.levels == b.levels and a.capped_levels == b.capped_levels
+    assert np.array_equal(a.best_spins, b.best_spins)
+
+
+def test_mixed_requests_match_blocking_solves(ctx):
+    graphs = {"lat": I.ea_lattice(40, 2, 1), "er": I.er_graph(2000, 8, 2, "pm1"),
+              "er_one": I.er_graph(800, 20, 3, "one"), "lat3": I.ea_lattice(10, 3, 4)}
+    insts = {k: ctx.add_csr(*g) for k, g in graphs.items()}
+    sk = I.sk_pm1(96, 5)
+    insts["sk"] = ctx.add_dense(sk)
+    gauss = I.sk_gauss(256, 6)
+    insts["sk_bf16"] = ctx.add_dense(gauss)
+    plan = [("lat", 200, 4.0, {}), ("er", 64, 6.0, {}), ("sk", 128, 20.0, {}),
+            ("er_one", 96, 10.0, {}), ("lat3", 50, 5.0, {}), ("lat", 33, 4.0, {}),
+            ("sk_bf16", 64, 2.0, {"precision": "bf16", "c_step": 1 / 16.0}), ("er", 7, 6.0, {})]
+    ctx.serve_limits(4)  # fewer slots than requests: some wait for a slot
+    reqs = []
+    for j, (k, R, tmax, kw) in enumerate(plan):
+        reqs.append(ctx.submit(insts[k], R, 0.0, tmax, seed=100 + j, **kw))
+    served = _wait(ctx, reqs)
+    for j, (k, R, tmax, kw) in enumerate(plan):
+        ref = ctx.solve(insts[k], R, 0.0, tmax, seed=100 + j, **kw)
+        _same(served[reqs[j]], ref)
+    # exact energies of the returned spins
+    r0 = served[reqs[0]]
+    assert r0.best_energy == O.energy(O.Instance.csr(graphs["lat"]), r0.best_spins)
+    r6 = served[reqs[6]]
+    assert r6.best_energy == O.energy(O.Instance.dense(gauss), r6.best_spins)
+    assert ctx.serve_status() == (0, 0)
+    for i in insts.values():
+        ctx.free(i)
+
+
+def test_budget_admission_and_oversized_request():
+    torch = pytest.importorskip("torch")
+    from paper_1907_05124_gb300 import mars
+    from paper_1907_05124_gb300.mars import MarsError, MARS_ENOMEM
+    c = mars.Context(0, hbm_budget_bytes=24 << 20)
+    g = I.ea_lattice(30, 2, 0)
+    inst = c.add_csr(*g)
+    small = [c.submit(inst, 256, 0.0, 4.0, seed=s) for s in range(6)]
+    big = c.submit(inst, 40000, 0.0, 4.0, seed=9)  # ~36 MB of spins: can never fit
+    done = _wait(c, small)
+    assert len(done) == 6
+    with pytest.raises(MarsError) as e:
+        while c.poll(big) is None:
+            time.sleep(0.001)
+    assert e.value.code == MARS_ENOMEM
+    c.close()
+
+
+def test_poll_unknown_request(ctx):
+    from paper_1907_05124_gb300.mars import MarsError
+    ctx._req_n = getattr(ctx, "_req_n", {})
+    ctx._req_n[123456] = 4
+    with pytest.raises(MarsError):
+        ctx.poll(123456)
