@@ -61,9 +61,15 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="ea2d", choices=["ea2d", "sk8192"],
-                    help="ea2d: the 2-D lattice (default); sk8192: dense SK on tensor cores")
+    ap.add_argument("--workload", default="ea2d", choices=["ea2d", "sk8192", "serve"],
+                    help="ea2d: the 2-D lattice (default); sk8192: dense SK on tensor cores; "
+                         "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
+    ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=3.0,
+                    help="serve: mean arrivals per second (about 80 %% of the mix's capacity)")
     ap.add_argument("--replicas", type=int, default=0, help="override R (profiling runs)")
+    ap.add_argument("--fixed-sweeps", type=int, default=0,
+                    help="profiling runs only: exactly this many sweeps per level")
     return ap.parse_args()
 
 
@@ -214,6 +220,21 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(tot_ms, updates, device):
+    """Whole-job numbers across ranks: the slowest rank's time, all ranks' updates.
+
+    Ranks solve disjoint replica sets (Philox stream = rank) of the same
+    instance; nothing else is exchanged.
+    """
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(tot_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -247,6 +268,9 @@ class Workload:
             self.config = dict(SK_WORKLOAD, replicas=self.R)
             self.dtype = "bf16"
         self.rank = rank
+        self.fixed = args.fixed_sweeps
+        if self.fixed:
+            self.config = dict(self.config, fixed_sweeps=self.fixed, note="profiling run")
 
     def add(self, ctx):
         return ctx.add_csr(*self.csr) if self.csr is not None else ctx.add_dense(self.J)
@@ -254,7 +278,7 @@ class Workload:
     def solve(self, ctx, inst, seed):
         return ctx.solve(inst, self.R, T_MIN, self.t_max, c_step=self.c_step, d_min=D_MIN,
                          k_max=K_MAX, seed=seed, stream=self.rank, precision=self.precision,
-                         outputs=())
+                         fixed_sweeps=self.fixed, outputs=())
 
 
 def run_mars(args, world, rank, local):
@@ -308,13 +332,8 @@ def run_mars(args, world, rank, local):
     torch.cuda.synchronize()
     tot_ms = sum(step_ms)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([updates], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        tot_ms, updates_all = float(t.item()), float(u.item())
-        dist.barrier()
+        tot_ms, updates_all = aggregate(tot_ms, updates, "cuda")
+        torch.distributed.barrier()
     else:
         updates_all = updates
     value = updates_all / (tot_ms * 1e-3)
@@ -340,19 +359,19 @@ def run_mars(args, world, rank, local):
     d_mean = statistics.mean(descent_s)
     upd_per_launch = updates / args.steps
     if wl.name == "ea2d":
-        # The descent kernel keeps every magnetisation on chip; HBM sees only the
-        # coupling table and the outputs. Its ceiling is the SFU: each update
-        # needs one exponential and one reciprocal (the tanh), at 16 SFU results
-        # per clock per SM.
-        sfu_per_update = 2.0
-        achieved = sfu_per_update * upd_per_launch / d_mean / 1e12
-        peak = 152 * 16 * sm_clock_ghz / 1e3
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T SFU-ops/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": "sparse_sell_kernel<RT=2, 1024 threads, +-1 couplings>",
-                    "peak_source": "152 SMs x 16 SFU ops/clk x SM clock",
-                    "descent_ms_mean": 1e3 * d_mean,
-                    "spin_updates_per_s_descent": upd_per_launch / d_mean}
+        # The descent kernel keeps every magnetisation and coupling on chip;
+        # HBM sees ~1 MB per launch. Its hardware ceiling for this method is
+        # the SFU: each update's tanh needs one ex2 and one rcp, and a GB300 SM
+        # retires 32 ex2 or 16 rcp per clock (measured with a throughput
+        # microbenchmark), i.e. 1 / (1/32 + 1/16) = 10.67 updates per clock.
+        sfu_updates_per_clk = 1.0 / (1.0 / 32.0 + 1.0 / 16.0)
+        achieved = upd_per_launch / d_mean
+        peak = 152 * sfu_updates_per_clk * sm_clock_ghz * 1e9
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                    "unit": "spin-updates/s (SFU-bound)", "frac": achieved / peak, "traffic": None,
+                    "kernel": "sparse_sell_kernel<RT=2, 1024 threads, halfword couplings, degree 4>",
+                    "peak_source": "152 SMs x (1/32 + 1/16 SFU clocks per tanh)^-1 x SM clock",
+                    "descent_ms_mean": 1e3 * d_mean}
     else:
         achieved = gemm_flops / gemm_s / 1e12 if gemm_s > 0 else 0.0
         peak = peaks["bf16_tflops_sustained"]
@@ -387,11 +406,86 @@ def run_mars(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_serve(args, world, rank, local):
+    """Serving: Poisson arrivals of mixed Ising / max-cut requests, p50/p99 latency.
+
+    The request mix follows the serving configuration in shape (dense SK with
+    +-1 or Gaussian couplings, sparse lattices and random graphs, replica
+    counts 64-1024) with sizes scaled so that a run ends within minutes:
+    dense N 256-1024 (tensor-core BF16 for the Gaussian ones), sparse N 1k-100k.
+    """
+    import numpy as np
+    import torch
+
+    from paper_1907_05124_gb300 import build, instances, mars
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    build.build()
+    rng = np.random.default_rng(0)
+    ctx = mars.Context(local, hbm_budget_bytes=120 << 30)
+    pool = []  # (name, inst, n, t_max, c_step, precision)
+    for nn in (256, 512, 1024):
+        pool.append((f"sk_pm1_{nn}", ctx.add_dense(instances.sk_pm1(nn, nn)), nn, 2.0 * nn ** 0.5, 1.0, "fp32" if nn == 256 else "bf16"))
+        pool.append((f"sk_gauss_{nn}", ctx.add_dense(instances.sk_gauss(nn, nn + 1)), nn, 2.0, 1.0 / nn ** 0.5, "bf16"))
+    for L in (32, 64, 100, 200):
+        g = instances.ea_lattice(L, 2, L)
+        pool.append((f"ea2d_{L}", ctx.add_csr(*g), g.n, 4.0, 1.0, "fp32"))
+    for L in (16, 32):
+        g = instances.ea_lattice(L, 3, L)
+        pool.append((f"ea3d_{L}", ctx.add_csr(*g), g.n, 6.0, 1.0, "fp32"))
+    for nn, d in ((1000, 40), (5000, 12), (20000, 4), (100000, 4)):
+        g = instances.er_graph(nn, d, nn + d, "pm1")
+        pool.append((f"er_{nn}_{d}", ctx.add_csr(*g), g.n, 2.0 * d ** 0.5 + 1.0, 1.0, "fp32"))
+    n_req = args.requests
+    kinds = rng.integers(0, len(pool), size=n_req)
+    reps = rng.choice(np.array([64, 128, 256, 512, 1024]), size=n_req)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n_req))
+    ctx.serve_limits(8)
+    pending, lat, upd = {}, [], 0
+    t_start = time.perf_counter()
+    nxt = 0
+    while nxt < n_req or pending:
+        now = time.perf_counter() - t_start
+        while nxt < n_req and arrivals[nxt] <= now:
+            name, inst, nn, tmax, cstep, prec = pool[kinds[nxt]]
+            req = ctx.submit(inst, int(reps[nxt]), 0.0, tmax, c_step=cstep, seed=nxt,
+                             precision=prec)
+            pending[req] = arrivals[nxt]
+            nxt += 1
+        for req in list(pending):
+            r = ctx.poll(req)
+            if r is not None:
+                lat.append(time.perf_counter() - t_start - pending.pop(req))
+                upd += r.spin_updates
+        time.sleep(0.0002)
+    wall = time.perf_counter() - t_start
+    lat_ms = 1e3 * np.array(lat)
+    line = {
+        "metric": "spin-updates/s", "value": upd / wall, "unit": "spin-updates/s", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * wall, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+        "data": "synthetic (seeded instances, Poisson arrivals)",
+        "config": {"workload": f"serving: {n_req} Poisson arrivals at {args.rate}/s, mixed dense SK "
+                               "(N 256-1024, +-1 / Gaussian) and sparse lattices / ER graphs "
+                               "(N 1k-100k), R 64-1024, 8 in flight, 120 GB budget",
+                   "requests": n_req, "rate_per_s": args.rate},
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                       "p99": float(np.percentile(lat_ms, 99)),
+                       "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "serve":
+        run_serve(args, world, rank, local)
         return
     run_mars(args, world, rank, local)
 

@@ -61,7 +61,14 @@ typedef enum {
 
 typedef enum { MARS_I8 = 1, MARS_F32 = 2, MARS_F64 = 3 } mars_dtype;
 
-enum { MARS_DEVICE_PTR = 1u };
+enum {
+    MARS_DEVICE_PTR = 1u,
+    /* mars_params.flags: after a MARS_BF16 descent of a dense instance,
+     * re-converge every replica's last level with FP32 local fields (the
+     * SIMT path), from its BF16 final state at that level's temperature.
+     * Its sweeps are added to the replica's counts. */
+    MARS_POLISH_FP32 = 2u
+};
 
 typedef enum { MARS_UPDATE_GS = 0, MARS_UPDATE_JACOBI = 1 } mars_update;
 
@@ -153,7 +160,7 @@ int mars_instance_order(mars_ctx* ctx, int32_t inst, int32_t* order_out);
  *  m0, t0        optional caller start states: m0 R*n floats (replica-major,
  *                original spin labels, values in [-1, 1]) and t0 R floats;
  *                NULL draws them as above
- *  flags         MARS_DEVICE_PTR if m0/t0 are device pointers
+ *  flags         MARS_DEVICE_PTR if m0/t0 are device pointers; MARS_POLISH_FP32
  */
 typedef struct {
     int32_t replicas;

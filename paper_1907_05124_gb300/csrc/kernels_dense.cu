@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kDenseWarps * 32) dense_descent_kernel(DevInst
     }
     __syncwarp();
 
-    double T = (double)s.t0[r] - s.c_step;
+    double T = s.t_first ? s.t_first[r] : (double)s.t0[r] - s.c_step;
     bool act = T > 0.0;
     float invT = act ? (float)(1.0 / T) : 0.f;
     int levels = act ? 1 : 0, sweeps = 0, capped = 0, lvl_sweeps = 0;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kDenseWarps * 32) dense_descent_kernel(DevInst
             if (s.fixed_sweeps == 0 && !(d <= s.d_min)) ++capped;
             T = T - s.c_step;
             lvl_sweeps = 0;
-            if (T > 0.0) {
+            if (T > 0.0 && !s.one_level) {
                 ++levels;
                 invT = (float)(1.0 / T);
             } else {
@@ -138,9 +138,14 @@ __global__ void __launch_bounds__(kDenseWarps * 32) dense_descent_kernel(DevInst
     if (lane == 0) {
         s.energy[r] = in.integer ? (double)ei : ef;
         s.energy_i64[r] = in.integer ? ei : 0;
-        s.sweeps[r] = sweeps;
-        s.levels[r] = levels;
-        s.capped[r] = capped;
+        if (s.add_counts) {
+            s.sweeps[r] += sweeps;
+            s.capped[r] += capped;
+        } else {
+            s.sweeps[r] = sweeps;
+            s.levels[r] = levels;
+            s.capped[r] = capped;
+        }
     }
 }
 

@@ -333,7 +333,27 @@ __global__ void __launch_bounds__(256) tc_finalize_kernel(TcState t, DevInstance
     }
 }
 
+__global__ void tc_export_kernel(TcState t, DevInstance in, float* m_out, double* t_last)
+{
+    const size_t total = (size_t)t.R * t.n;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int slot = (int)(idx / t.n), a = (int)(idx % t.n);
+        const int r = t.rep[slot];
+        m_out[(size_t)r * t.n + __ldg(in.new2old + a)] = t.S[(size_t)slot * t.n_pad + a];
+    }
+    for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < t.R; slot += gridDim.x * blockDim.x)
+        t_last[t.rep[slot]] = t.levels[slot] > 0 ? t.T[slot] + t.c_step : 0.0;
+}
+
 }  // namespace
+
+cudaError_t launch_tc_export(const TcState& t, const DevInstance& in, float* m_out, double* t_last,
+                             cudaStream_t st)
+{
+    tc_export_kernel<<<1024, 256, 0, st>>>(t, in, m_out, t_last);
+    return cudaGetLastError();
+}
 
 size_t tc_gemm_smem(int bn) { return bn == 64 ? GemmSmem<64>::kBytes : GemmSmem<128>::kBytes; }
 

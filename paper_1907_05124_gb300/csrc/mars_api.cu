@@ -512,7 +512,8 @@ int tc_after_batch(mars_ctx* c, TcRun* run)
 // sequential chain}, then the level step; the host checks the active count
 // between batches of sweeps.
 int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve& s,
-                 const std::vector<int32_t>& reps, float t0_max, Scratch& S, TcProfile* prof)
+                 const std::vector<int32_t>& reps, float t0_max, Scratch& S, TcProfile* prof,
+                 bool polish)
 {
     (void)p;
     cudaStream_t st = c->stream;
@@ -555,6 +556,24 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     if (se != cudaSuccess) return fail(c, MARS_EDEVICE, "CUDA error: %s", cudaGetErrorString(se));
     if (state < 0) return state;
     MARS_CUDA(c, launch_tc_finalize(run.t, in->dev, s, st));
+    if (polish) {
+        // FP32 polish: the SIMT dense path re-converges each replica's last
+        // level from its BF16 final state; it writes the spins and energies.
+        float* m_out = nullptr;
+        double* t_last = nullptr;
+        if ((rc = S.get((size_t)s.R * in->dev.n, &m_out))) return rc;
+        if ((rc = S.get(s.R, &t_last))) return rc;
+        MARS_CUDA(c, launch_tc_export(run.t, in->dev, m_out, t_last, st));
+        DevSolve ps = s;
+        ps.m0 = m_out;
+        ps.t_first = t_last;
+        ps.one_level = 1;
+        ps.add_counts = 1;
+        ps.jacobi = 0;
+        DensePlan dp = plan_dense(in->dev, s.R, 0, c->device);
+        if (dp.scratch_floats && (rc = S.get(dp.scratch_floats, &ps.m_scratch))) return rc;
+        MARS_CUDA(c, launch_dense(in->dev, ps, dp, st));
+    }
     return MARS_OK;
 }
 
@@ -1453,7 +1472,8 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     MARS_CUDA(c, cudaEventRecord(c->ev0, st));
     if (tc) {
         const float t0_max = *std::max_element(t0h.begin(), t0h.end());
-        if ((rc = run_dense_tc(c, in, p, s, reps, t0_max, S, &tcprof))) return rc;
+        if ((rc = run_dense_tc(c, in, p, s, reps, t0_max, S, &tcprof, (p->flags & MARS_POLISH_FP32) != 0)))
+            return rc;
     } else if (in->dev.dense) {
         MARS_CUDA(c, launch_dense(in->dev, s, dp, st));
     } else {

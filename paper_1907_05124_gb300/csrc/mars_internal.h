@@ -67,6 +67,9 @@ struct DevSolve {
     int32_t k_max = 1000;
     int32_t fixed_sweeps = 0;
     int32_t jacobi = 0;
+    const double* t_first = nullptr;   // optional per-replica temperature of the first level
+    int32_t one_level = 0;             // stop after the first level (the FP32 polish)
+    int32_t add_counts = 0;            // add sweeps/levels/capped to the outputs' values
     float* m_scratch = nullptr;        // per-CTA state when it does not fit on chip
     float* m_next = nullptr;           // per-CTA second buffer for synchronous sweeps
     // outputs
@@ -172,6 +175,10 @@ cudaError_t launch_tc_advance(const TcState& t, cudaStream_t st);
 cudaError_t launch_tc_prefix(const TcState& t, cudaStream_t st);
 cudaError_t launch_tc_finalize(const TcState& t, const DevInstance& in, const DevSolve& s,
                                cudaStream_t st);
+// The tensor-core descent's final state in caller labels (R*n floats) and each
+// replica's last temperature (0 for a replica that visited no level).
+cudaError_t launch_tc_export(const TcState& t, const DevInstance& in, float* m_out, double* t_last,
+                             cudaStream_t st);
 
 struct DensePlan {
     int warps_per_block = 4;

@@ -20,6 +20,7 @@ MARS_OK, MARS_EINVAL, MARS_ENOMEM, MARS_EAGAIN, MARS_ETIMEOUT, MARS_EDEVICE, MAR
     0, -1, -2, -3, -4, -5, -6
 MARS_I8, MARS_F32, MARS_F64 = 1, 2, 3
 MARS_DEVICE_PTR = 1
+MARS_POLISH_FP32 = 2
 NOALLOC_SCRATCH_BYTES = 16 << 20  # MARS_NOALLOC_SCRATCH_BYTES
 UPDATE = {"gs": 0, "jacobi": 1}
 PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
@@ -280,7 +281,8 @@ class Context:
     # -- solve ----------------------------------------------------------------
     def solve(self, inst: int, replicas: int, t_min: float, t_max: float, *, c_step=1.0,
               d_min=1e-4, k_max=1000, fixed_sweeps=0, seed=0, stream=0, update="gs",
-              precision="fp32", m0=None, t0=None, outputs=("energies",), device_outputs=False):
+              precision="fp32", m0=None, t0=None, outputs=("energies",), device_outputs=False,
+              polish=False):
         """Run mars_solve; `outputs` names the per-replica arrays to return."""
         n = self._n[inst]
         p = Params()
@@ -293,7 +295,7 @@ class Context:
         if m0 is not None and t0 is not None and dm != dt_:
             raise ValueError("m0 and t0 must both be host arrays or both device tensors")
         p.m0, p.t0 = pm, pt
-        p.flags = MARS_DEVICE_PTR if (dm or dt_) else 0
+        p.flags = (MARS_DEVICE_PTR if (dm or dt_) else 0) | (MARS_POLISH_FP32 if polish else 0)
         R = int(replicas)
         want = set(outputs or ())
         o = Outputs()

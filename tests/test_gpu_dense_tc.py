@@ -139,3 +139,30 @@ def test_bf16_rejected_where_not_available(ctx):
     with pytest.raises(MarsError):
         ctx.solve(dinst, 4, 0.0, 4.0, precision="bf16", update="jacobi")
     ctx.free(dinst)
+
+
+def test_fp32_polish_leaves_fixed_points(ctx):
+    """After a BF16 descent with the FP32 polish, every replica that converged
+    its last level sits at a fixed point of the update at that temperature:
+    ||m + tanh((J m + h)/T)||_inf <= d_min ||J||_inf / T (the bound the oracle
+    pins), up to FP32 rounding of m."""
+    n, R, c = 256, 32, 1.0 / 16.0
+    J = I.sk_gauss(n, 11)
+    inst = ctx.add_dense(J)
+    g = ctx.solve(inst, R, 0.0, 2.0, c_step=c, precision="bf16", polish=True,
+                  outputs=("m_final", "t0", "levels", "energies", "spins", "capped"))
+    jinf = np.abs(J).sum(axis=1).max()
+    checked = 0
+    for r in range(R):
+        if g.replica_levels[r] == 0 or g.replica_capped[r] > 0:
+            continue
+        T = float(g.t0[r])
+        for _ in range(int(g.replica_levels[r])):
+            T = T - c
+        m = g.m_final[r].astype(np.float64)
+        resid = np.abs(m + np.tanh(J @ m / T)).max()
+        assert resid <= 1e-4 * jinf / T + 1e-5, (r, resid)
+        checked += 1
+    assert checked >= R // 2
+    assert np.array_equal(g.energies, O.energies(O.Instance.dense(J), g.spins))
+    ctx.free(inst)
