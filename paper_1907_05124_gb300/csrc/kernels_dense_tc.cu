@@ -32,16 +32,16 @@ constexpr int kChainWarps = 8;
 
 __device__ __forceinline__ float tanh_sfu(float x)
 {
-    // tanh(x) = sign(x) (1 - 2 / (1 + 2^{2|x| log2 e})), SFU ex2 and rcp; below
-    // |x| = 1e-3 the odd series x - x^3/3 (error < 2e-16) keeps tiny fields'
-    // signs, which the difference 1 - 2/(1+e) would round away.
+    // tanh(x) = sign(x) (1 - 2 / (1 + 2^{2|x| log2 e})), SFU ex2 and rcp
+    // (absolute error ~6e-8). Below |x| = 4e-3, tanh(x) = x to within
+    // x^3/3 <= 2.2e-8, which also keeps the sign of tiny fields that the
+    // difference 1 - 2/(1+e) would round away.
     const float a = fabsf(x) * 2.8853900817779268f;
     float e, r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(a));
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
     const float big = copysignf(fmaf(-2.0f, r, 1.0f), x);
-    const float small = fmaf(x * x, x * -0.333333343f, x);
-    return fabsf(x) < 1e-3f ? small : big;
+    return fabsf(x) < 4e-3f ? x : big;
 }
 
 template <int BN>
@@ -152,6 +152,24 @@ __device__ __forceinline__ void acc2(float& s, float& c, float a, float b)
 }
 
 // One warp per replica slot: the panel's 128 spins in sequence.
+// Per spin of the panel, what every lane of a replica's warp reads at that
+// spin's step: the low part of its field, its old FP32 and BF16 values and
+// J[a-1][a], the coupling to the spin updated just before it.
+struct ChainSpin {
+    float gc, s_old, s_old_bf, j_prev;
+};
+constexpr int kMaxSplit = 8;
+constexpr int kChainSmem = kBM * kBM * (int)sizeof(float) + kChainWarps * kBM * (int)sizeof(ChainSpin);
+
+// The chain with one step of lookahead. Every lane computes the update of the
+// current spin a itself, from g_a as it stood before the last change
+// (broadcast during the previous step) plus J[a-1][a] * delta_{a-1}; the
+// lanes that own the panel's other spins fold delta_a into their fields. The
+// broadcast of g_{a+1} thus overlaps the update of spin a, and a step's
+// critical path is one FMA, the tanh and one subtraction, with no shuffle
+// and no divergence. Operations and their order are those of the plain
+// chain (the owner of spin a would apply the same FMAs), so the fields are
+// bit-identical to it.
 __global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t, int p)
 {
     extern __shared__ __align__(16) float Jb[];  // FP32 diagonal block of J (symmetric), 64 KB
@@ -159,46 +177,56 @@ __global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t
     const float* src = t.Jdiag + (size_t)p * kBM * kBM;
     for (int i = threadIdx.x; i < kBM * kBM / 4; i += blockDim.x)
         reinterpret_cast<float4*>(Jb)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
+    ChainSpin* cs = reinterpret_cast<ChainSpin*>(Jb + kBM * kBM) + warp * kBM;
     __syncthreads();
     const int slot = blockIdx.x * kChainWarps + warp;
     if (slot >= t.R || !t.active[slot]) return;
     const int p0 = p * kBM;
     const float invT = t.invT[slot];
-    float g[4], gc[4], sf[4], so_f[4], so_b[4];
+    // Split-K partial fields: every load first, then the compensated sum in
+    // split order, then h.
+    float gp[kMaxSplit][4];
+#pragma unroll
+    for (int sp = 0; sp < kMaxSplit; ++sp)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            gp[sp][q] = sp < t.splitk ? t.G[((size_t)sp * t.R_pad + slot) * kBM + lane + 32 * q] : 0.f;
+    float g[4], sf[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int a = lane + 32 * q;
         float acc = 0.f, accc = 0.f;
-        for (int sp = 0; sp < t.splitk; ++sp)
-            acc2(acc, accc, t.G[((size_t)sp * t.R_pad + slot) * kBM + a], 1.0f);
+#pragma unroll
+        for (int sp = 0; sp < kMaxSplit; ++sp)
+            if (sp < t.splitk) acc2(acc, accc, gp[sp][q], 1.0f);
         if (t.h && p0 + a < t.n) acc2(acc, accc, __ldg(t.h + p0 + a), 1.0f);
         g[q] = acc;
-        gc[q] = accc;
         const size_t idx = (size_t)slot * t.n_pad + p0 + a;
-        so_f[q] = t.S[idx];
-        so_b[q] = __bfloat162float(t.Sb[idx]);
-        sf[q] = so_f[q];
+        sf[q] = t.S[idx];
+        cs[a] = ChainSpin{accc, sf[q], __bfloat162float(t.Sb[idx]), a > 0 ? Jb[(a - 1) * kBM + a] : 0.f};
     }
-    float dloc = 0.f;
+    __syncwarp();
+    float ghat = __shfl_sync(0xffffffffu, g[0], 0);
+    // -0 * 0 + ghat == ghat for every ghat, so the first step's FMA is exact
+    float dprev = -0.f, dloc = 0.f;
 #pragma unroll
     for (int qa = 0; qa < 4; ++qa) {
 #pragma unroll 4
         for (int l = 0; l < 32; ++l) {
             const int a = qa * 32 + l;
-            float delta = 0.f;
-            if (lane == l) {
-                const float sn = -tanh_sfu((g[qa] + gc[qa]) * invT);
-                dloc = fmaxf(dloc, fabsf(sn - so_f[qa]));
-                delta = sn - so_b[qa];
-                sf[qa] = sn;
-            }
-            delta = __shfl_sync(0xffffffffu, delta, l);
+            const ChainSpin c = cs[a];
+            const float x = fmaf(c.j_prev, dprev, ghat);
+            const float sn = -tanh_sfu((x + c.gc) * invT);
+            dloc = fmaxf(dloc, fabsf(sn - c.s_old));
+            const float delta = sn - c.s_old_bf;
+            if (lane == l) sf[qa] = sn;
+            // g_{a+1} before delta_a reaches it; its owner applies delta_a below
+            const float gsrc = l < 31 ? g[qa] : g[qa < 3 ? qa + 1 : 3];
+            ghat = __shfl_sync(0xffffffffu, gsrc, (l + 1) & 31);
             const float* Jrow = Jb + a * kBM;
 #pragma unroll
-            for (int q = qa; q < 4; ++q) {
-                const int k = lane + 32 * q;
-                if (k > a) g[q] = fmaf(Jrow[k], delta, g[q]);
-            }
+            for (int q = qa; q < 4; ++q) g[q] = fmaf(Jrow[lane + 32 * q], delta, g[q]);
+            dprev = delta;
         }
     }
 #pragma unroll
@@ -210,7 +238,7 @@ __global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t
             t.Sb[idx] = __float2bfloat16_rn(sf[q]);
         }
     }
-    dloc = warp_reduce_strided<1>(dloc, MaxOp());
+    // every lane computed every spin's change, so dloc is the warp's maximum
     if (lane == 0) t.d[slot] = fmaxf(t.d[slot], dloc);
 }
 
@@ -372,10 +400,11 @@ cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS,
 
 cudaError_t launch_tc_chain(const TcState& t, int p, cudaStream_t st)
 {
-    constexpr int smem = kBM * kBM * (int)sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(panel_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (t.splitk < 1 || t.splitk > kMaxSplit) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(panel_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kChainSmem);
     if (e != cudaSuccess) return e;
-    panel_chain_kernel<<<(t.R + kChainWarps - 1) / kChainWarps, kChainWarps * 32, smem, st>>>(t, p);
+    panel_chain_kernel<<<(t.R + kChainWarps - 1) / kChainWarps, kChainWarps * 32, kChainSmem, st>>>(t, p);
     return cudaGetLastError();
 }
 

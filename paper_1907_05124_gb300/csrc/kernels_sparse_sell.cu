@@ -34,16 +34,16 @@ namespace {
 // ABI by the fields-only test); saturates to +-1 when 2|x| log2 e overflows.
 __device__ __forceinline__ float tanh_sfu(float x)
 {
-    // tanh(x) = sign(x) (1 - 2 / (1 + 2^{2|x| log2 e})), SFU ex2 and rcp; below
-    // |x| = 1e-3 the odd series x - x^3/3 (error < 2e-16) keeps tiny fields'
-    // signs, which the difference 1 - 2/(1+e) would round away.
+    // tanh(x) = sign(x) (1 - 2 / (1 + 2^{2|x| log2 e})), SFU ex2 and rcp
+    // (absolute error ~6e-8). Below |x| = 4e-3, tanh(x) = x to within
+    // x^3/3 <= 2.2e-8, which also keeps the sign of tiny fields that the
+    // difference 1 - 2/(1+e) would round away.
     const float a = fabsf(x) * 2.8853900817779268f;
     float e, r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(a));
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
     const float big = copysignf(fmaf(-2.0f, r, 1.0f), x);
-    const float small = fmaf(x * x, x * -0.333333343f, x);
-    return fabsf(x) < 1e-3f ? small : big;
+    return fabsf(x) < 4e-3f ? x : big;
 }
 
 template <int RT>
@@ -81,7 +81,8 @@ struct Vec<4> {
 
 // One coupling: (column, weight). Format 0: (column, float bits) pairs;
 // format 1: +-1 words, column | sign << 31; format 2: +-1 halfwords,
-// column | sign << 15, staged in shared memory for the whole kernel.
+// column | sign << 15, staged in shared memory for the whole kernel;
+// format 3: the same halfwords read from global memory through L1.
 template <int FMT>
 struct Entry;
 template <>
@@ -110,6 +111,17 @@ struct Entry<2> {
     __device__ void get(int idx, int& col, float& w) const
     {
         const uint32_t v = e[idx];
+        col = (int)(v & 0x7fffu);
+        w = (v >> 15) ? -1.f : 1.f;
+    }
+};
+
+template <>
+struct Entry<3> {
+    const uint16_t* e;  // the halfword table in global memory, read through L1
+    __device__ void get(int idx, int& col, float& w) const
+    {
+        const uint32_t v = __ldg(e + idx);
         col = (int)(v & 0x7fffu);
         w = (v >> 15) ? -1.f : 1.f;
     }
@@ -157,6 +169,7 @@ __device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, Slot
     const int4* slices = in.slices;
     if constexpr (FMT == 0) ent.e = in.sell_gen;
     if constexpr (FMT == 1) ent.e = in.sell_pm1;
+    if constexpr (FMT == 3) ent.e = in.sell16;
     if constexpr (FMT == 2) {
         // Stage the slice table and the halfword couplings in shared memory,
         // after the magnetisations; they serve every replica this CTA runs.
@@ -385,28 +398,39 @@ __device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, Slot
             if (lane == 0) s_dred[warp][k] = v;
         }
         __syncthreads();
-        if (tid < RT && s_active[tid]) {
-            float dd = 0.f;
-#pragma unroll 8
-            for (int w = 0; w < kWarps; ++w) dd = fmaxf(dd, s_dred[w][tid]);
-            int ls = s_lvl_sweeps[tid] + 1;
-            s_sweeps[tid] += 1;
-            const bool level_done = s.fixed_sweeps > 0 ? ls >= s.fixed_sweeps
-                                                       : (dd <= s.d_min || ls >= s.k_max);
-            if (level_done) {
-                if (s.fixed_sweeps == 0 && !(dd <= s.d_min)) s_capped[tid] += 1;
-                const double T = s_T[tid] - s.c_step;
-                s_T[tid] = T;
-                ls = 0;
-                if (T > 0.0) {
-                    s_levels[tid] += 1;
-                    s_invT[tid] = (float)(1.0 / T);
-                } else {
-                    s_active[tid] = 0;
-                    s_done[tid] = 1;
-                }
+        if (warp == 0) {
+            // the per-warp maxima of each slot, reduced by warp 0's lanes
+            float dk[RT];
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                float v = lane < kWarps ? s_dred[lane][k] : 0.f;
+                dk[k] = warp_reduce_strided<1>(v, MaxOp());
             }
-            s_lvl_sweeps[tid] = ls;
+            if (lane < RT && s_active[lane]) {
+                const int k = lane;
+                float dd = dk[0];
+#pragma unroll
+                for (int q = 1; q < RT; ++q)
+                    if (q == k) dd = dk[q];
+                int ls = s_lvl_sweeps[k] + 1;
+                s_sweeps[k] += 1;
+                const bool level_done = s.fixed_sweeps > 0 ? ls >= s.fixed_sweeps
+                                                           : (dd <= s.d_min || ls >= s.k_max);
+                if (level_done) {
+                    if (s.fixed_sweeps == 0 && !(dd <= s.d_min)) s_capped[k] += 1;
+                    const double T = s_T[k] - s.c_step;
+                    s_T[k] = T;
+                    ls = 0;
+                    if (T > 0.0) {
+                        s_levels[k] += 1;
+                        s_invT[k] = (float)(1.0 / T);
+                    } else {
+                        s_active[k] = 0;
+                        s_done[k] = 1;
+                    }
+                }
+                s_lvl_sweeps[k] = ls;
+            }
         }
         __syncthreads();
     }
@@ -453,6 +477,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_batch_kernel(const 
         __syncthreads();
         const BatchJob& job = s_jobcopy;
         switch (job.fmt) {
+        case 3: run_job<RT, NT, 3>(job.in, job.s, m, S); break;
         case 2: run_job<RT, NT, 2>(job.in, job.s, m, S); break;
         case 1: run_job<RT, NT, 1>(job.in, job.s, m, S); break;
         default: run_job<RT, NT, 0>(job.in, job.s, m, S); break;
@@ -464,7 +489,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_batch_kernel(const 
 template <int RT, int NT, int DEG>
 const void* pick_nt(int fmt)
 {
-    return fmt == 2 ? (const void*)sparse_sell_kernel<RT, NT, 2, DEG>
+    return fmt == 3 ? (const void*)sparse_sell_kernel<RT, NT, 3, DEG>
+         : fmt == 2 ? (const void*)sparse_sell_kernel<RT, NT, 2, DEG>
          : fmt == 1 ? (const void*)sparse_sell_kernel<RT, NT, 1, DEG>
                     : (const void*)sparse_sell_kernel<RT, NT, 0, DEG>;
 }
@@ -536,6 +562,7 @@ bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p)
     if (fmt != 2) {
         while (rt > 1 && m_bytes(rt) > budget) rt /= 2;
         if (m_bytes(rt) > budget) return false;
+        if (in.sell16 && env_int("MARS_SELL_HALF_L1", 1)) fmt = 3;  // halfwords through L1
     }
     p->rt = rt;
     p->onchip = 1;
@@ -605,6 +632,7 @@ bool plan_sparse_batch(const DevInstance* ins, int count, int device, BatchPlan*
         const DevInstance& in = ins[j];
         const size_t table = (size_t)in.nslices * 16 + (size_t)in.sell_len * 2;
         int fmt = in.sell_pm1 ? 1 : 0;
+        if (in.sell16) fmt = 3;
         if (in.sell16 && env_int("MARS_SELL_SMEM_TABLE", 1) && m_bytes(in.n, rt) + table <= budget) fmt = 2;
         fmts[j] = fmt;
         smem = std::max(smem, m_bytes(in.n, rt) + (fmt == 2 ? table : 0));
