@@ -212,7 +212,8 @@ typedef struct {
     int64_t levels;           /* temperature levels over all replicas */
     int64_t capped_levels;    /* levels ended by k_max */
     double gpu_seconds;       /* device time of the solve (CUDA events) */
-    double descent_seconds;   /* device time of the descent kernel alone */
+    double descent_seconds;   /* device time of the descent alone: start states to final
+                                 magnetisations, without the energies and the argmin */
     double energy_err_bound;  /* 0 when energies are exact */
     int32_t status;           /* MARS_OK or the device-side error */
     int32_t integer;          /* 1 if energies are exact integers */
@@ -222,6 +223,9 @@ typedef struct {
     double gemm_seconds;
     int64_t gemm_launches;
     double gemm_flops;
+    /* Kernels mars_solve launched for this result (a captured sweep's graph
+     * nodes counted one by one); 0 from the batch and serving calls. */
+    int64_t kernel_launches;
 } mars_result;
 
 /*
@@ -247,6 +251,44 @@ int mars_solve(mars_ctx* ctx, int32_t inst, const mars_params* params, int8_t* b
  */
 int mars_solve_batch(mars_ctx* ctx, int32_t count, const int32_t* insts, const mars_params* params,
                      int8_t* const* best_spins, mars_result* results);
+
+/*
+ * Launch shape of an instance's solves. The paper has no counterpart: these
+ * knobs choose how the same arithmetic is laid out on the GPU. -1 leaves a
+ * knob to the library's default (or to its MARS_* environment override).
+ *   sell_rt          sparse sliced-ELL kernel: replica slots per CTA, 1|2|4
+ *   sell_threads     threads per CTA, 512|1024
+ *   sell_smem_table  couplings staged in shared memory when they fit, 0|1
+ *   tc_rpw           dense BF16 tensor-core descent: replicas per chain warp, 1|2|4
+ *   tc_overlap       panel p+1's GEMM overlapped with panel p's chain, 0|1
+ * Only tc_overlap changes results: with it, the previous panel's part of a
+ * panel's fields is summed in FP32 instead of through the BF16 GEMM.
+ */
+typedef struct mars_shape {
+    int32_t sell_rt, sell_threads, sell_smem_table;
+    int32_t tc_rpw, tc_overlap;
+} mars_shape;
+
+/* Set (shape non-NULL) or clear (NULL) an instance's launch shape.
+ * Errors: MARS_ENOTFOUND, MARS_EINVAL for a value outside the sets above. */
+int mars_set_shape(mars_ctx* ctx, int32_t inst, const mars_shape* shape);
+int mars_get_shape(mars_ctx* ctx, int32_t inst, mars_shape* out);
+
+/*
+ * Autotuner for batched execution (the launch shape is not in the paper).
+ * Times every candidate shape of the path that params select (sparse
+ * sliced-ELL: slots x threads x table placement; dense BF16: replicas per
+ * warp x overlap) on `repeats` blocking solves with params each, keeps the
+ * fastest descent, stores that shape on the instance for later solves and
+ * returns it in *best (nullable) with its time in *seconds (nullable). A
+ * path with no choices times the default once per repeat. Blocking; the
+ * caller's params drive every trial, so tune on a short schedule (e.g.
+ * fixed_sweeps) when a full solve is long. Errors: as mars_solve, plus
+ * MARS_EINVAL for repeats outside [1, 100]; on error the previous shape
+ * stays.
+ */
+int mars_autotune(mars_ctx* ctx, int32_t inst, const mars_params* params, int32_t repeats,
+                  mars_shape* best, double* seconds);
 
 /*
  * Serving. Requests are solves queued with mars_submit and collected with

@@ -72,6 +72,11 @@ __global__ void __launch_bounds__(128, 1)
     const int split = blockIdx.y;
     const int kb0 = split * g.kblocks;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // K blocks [skip_kb, skip_kb + 2), one 128-spin panel, may be left out;
+    // every thread counts the blocks this split keeps.
+    auto skipped = [&](int kb) { return g.skip_kb >= 0 && kb0 + kb >= g.skip_kb && kb0 + kb < g.skip_kb + 2; };
+    int issued = 0;
+    for (int kb = 0; kb < g.kblocks; ++kb) issued += skipped(kb) ? 0 : 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -89,42 +94,54 @@ __global__ void __launch_bounds__(128, 1)
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
+    if (issued > 0 && warp == 0 && lane == 0) {
         // TMA producer: stage s is free once the MMAs that read it completed.
+        int it = 0;
         for (int kb = 0; kb < g.kblocks; ++kb) {
-            const int s = kb % kStages;
-            if (kb >= kStages && !tc::mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, g.err)) break;
+            if (skipped(kb)) continue;
+            const int s = it % kStages;
+            if (it >= kStages && !tc::mbar_wait(&empty[s], ((it / kStages) - 1) & 1, g.err)) break;
             tc::mbar_arrive_expect_tx(&full[s], L::kA + L::kB);
             tc::tma_load_2d(sA + s * L::kA, &tmJ, &full[s], (kb0 + kb) * kBK, g.p0);
             tc::tma_load_2d(sB + s * L::kB, &tmS, &full[s], (kb0 + kb) * kBK, n0);
+            ++it;
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (issued > 0 && warp == 1 && lane == 0) {
         // MMA issuer: four K=16 steps per stage, accumulator in TMEM.
         constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+        int it = 0;
         for (int kb = 0; kb < g.kblocks; ++kb) {
-            const int s = kb % kStages;
-            if (!tc::mbar_wait(&full[s], (kb / kStages) & 1, g.err)) break;
+            if (skipped(kb)) continue;
+            const int s = it % kStages;
+            if (!tc::mbar_wait(&full[s], (it / kStages) & 1, g.err)) break;
             tc::tc_fence_after();
             const uint32_t a0 = tc::smem_addr(sA + s * L::kA), b0 = tc::smem_addr(sB + s * L::kB);
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k)
                 tc::mma_bf16(tmem, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
-                             idesc, (kb | k) != 0);
+                             idesc, (it | k) != 0);
             tc::mma_commit(&empty[s]);
+            ++it;
         }
         tc::mma_commit(done);
     }
     __syncwarp();
 
-    // Epilogue: TMEM lane = panel row, columns = replica slots.
-    const bool ok = tc::mbar_wait(done, 0, g.err);
+    // Epilogue: TMEM lane = panel row, columns = replica slots. A split
+    // whose K blocks were all left out writes zeros and waits for nothing.
+    const bool ok = issued > 0 ? tc::mbar_wait(done, 0, g.err) : true;
     tc::tc_fence_after();
     const int row = warp * 32 + lane;
     float* dst = g.G + ((size_t)split * g.R_pad + n0) * kBM + row;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
-        tc::tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (issued > 0) {
+            tc::tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        }
         if (ok) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) dst[(size_t)(c0 + j) * kBM] = v[j];
@@ -151,95 +168,172 @@ __device__ __forceinline__ void acc2(float& s, float& c, float a, float b)
     c = __fadd_rn(c, __fadd_rn(e, pe));
 }
 
-// One warp per replica slot: the panel's 128 spins in sequence.
-// Per spin of the panel, what every lane of a replica's warp reads at that
-// spin's step: the low part of its field, its old FP32 and BF16 values and
-// J[a-1][a], the coupling to the spin updated just before it.
+// Per spin of the panel and replica: its field (high and low parts of the
+// compensated sum of the split-K partials, the previous panel's FP32 part
+// and h) and its old FP32 and BF16 values.
 struct ChainSpin {
-    float gc, s_old, s_old_bf, j_prev;
+    float g, gc, s_old, s_old_bf;
 };
 constexpr int kMaxSplit = 8;
-constexpr int kChainSmem = kBM * kBM * (int)sizeof(float) + kChainWarps * kBM * (int)sizeof(ChainSpin);
 
-// The chain with one step of lookahead. Every lane computes the update of the
+// Shared memory of the chain: the FP32 block J[p][p] (and J[p][p+1] when the
+// chain feeds the next panel), the CTA's ChainSpin rows, J[a-1][a] per spin,
+// and the mbarrier of the bulk copies.
+template <int RPW, bool NEXT>
+struct ChainSmem {
+    static constexpr int kJ = kBM * kBM * (int)sizeof(float);
+    static constexpr int kBlocks = NEXT ? 2 : 1;
+    static constexpr int kCs = kChainWarps * RPW * kBM * (int)sizeof(ChainSpin);
+    static constexpr int kBytes = kBlocks * kJ + kCs + kBM * (int)sizeof(float) + 16;
+};
+
+// The panel's spins in sequence for RPW replicas per warp, 32/RPW lanes per
+// replica; lane j of a replica's group owns the spins j + (32/RPW) q.
+//
+// Prologue: one thread starts bulk copies of the J blocks; meanwhile the
+// CTA assembles every field of its replicas with coalesced 16-byte loads.
+//
+// One step of lookahead: every lane of the group computes the update of the
 // current spin a itself, from g_a as it stood before the last change
-// (broadcast during the previous step) plus J[a-1][a] * delta_{a-1}; the
-// lanes that own the panel's other spins fold delta_a into their fields. The
-// broadcast of g_{a+1} thus overlaps the update of spin a, and a step's
-// critical path is one FMA, the tanh and one subtraction, with no shuffle
-// and no divergence. Operations and their order are those of the plain
-// chain (the owner of spin a would apply the same FMAs), so the fields are
-// bit-identical to it.
-__global__ void __launch_bounds__(kChainWarps * 32) panel_chain_kernel(TcState t, int p)
+// (broadcast during the previous step) plus J[a-1][a] * delta_{a-1}, and the
+// owners fold delta_a into the fields of the panel's later spins. The
+// broadcast of g_{a+1} thus overlaps the update of spin a: a step's critical
+// path is one FMA, the tanh and one subtraction, with no divergence.
+// Operations and their order are those of the plain chain (the owner of
+// spin a would apply the same FMAs), so the fields are bit-identical to it.
+//
+// NEXT: the GEMM of the next panel left this panel's K range out, so that it
+// could run beside this chain; each new s_a goes into the next panel's
+// fields here instead, in FP32 (gx_out), from the block J[p][p+1]. Lane j
+// owns next-panel spins 4 (32/RPW) u + 4 j + i, read as float4.
+template <int RPW, bool NEXT>
+__global__ void __launch_bounds__(kChainWarps * 32, 1)
+    panel_chain_kernel(TcState t, int p, const float* __restrict__ G, const float* __restrict__ gx_in,
+                       float* __restrict__ gx_out)
 {
-    extern __shared__ __align__(16) float Jb[];  // FP32 diagonal block of J (symmetric), 64 KB
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float* src = t.Jdiag + (size_t)p * kBM * kBM;
-    for (int i = threadIdx.x; i < kBM * kBM / 4; i += blockDim.x)
-        reinterpret_cast<float4*>(Jb)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
-    ChainSpin* cs = reinterpret_cast<ChainSpin*>(Jb + kBM * kBM) + warp * kBM;
-    __syncthreads();
-    const int slot = blockIdx.x * kChainWarps + warp;
-    if (slot >= t.R || !t.active[slot]) return;
+    using L = ChainSmem<RPW, NEXT>;
+    constexpr int LPR = 32 / RPW, SPL = kBM / LPR, RPC = kChainWarps * RPW;
+    extern __shared__ __align__(16) unsigned char chain_smem[];
+    float* Jb = reinterpret_cast<float*>(chain_smem);  // J[p][p] (symmetric)
+    float* Jn = Jb + kBM * kBM;                         // NEXT: J[p][p+1], row a = this panel's spin
+    ChainSpin* cs_all = reinterpret_cast<ChainSpin*>(chain_smem + L::kBlocks * L::kJ);
+    float* jprev = reinterpret_cast<float*>(chain_smem + L::kBlocks * L::kJ + L::kCs);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(jprev + kBM);
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int slot0 = blockIdx.x * RPC;
     const int p0 = p * kBM;
-    const float invT = t.invT[slot];
-    // Split-K partial fields: every load first, then the compensated sum in
-    // split order, then h.
-    float gp[kMaxSplit][4];
-#pragma unroll
-    for (int sp = 0; sp < kMaxSplit; ++sp)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            gp[sp][q] = sp < t.splitk ? t.G[((size_t)sp * t.R_pad + slot) * kBM + lane + 32 * q] : 0.f;
-    float g[4], sf[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int a = lane + 32 * q;
-        float acc = 0.f, accc = 0.f;
+    const float* Jdiag = t.Jdiag + (size_t)p * kBM * kBM;
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_barrier_init();
+        tc::mbar_arrive_expect_tx(bar, L::kBlocks * L::kJ);
+        tc::bulk_load(Jb, Jdiag, L::kJ, bar);
+        if (NEXT) tc::bulk_load(Jn, t.Jsup + (size_t)p * kBM * kBM, L::kJ, bar);
+    }
+    // The fields of RPC replicas x 128 spins, four spins per thread and pass:
+    // split-K partials in split order, the previous panel's part, then h.
+    for (int e = tid; e < RPC * (kBM / 4); e += blockDim.x) {
+        const int r = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
+        const int sl = slot0 + r < t.R ? slot0 + r : 0;
+        float4 gp[kMaxSplit];
 #pragma unroll
         for (int sp = 0; sp < kMaxSplit; ++sp)
-            if (sp < t.splitk) acc2(acc, accc, gp[sp][q], 1.0f);
-        if (t.h && p0 + a < t.n) acc2(acc, accc, __ldg(t.h + p0 + a), 1.0f);
-        g[q] = acc;
-        const size_t idx = (size_t)slot * t.n_pad + p0 + a;
-        sf[q] = t.S[idx];
-        cs[a] = ChainSpin{accc, sf[q], __bfloat162float(t.Sb[idx]), a > 0 ? Jb[(a - 1) * kBM + a] : 0.f};
+            gp[sp] = sp < t.splitk ? *reinterpret_cast<const float4*>(G + ((size_t)sp * t.R_pad + sl) * kBM + a4)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 gx = gx_in ? *reinterpret_cast<const float4*>(gx_in + (size_t)sl * kBM + a4)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        const size_t idx = (size_t)sl * t.n_pad + p0 + a4;
+        const float4 so = *reinterpret_cast<const float4*>(t.S + idx);
+        const uint2 sbw = *reinterpret_cast<const uint2*>(t.Sb + idx);  // four BF16
+        const float sob[4] = {__uint_as_float(sbw.x << 16), __uint_as_float(sbw.x & 0xffff0000u),
+                              __uint_as_float(sbw.y << 16), __uint_as_float(sbw.y & 0xffff0000u)};
+        const float sof[4] = {so.x, so.y, so.z, so.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float acc = 0.f, accc = 0.f;
+#pragma unroll
+            for (int sp = 0; sp < kMaxSplit; ++sp) {
+                const float v = i == 0 ? gp[sp].x : i == 1 ? gp[sp].y : i == 2 ? gp[sp].z : gp[sp].w;
+                if (sp < t.splitk) acc2(acc, accc, v, 1.0f);
+            }
+            if (gx_in) acc2(acc, accc, i == 0 ? gx.x : i == 1 ? gx.y : i == 2 ? gx.z : gx.w, 1.0f);
+            if (t.h && p0 + a4 + i < t.n) acc2(acc, accc, __ldg(t.h + p0 + a4 + i), 1.0f);
+            cs_all[r * kBM + a4 + i] = ChainSpin{acc, accc, sof[i], sob[i]};
+        }
     }
-    __syncwarp();
-    float ghat = __shfl_sync(0xffffffffu, g[0], 0);
+    if (tid < kBM) jprev[tid] = tid > 0 ? __ldg(Jdiag + (tid - 1) * kBM + tid) : 0.f;
+    if (tid == 0) s_ok = tc::mbar_wait(bar, 0, t.counters + 2) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) return;  // the error flag is set; the host reports it
+
+    const int grp = lane / LPR, j = lane % LPR;
+    const int r = warp * RPW + grp;
+    const int slot = slot0 + r;
+    const bool valid = slot < t.R && t.active[slot];
+    if (!__any_sync(0xffffffffu, valid)) return;  // the whole warp idle
+    const float invT = valid ? t.invT[slot] : 0.f;  // idle groups compute and store nothing
+    const ChainSpin* cs = cs_all + r * kBM;
+    float g[SPL], sf[SPL], gn[NEXT ? SPL : 1];
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+        g[q] = cs[j + LPR * q].g;
+        sf[q] = cs[j + LPR * q].s_old;
+        if (NEXT) gn[q] = 0.f;
+    }
+    const int g0 = grp * LPR;  // the group's first lane
+    float ghat = __shfl_sync(0xffffffffu, g[0], g0);
     // -0 * 0 + ghat == ghat for every ghat, so the first step's FMA is exact
     float dprev = -0.f, dloc = 0.f;
 #pragma unroll
-    for (int qa = 0; qa < 4; ++qa) {
-#pragma unroll 4
-        for (int l = 0; l < 32; ++l) {
-            const int a = qa * 32 + l;
+    for (int qa = 0; qa < SPL; ++qa) {
+#pragma unroll 2
+        for (int l = 0; l < LPR; ++l) {
+            const int a = qa * LPR + l;
             const ChainSpin c = cs[a];
-            const float x = fmaf(c.j_prev, dprev, ghat);
+            const float x = fmaf(jprev[a], dprev, ghat);
             const float sn = -tanh_sfu((x + c.gc) * invT);
             dloc = fmaxf(dloc, fabsf(sn - c.s_old));
             const float delta = sn - c.s_old_bf;
-            if (lane == l) sf[qa] = sn;
+            if (j == l) sf[qa] = sn;
             // g_{a+1} before delta_a reaches it; its owner applies delta_a below
-            const float gsrc = l < 31 ? g[qa] : g[qa < 3 ? qa + 1 : 3];
-            ghat = __shfl_sync(0xffffffffu, gsrc, (l + 1) & 31);
+            const float gsrc = l < LPR - 1 ? g[qa] : g[qa < SPL - 1 ? qa + 1 : SPL - 1];
+            ghat = __shfl_sync(0xffffffffu, gsrc, g0 + (l + 1) % LPR);
             const float* Jrow = Jb + a * kBM;
 #pragma unroll
-            for (int q = qa; q < 4; ++q) g[q] = fmaf(Jrow[lane + 32 * q], delta, g[q]);
+            for (int q = qa; q < SPL; ++q) g[q] = fmaf(Jrow[j + LPR * q], delta, g[q]);
+            if (NEXT) {
+                const float4* Jnr = reinterpret_cast<const float4*>(Jn + a * kBM);
+#pragma unroll
+                for (int u = 0; u < SPL / 4; ++u) {
+                    const float4 w = Jnr[LPR * u + j];
+                    gn[4 * u + 0] = fmaf(w.x, sn, gn[4 * u + 0]);
+                    gn[4 * u + 1] = fmaf(w.y, sn, gn[4 * u + 1]);
+                    gn[4 * u + 2] = fmaf(w.z, sn, gn[4 * u + 2]);
+                    gn[4 * u + 3] = fmaf(w.w, sn, gn[4 * u + 3]);
+                }
+            }
             dprev = delta;
         }
     }
+    if (!valid) return;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int a = lane + 32 * q;
+    for (int q = 0; q < SPL; ++q) {
+        const int a = j + LPR * q;
         if (p0 + a < t.n) {
             const size_t idx = (size_t)slot * t.n_pad + p0 + a;
             t.S[idx] = sf[q];
             t.Sb[idx] = __float2bfloat16_rn(sf[q]);
         }
     }
-    // every lane computed every spin's change, so dloc is the warp's maximum
-    if (lane == 0) t.d[slot] = fmaxf(t.d[slot], dloc);
+    if (NEXT) {
+#pragma unroll
+        for (int u = 0; u < SPL / 4; ++u)
+            *reinterpret_cast<float4*>(gx_out + (size_t)slot * kBM + 4 * (LPR * u + j)) =
+                make_float4(gn[4 * u], gn[4 * u + 1], gn[4 * u + 2], gn[4 * u + 3]);
+    }
+    // every lane of the group computed every spin's change: dloc is the replica's maximum
+    if (j == 0) t.d[slot] = fmaxf(t.d[slot], dloc);
 }
 
 // Start states in slot order: slot j holds replica rep[j].
@@ -398,14 +492,37 @@ cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS,
     return cudaLaunchKernel(k, dim3(n_tiles, splitk), dim3(128), args, smem, st);
 }
 
-cudaError_t launch_tc_chain(const TcState& t, int p, cudaStream_t st)
+template <int RPW, bool NEXT>
+cudaError_t launch_chain_as(const TcState& t, int p, const float* G, const float* gx_in, float* gx_out,
+                            cudaStream_t st)
+{
+    constexpr int smem = ChainSmem<RPW, NEXT>::kBytes;
+    cudaError_t e = cudaFuncSetAttribute(panel_chain_kernel<RPW, NEXT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int per_cta = kChainWarps * RPW;
+    panel_chain_kernel<RPW, NEXT><<<(t.R + per_cta - 1) / per_cta, kChainWarps * 32, smem, st>>>(
+        t, p, G, gx_in, gx_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, const float* gx_in,
+                            float* gx_out, cudaStream_t st)
 {
     if (t.splitk < 1 || t.splitk > kMaxSplit) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(panel_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kChainSmem);
-    if (e != cudaSuccess) return e;
-    panel_chain_kernel<<<(t.R + kChainWarps - 1) / kChainWarps, kChainWarps * 32, kChainSmem, st>>>(t, p);
-    return cudaGetLastError();
+    // the CTA's slots must lie inside G's R_pad rows (R_pad is a multiple of 128)
+    if (t.R_pad % (kChainWarps * rpw) != 0) return cudaErrorInvalidValue;
+    const bool next = gx_out != nullptr;
+    if (next && !t.Jsup) return cudaErrorInvalidValue;
+    switch (rpw * 2 + (next ? 1 : 0)) {
+    case 2: return launch_chain_as<1, false>(t, p, G, gx_in, gx_out, st);
+    case 3: return launch_chain_as<1, true>(t, p, G, gx_in, gx_out, st);
+    case 4: return launch_chain_as<2, false>(t, p, G, gx_in, gx_out, st);
+    case 5: return launch_chain_as<2, true>(t, p, G, gx_in, gx_out, st);
+    case 8: return launch_chain_as<4, false>(t, p, G, gx_in, gx_out, st);
+    case 9: return launch_chain_as<4, true>(t, p, G, gx_in, gx_out, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tc_init(const TcState& t, cudaStream_t st)

@@ -535,7 +535,8 @@ int env_int(const char* name, int dflt)
 // RT=2 with 1024 threads 3.46e11; RT=1/1024 2.63e11; RT=4/1024 2.64e11;
 // the 512-thread shapes 2.0-2.2e11. Wider CTAs give a lone replica's sweep
 // more threads; two slots amortise the coupling loads without the 4-wide
-// tail. MARS_SELL_RT / MARS_SELL_THREADS override the choice for tuning.
+// tail. The instance's launch shape (mars_autotune, mars_set_shape), else
+// MARS_SELL_RT / MARS_SELL_THREADS / MARS_SELL_SMEM_TABLE, override it.
 bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p)
 {
     if (!in.slices || (!in.sell_pm1 && !in.sell_gen)) return false;
@@ -543,15 +544,17 @@ bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     const size_t budget = (size_t)optin - 12 * 1024;  // static shared memory and slack
-    int rt = env_int("MARS_SELL_RT", 2);
-    int nt = env_int("MARS_SELL_THREADS", 1024);
+    const LaunchShape& sh = in.shape;
+    int rt = sh.sell_rt >= 0 ? sh.sell_rt : env_int("MARS_SELL_RT", 2);
+    int nt = sh.sell_threads >= 0 ? sh.sell_threads : env_int("MARS_SELL_THREADS", 1024);
+    const int smem_table = sh.sell_smem_table >= 0 ? sh.sell_smem_table : env_int("MARS_SELL_SMEM_TABLE", 1);
     if (rt != 1 && rt != 2 && rt != 4) rt = 1;
     if (nt != 512 && nt != 1024) nt = 512;
     auto m_bytes = [&](int c) { return align16((size_t)(in.n + 1) * c * sizeof(float)); };
     const size_t table = (size_t)in.nslices * 16 + (size_t)in.sell_len * 2;
     // Halfword couplings staged on chip when they fit beside the magnetisations.
     int fmt = in.sell_pm1 ? 1 : 0;
-    if (in.sell16 && env_int("MARS_SELL_SMEM_TABLE", 1)) {
+    if (in.sell16 && smem_table) {
         int c = rt;
         while (c > 1 && m_bytes(c) + table > budget) c /= 2;
         if (m_bytes(c) + table <= budget) {

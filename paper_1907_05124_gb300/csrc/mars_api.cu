@@ -11,8 +11,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <numeric>
@@ -56,7 +58,7 @@ struct mars_ctx {
     std::string err = "no error";
     std::map<int32_t, std::unique_ptr<Instance>> insts;
     int32_t next_id = 1;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;  // ev3: end of the descent
     std::vector<cudaEvent_t> prof;  // event pairs around sampled panel GEMM launches
     ~mars_ctx()
     {
@@ -353,6 +355,7 @@ bool encode_bf16_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t o
 struct TcProfile {
     double gemm_seconds = 0.0, gemm_flops = 0.0;
     int64_t gemm_launches = 0;
+    int64_t launches = 0;  // every kernel of the descent, graph nodes counted one by one
 };
 
 // One dense tensor-core descent in flight: its device state, tensor maps and
@@ -371,12 +374,31 @@ struct TcRun {
     // as a CUDA graph and replayed: 2P+2 launches become one graph launch.
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // Replicas per warp in the chain, and the overlap of panel p+1's GEMM
+    // with panel p's chain: the GEMMs run on `side`, the chains on the run's
+    // stream, ordered by the events ev (fork, then per panel GEMM done and
+    // chain done). G and the chains' next-panel fields Gx alternate between
+    // two buffers by panel parity.
+    int rpw = 1;
+    bool overlap = false;
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> ev;
+    float* Gbuf[2] = {nullptr, nullptr};
+    float* Gx[2] = {nullptr, nullptr};
     ~TcRun()
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (side) cudaStreamDestroy(side);
     }
 };
+
+int env_flag(const char* name, int dflt)
+{
+    const char* v = std::getenv(name);
+    return v && *v ? std::atoi(v) : dflt;
+}
 
 constexpr int kTcBN = 128;
 
@@ -397,12 +419,21 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     while (splitk < 8 && run->ntiles * splitk * 2 <= c->sms && (n_pad / 64) % (splitk * 2) == 0)
         splitk *= 2;
     run->splitk = splitk;
+    // Replicas per chain warp: several per warp cut the chain's issued
+    // instructions per replica and leave SMs to the overlapped GEMM.
+    const LaunchShape& sh = d.shape;
+    int rpw = sh.tc_rpw >= 0 ? sh.tc_rpw : env_flag("MARS_TC_RPW", R >= 1024 ? 4 : R >= 256 ? 2 : 1);
+    if (rpw != 1 && rpw != 2 && rpw != 4) rpw = 1;
+    run->rpw = rpw;
+    const int ov = sh.tc_overlap >= 0 ? sh.tc_overlap : env_flag("MARS_TC_OVERLAP", 1);
+    run->overlap = run->P >= 2 && ov != 0;
     t.R = R;
     t.R_pad = R_pad;
     t.n = n;
     t.n_pad = n_pad;
     t.splitk = splitk;
     t.Jdiag = d.Jdiag;
+    t.Jsup = d.Jsup;
     t.h = d.h;
     t.new2old = d.new2old;
     t.m0 = s.m0;
@@ -416,7 +447,19 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     t.rep = rep_dev;
     if ((rc = get((size_t)R * n_pad * sizeof(float), (void**)&t.S))) return rc;
     if ((rc = get((size_t)R_pad * n_pad * sizeof(__nv_bfloat16), (void**)&t.Sb))) return rc;
-    if ((rc = get((size_t)splitk * R_pad * 128 * sizeof(float), (void**)&t.G))) return rc;
+    const size_t g_floats = (size_t)splitk * R_pad * 128;
+    if ((rc = get(2 * g_floats * sizeof(float), (void**)&t.G))) return rc;
+    run->Gbuf[0] = t.G;
+    run->Gbuf[1] = t.G + g_floats;
+    if (run->overlap) {
+        float* gx = nullptr;
+        if ((rc = get(2 * (size_t)R_pad * 128 * sizeof(float), (void**)&gx))) return rc;
+        run->Gx[0] = gx;
+        run->Gx[1] = gx + (size_t)R_pad * 128;
+        MARS_CUDA(c, cudaStreamCreateWithFlags(&run->side, cudaStreamNonBlocking));
+        run->ev.resize(1 + 2 * (size_t)run->P, nullptr);
+        for (cudaEvent_t& e : run->ev) MARS_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     if ((rc = get((size_t)R * sizeof(double), (void**)&t.T))) return rc;
     if ((rc = get((size_t)R * sizeof(float), (void**)&t.invT))) return rc;
     if ((rc = get((size_t)R * sizeof(float), (void**)&t.d))) return rc;
@@ -447,14 +490,36 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
 }
 
 // One sweep as direct launches; with `timed`, event pairs bracket each GEMM.
+// With the overlap, panel p's GEMM (on the side stream) leaves panel p-1's
+// K range out and waits only for chain p-2, whose G buffer it overwrites;
+// chain p waits for GEMM p and takes panel p-1's part of its fields from
+// chain p-1 (Gx).
 int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
 {
-    for (int pp = 0; pp < run->P; ++pp) {
-        run->g.p0 = pp * 128;
-        if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp], st));
-        MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, run->g, kTcBN, run->ntiles, run->splitk, st));
-        if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp + 1], st));
-        MARS_CUDA(c, launch_tc_chain(run->t, pp, st));
+    const bool ov = run->overlap;
+    const int P = run->P;
+    cudaStream_t gs = ov ? run->side : st;
+    if (ov) {
+        MARS_CUDA(c, cudaEventRecord(run->ev[0], st));
+        MARS_CUDA(c, cudaStreamWaitEvent(gs, run->ev[0], 0));
+    }
+    for (int pp = 0; pp < P; ++pp) {
+        TcPanel g = run->g;
+        g.p0 = pp * 128;
+        g.G = run->Gbuf[pp & 1];
+        g.skip_kb = ov && pp > 0 ? 2 * (pp - 1) : -1;
+        if (ov && pp >= 2) MARS_CUDA(c, cudaStreamWaitEvent(gs, run->ev[2 + 2 * (pp - 2)], 0));
+        if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp], gs));
+        MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->ntiles, run->splitk, gs));
+        if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp + 1], gs));
+        if (ov) {
+            MARS_CUDA(c, cudaEventRecord(run->ev[1 + 2 * pp], gs));
+            MARS_CUDA(c, cudaStreamWaitEvent(st, run->ev[1 + 2 * pp], 0));
+        }
+        const float* gx_in = ov && pp > 0 ? run->Gx[pp & 1] : nullptr;
+        float* gx_out = ov && pp + 1 < P ? run->Gx[(pp + 1) & 1] : nullptr;
+        MARS_CUDA(c, launch_tc_chain(run->t, pp, run->rpw, run->Gbuf[pp & 1], gx_in, gx_out, st));
+        if (ov) MARS_CUDA(c, cudaEventRecord(run->ev[2 + 2 * pp], st));
     }
     MARS_CUDA(c, launch_tc_advance(run->t, st));
     return MARS_OK;
@@ -529,6 +594,7 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
         return r;
     };
     if ((rc = tc_setup(c, in->dev, s, rep, t0_max, st, get, &run))) return rc;
+    prof->launches += 2;  // start states, active prefix
     int32_t* pinned = nullptr;
     MARS_CUDA(c, cudaMallocHost((void**)&pinned, 4 * sizeof(int32_t)));
     run.h_counters = pinned;
@@ -541,6 +607,7 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     while (state == 1) {
         const int32_t active_now = run.active_at_batch;
         if ((rc = tc_enqueue_batch(c, &run, st))) { cudaFreeHost(pinned); return rc; }
+        prof->launches += (int64_t)run.batch * (2 * run.P + 2);  // per sweep: P GEMMs, P chains, level step
         se = cudaStreamSynchronize(st);
         if (se != cudaSuccess) break;
         for (int pp = 0; pp < run.P; ++pp) {
@@ -555,7 +622,9 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     cudaFreeHost(pinned);
     if (se != cudaSuccess) return fail(c, MARS_EDEVICE, "CUDA error: %s", cudaGetErrorString(se));
     if (state < 0) return state;
+    if (!polish) MARS_CUDA(c, cudaEventRecord(c->ev3, st));
     MARS_CUDA(c, launch_tc_finalize(run.t, in->dev, s, st));
+    prof->launches += 1;
     if (polish) {
         // FP32 polish: the SIMT dense path re-converges each replica's last
         // level from its BF16 final state; it writes the spins and energies.
@@ -573,6 +642,8 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
         DensePlan dp = plan_dense(in->dev, s.R, 0, c->device);
         if (dp.scratch_floats && (rc = S.get(dp.scratch_floats, &ps.m_scratch))) return rc;
         MARS_CUDA(c, launch_dense(in->dev, ps, dp, st));
+        MARS_CUDA(c, cudaEventRecord(c->ev3, st));
+        prof->launches += 2;
     }
     return MARS_OK;
 }
@@ -953,7 +1024,7 @@ int mars_create(mars_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_
     }
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
-        cudaEventCreate(&c->ev2) != cudaSuccess)
+        cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess)
         return MARS_EDEVICE;
     *out = c.release();
     return MARS_OK;
@@ -972,6 +1043,7 @@ void mars_destroy(mars_ctx* c)
         if (c->ev0) cudaEventDestroy(c->ev0);
         if (c->ev1) cudaEventDestroy(c->ev1);
         if (c->ev2) cudaEventDestroy(c->ev2);
+        if (c->ev3) cudaEventDestroy(c->ev3);
         if (c->own_stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -1047,17 +1119,20 @@ int mars_instance_dense(mars_ctx* c, int32_t n, const void* J, int32_t jt, const
         hd.resize(n);
         for (int32_t a = 0; a < n; ++a) { hf[a] = (float)hh[o[a]]; hd[a] = hh[o[a]]; }
     }
-    // Tensor-core operands: BF16 J padded to whole 128-spin panels, and the
-    // panels' FP32 diagonal blocks for the in-panel sequential updates.
+    // Tensor-core operands: BF16 J padded to whole 128-spin panels, the
+    // panels' FP32 diagonal blocks for the in-panel sequential updates, and
+    // the FP32 blocks J[p][p+1] through which a chain feeds the next panel.
     const int32_t n_pad = (n + 127) / 128 * 128;
     std::vector<uint16_t> Jb((size_t)n_pad * n_pad, 0);
-    std::vector<float> Jdiag((size_t)n_pad * 128, 0.f);
+    std::vector<float> Jdiag((size_t)n_pad * 128, 0.f), Jsup((size_t)n_pad * 128, 0.f);
     for (int32_t a = 0; a < n; ++a)
         for (int32_t b = 0; b < n; ++b) {
             const float v = Jf[(size_t)a * n + b];
             Jb[(size_t)a * n_pad + b] = float_to_bf16_bits(v);
             if (a / 128 == b / 128)
                 Jdiag[((size_t)(a / 128) * 128 + a % 128) * 128 + b % 128] = v;
+            else if (b / 128 == a / 128 + 1)
+                Jsup[((size_t)(a / 128) * 128 + a % 128) * 128 + b % 128] = v;
         }
     DevInstance& d = in->dev;
     d.n = n;
@@ -1072,6 +1147,7 @@ int mars_instance_dense(mars_ctx* c, int32_t n, const void* J, int32_t jt, const
         if ((rc = upload(c, in.get(), Jb, &jb))) return rc;
         d.Jbf = (const __nv_bfloat16*)jb;
         if ((rc = upload(c, in.get(), Jdiag, &d.Jdiag))) return rc;
+        if ((rc = upload(c, in.get(), Jsup, &d.Jsup))) return rc;
     }
     if ((rc = upload(c, in.get(), Jf, &d.Jf))) return rc;
     if ((rc = upload(c, in.get(), Ji, &d.J_i8))) return rc;
@@ -1371,6 +1447,7 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     const bool odev = outs && (outs->flags & MARS_DEVICE_PTR);
     Scratch S(c);
     int rc;
+    int64_t launches = 0;  // kernels this solve launches
     DevSolve s;
     s.R = R;
     s.seed = p->seed;
@@ -1395,6 +1472,7 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     } else {
         MARS_CUDA(c, launch_draw(p->seed, p->stream, 0, R, 0, p->t_min, p->t_max, nullptr, t0, st));
         MARS_CUDA(c, cudaMemcpyAsync(t0h.data(), t0, R * sizeof(float), cudaMemcpyDeviceToHost, st));
+        ++launches;
     }
     for (float v : t0h)
         if (!std::isfinite(v) || v / p->c_step > kMaxLevels)
@@ -1476,16 +1554,24 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
             return rc;
     } else if (in->dev.dense) {
         MARS_CUDA(c, launch_dense(in->dev, s, dp, st));
+        MARS_CUDA(c, cudaEventRecord(c->ev3, st));
+        ++launches;
     } else {
         if (sp.sell)
             MARS_CUDA(c, launch_sparse_sell(in->dev, s, sp, st));
         else
             MARS_CUDA(c, launch_sparse(in->dev, s, sp, st));
+        MARS_CUDA(c, cudaEventRecord(c->ev3, st));
+        ++launches;
     }
-    if (!in->dev.integer && in->dev.exact_ok)  // replace the kernels' FP64 sums by exact ones
+    launches += tcprof.launches;
+    if (!in->dev.integer && in->dev.exact_ok) {  // replace the kernels' FP64 sums by exact ones
         MARS_CUDA(c, launch_energy(in->dev, s.sigma, R, s.energy, nullptr, s.status, st));
+        ++launches;
+    }
     MARS_CUDA(c, cudaEventRecord(c->ev2, st));
     MARS_CUDA(c, launch_best(s, n, in->dev.integer, dbest, dres, st));
+    ++launches;
     MARS_CUDA(c, cudaEventRecord(c->ev1, st));
     DevResult hres;
     int32_t hstatus = 0;
@@ -1507,7 +1593,7 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     MARS_CUDA(c, cudaStreamSynchronize(st));
     float ms = 0.f, ms_descent = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    cudaEventElapsedTime(&ms_descent, c->ev0, c->ev2);
+    cudaEventElapsedTime(&ms_descent, c->ev0, c->ev3);
     if (hstatus != kDevOk) return fail(c, MARS_EDEVICE, "device status %d", hstatus);
     if (result) {
         std::memset(result, 0, sizeof *result);
@@ -1526,6 +1612,7 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
         result->gemm_seconds = tcprof.gemm_seconds;
         result->gemm_launches = tcprof.gemm_launches;
         result->gemm_flops = tcprof.gemm_flops;
+        result->kernel_launches = launches;
         result->integer = in->dev.integer;
         result->energy_err_bound = (in->dev.integer || in->dev.exact_ok)
                                        ? 0.0
@@ -1677,6 +1764,98 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
                                   : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + dins[j].n);
         r->status = MARS_OK;
     }
+    return MARS_OK;
+}
+
+int mars_set_shape(mars_ctx* c, int32_t id, const mars_shape* shape)
+{
+    if (!c) return MARS_EINVAL;
+    Instance* in = find(c, id);
+    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    LaunchShape sh;
+    if (shape) {
+        auto in_set = [](int32_t v, std::initializer_list<int32_t> allowed) {
+            if (v == -1) return true;
+            for (int32_t a : allowed)
+                if (v == a) return true;
+            return false;
+        };
+        if (!in_set(shape->sell_rt, {1, 2, 4}) || !in_set(shape->sell_threads, {512, 1024}) ||
+            !in_set(shape->sell_smem_table, {0, 1}) || !in_set(shape->tc_rpw, {1, 2, 4}) ||
+            !in_set(shape->tc_overlap, {0, 1}))
+            return fail(c, MARS_EINVAL, "launch shape value outside its allowed set");
+        sh.sell_rt = shape->sell_rt;
+        sh.sell_threads = shape->sell_threads;
+        sh.sell_smem_table = shape->sell_smem_table;
+        sh.tc_rpw = shape->tc_rpw;
+        sh.tc_overlap = shape->tc_overlap;
+    }
+    in->dev.shape = sh;
+    return MARS_OK;
+}
+
+int mars_get_shape(mars_ctx* c, int32_t id, mars_shape* out)
+{
+    if (!c || !out) return MARS_EINVAL;
+    Instance* in = find(c, id);
+    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    const LaunchShape& sh = in->dev.shape;
+    *out = mars_shape{sh.sell_rt, sh.sell_threads, sh.sell_smem_table, sh.tc_rpw, sh.tc_overlap};
+    return MARS_OK;
+}
+
+int mars_autotune(mars_ctx* c, int32_t id, const mars_params* p, int32_t repeats, mars_shape* best,
+                  double* seconds)
+{
+    if (!c || !p) return MARS_EINVAL;
+    Instance* in = find(c, id);
+    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
+    if (repeats < 1 || repeats > 100) return fail(c, MARS_EINVAL, "repeats must be in [1, 100]");
+    const DevInstance& d = in->dev;
+    std::vector<LaunchShape> cands;
+    if (d.dense && p->precision == MARS_BF16) {
+        for (int ov = 1; ov >= 0; --ov)
+            for (int rpw : {1, 2, 4}) {
+                LaunchShape sh;
+                sh.tc_rpw = rpw;
+                sh.tc_overlap = ov;
+                cands.push_back(sh);
+            }
+    } else if (!d.dense && p->update == MARS_UPDATE_GS && d.slices && (d.sell_pm1 || d.sell_gen)) {
+        for (int tab = 1; tab >= (d.sell16 ? 0 : 1); --tab)
+            for (int nt : {1024, 512})
+                for (int rt : {1, 2, 4}) {
+                    LaunchShape sh;
+                    sh.sell_rt = rt;
+                    sh.sell_threads = nt;
+                    sh.sell_smem_table = tab;
+                    cands.push_back(sh);
+                }
+    }
+    if (cands.empty()) cands.push_back(d.shape);  // nothing to choose: time the current shape
+    const LaunchShape saved = d.shape;
+    LaunchShape win = saved;
+    double best_t = INFINITY;
+    for (const LaunchShape& sh : cands) {
+        in->dev.shape = sh;
+        double t = INFINITY;
+        for (int r = 0; r < repeats; ++r) {
+            mars_result res{};
+            const int rc = mars_solve(c, id, p, nullptr, nullptr, &res);
+            if (rc != MARS_OK) {
+                in->dev.shape = saved;
+                return rc;
+            }
+            t = std::min(t, res.descent_seconds);
+        }
+        if (t < best_t) {
+            best_t = t;
+            win = sh;
+        }
+    }
+    in->dev.shape = win;
+    if (best) *best = mars_shape{win.sell_rt, win.sell_threads, win.sell_smem_table, win.tc_rpw, win.tc_overlap};
+    if (seconds) *seconds = best_t;
     return MARS_OK;
 }
 

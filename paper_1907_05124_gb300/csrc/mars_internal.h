@@ -13,6 +13,15 @@ enum DeviceStatus : int32_t { kDevOk = 0, kDevBadIndex = 1 };
 
 // Instance data on the device, relabelled so that one sweep is "levels in
 // order, any order within a level": new label a has caller label new2old[a].
+// Launch-shape choices of an instance's solves, set by mars_autotune or
+// mars_set_shape; -1 leaves a knob to its MARS_* environment override, else
+// to the built-in default. None changes a replica's arithmetic except
+// tc_overlap, which takes the previous panel's part of the fields in FP32.
+struct LaunchShape {
+    int32_t sell_rt = -1, sell_threads = -1, sell_smem_table = -1;
+    int32_t tc_rpw = -1, tc_overlap = -1;
+};
+
 struct DevInstance {
     int32_t n = 0;
     int32_t dense = 0;
@@ -39,6 +48,8 @@ struct DevInstance {
     int32_t n_pad = 0;                   // n rounded up to the 128-spin panel
     const __nv_bfloat16* Jbf = nullptr;  // n_pad*n_pad BF16, zero padded (tensor-core operand)
     const float* Jdiag = nullptr;        // (n_pad/128) FP32 128x128 diagonal blocks
+    const float* Jsup = nullptr;         // (n_pad/128) FP32 128x128 blocks J[p][p+1] (last: zero)
+    LaunchShape shape;                   // host-side choice; kernels ignore it
     const float* Jf = nullptr;
     const int8_t* J_i8 = nullptr;
     const double* J_f64 = nullptr;
@@ -137,6 +148,7 @@ struct TcPanel {
     int32_t kblocks = 0;     // 64-wide K blocks per split
     int32_t R_pad = 0;
     float* G = nullptr;      // [split][R_pad][128]
+    int32_t skip_kb = -1;    // first of two 64-wide K blocks left out (-1: none)
     const int32_t* active_prefix = nullptr;
     int32_t* err = nullptr;
 };
@@ -146,6 +158,7 @@ struct TcState {
     float* S = nullptr;            // [R][n_pad] FP32 magnetisations, slot order
     __nv_bfloat16* Sb = nullptr;   // [R_pad][n_pad] BF16 shadow (tensor-core operand)
     const float* Jdiag = nullptr;
+    const float* Jsup = nullptr;       // [P][128][128] FP32 blocks J[p][p+1]
     const float* h = nullptr;
     const int32_t* rep = nullptr;      // slot -> replica
     const int32_t* new2old = nullptr;
@@ -169,7 +182,12 @@ struct TcState {
 size_t tc_gemm_smem(int bn);
 cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g,
                                  int bn, int n_tiles, int splitk, cudaStream_t st);
-cudaError_t launch_tc_chain(const TcState& t, int p, cudaStream_t st);
+// In-panel chain of panel p for rpw (1, 2 or 4) replicas per warp, on the
+// split-K fields G; gx_in (nullable) holds the previous panel's FP32 part
+// of the fields, and with gx_out (nullable) the chain writes this panel's
+// part of the next panel's fields there.
+cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, const float* gx_in,
+                            float* gx_out, cudaStream_t st);
 cudaError_t launch_tc_init(const TcState& t, cudaStream_t st);
 cudaError_t launch_tc_advance(const TcState& t, cudaStream_t st);
 cudaError_t launch_tc_prefix(const TcState& t, cudaStream_t st);

@@ -62,7 +62,7 @@ class Result(ctypes.Structure):
                 ("energy_err_bound", ctypes.c_double),
                 ("status", ctypes.c_int32), ("integer", ctypes.c_int32),
                 ("gemm_seconds", ctypes.c_double), ("gemm_launches", ctypes.c_int64),
-                ("gemm_flops", ctypes.c_double)]
+                ("gemm_flops", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
 
 
 class InstanceInfo(ctypes.Structure):
@@ -73,6 +73,13 @@ class InstanceInfo(ctypes.Structure):
 
 # Every symbol include/mars.h declares, with its ctypes signature.
 P = ctypes.c_void_p
+class Shape(ctypes.Structure):
+    """mars_shape: an instance's launch shape (-1 = library default)."""
+    _fields_ = [("sell_rt", ctypes.c_int32), ("sell_threads", ctypes.c_int32),
+                ("sell_smem_table", ctypes.c_int32), ("tc_rpw", ctypes.c_int32),
+                ("tc_overlap", ctypes.c_int32)]
+
+
 SIGNATURES = {
     "mars_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t, P]),
     "mars_destroy": (None, [P]),
@@ -97,6 +104,9 @@ SIGNATURES = {
     "mars_submit": (ctypes.c_int, [P, ctypes.c_int32, P, P]),
     "mars_poll": (ctypes.c_int, [P, ctypes.c_int64, P, P]),
     "mars_serve_status": (ctypes.c_int, [P, P, P]),
+    "mars_set_shape": (ctypes.c_int, [P, ctypes.c_int32, P]),
+    "mars_get_shape": (ctypes.c_int, [P, ctypes.c_int32, P]),
+    "mars_autotune": (ctypes.c_int, [P, ctypes.c_int32, P, ctypes.c_int32, P, P]),
 }
 
 _lib = None
@@ -170,6 +180,7 @@ class SolveResult:
     gemm_seconds: float = 0.0
     gemm_launches: int = 0
     gemm_flops: float = 0.0
+    kernel_launches: int = 0
     energies: np.ndarray | None = None
     spins: np.ndarray | None = None
     m_final: np.ndarray | None = None
@@ -332,10 +343,47 @@ class Context:
             descent_seconds=res.descent_seconds,
             energy_err_bound=res.energy_err_bound, integer=bool(res.integer), best_spins=best,
             gemm_seconds=res.gemm_seconds, gemm_launches=res.gemm_launches,
-            gemm_flops=res.gemm_flops,
+            gemm_flops=res.gemm_flops, kernel_launches=res.kernel_launches,
             energies=keep.get("energies"), spins=keep.get("spins"), m_final=keep.get("m_final"),
             t0=keep.get("t0"), replica_sweeps=keep.get("sweeps"),
             replica_levels=keep.get("levels"), replica_capped=keep.get("capped"))
+
+    # -- launch shape and autotuner -------------------------------------------
+    def set_shape(self, inst: int, **shape):
+        """mars_set_shape: sell_rt, sell_threads, sell_smem_table, tc_rpw,
+        tc_overlap (omitted = -1, the default); no keywords clears the shape."""
+        unknown = set(shape) - {k for k, _ in Shape._fields_}
+        if unknown:
+            raise ValueError(f"unknown launch-shape keys {sorted(unknown)}")
+        if not shape:
+            self._check(self._lib.mars_set_shape(self._ctx, int(inst), None))
+            return
+        sh = Shape(*[int(shape.get(k, -1)) for k, _ in Shape._fields_])
+        self._check(self._lib.mars_set_shape(self._ctx, int(inst), ctypes.byref(sh)))
+
+    def get_shape(self, inst: int) -> dict:
+        sh = Shape()
+        self._check(self._lib.mars_get_shape(self._ctx, int(inst), ctypes.byref(sh)))
+        return {k: getattr(sh, k) for k, _ in Shape._fields_}
+
+    def autotune(self, inst: int, replicas: int, t_min: float, t_max: float, *, repeats=3,
+                 c_step=1.0, d_min=1e-4, k_max=1000, fixed_sweeps=0, seed=0, stream=0,
+                 update="gs", precision="fp32", m0=None, t0=None):
+        """mars_autotune with these solve parameters (host m0/t0 only).
+        Returns (shape dict stored on the instance, fastest descent seconds)."""
+        p = Params()
+        self._lib.mars_params_default(ctypes.byref(p))
+        p.replicas, p.t_min, p.t_max, p.c_step, p.d_min = int(replicas), t_min, t_max, c_step, d_min
+        p.k_max, p.fixed_sweeps, p.seed, p.stream = int(k_max), int(fixed_sweeps), int(seed), int(stream)
+        p.update, p.precision = UPDATE[update], PRECISION[precision]
+        pm, km, dm = _arr(None if m0 is None else np.asarray(m0, np.float32), np.float32)
+        pt, kt, dt_ = _arr(None if t0 is None else np.asarray(t0, np.float32), np.float32)
+        p.m0, p.t0 = pm, pt
+        sh = Shape()
+        sec = ctypes.c_double()
+        self._check(self._lib.mars_autotune(self._ctx, int(inst), ctypes.byref(p), int(repeats),
+                                            ctypes.byref(sh), ctypes.byref(sec)))
+        return {k: getattr(sh, k) for k, _ in Shape._fields_}, sec.value
 
     def solve_batch(self, jobs):
         """mars_solve_batch over [(inst, replicas, t_min, t_max, kwargs), ...].

@@ -1,0 +1,105 @@
+"""mars_autotune and the per-instance launch shape.
+
+A launch shape lays the same per-replica arithmetic out differently on the
+GPU (slots per CTA, threads, where the couplings live, replicas per chain
+warp), so every sparse shape and every replicas-per-warp choice must return
+bit-identical results; only the dense overlap changes rounding (the previous
+panel's part of the fields in FP32), and its results stay exact in energy.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1907_05124_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_05124_gb300 import build, mars
+    build.build()
+    c = mars.Context(0)
+    yield c
+    c.close()
+
+
+def _same(a, b):
+    assert a.best_energy == b.best_energy and a.best_replica == b.best_replica
+    assert a.sweeps == b.sweeps and a.levels == b.levels
+    assert np.array_equal(a.energies, b.energies)
+    assert np.array_equal(a.best_spins, b.best_spins)
+
+
+def test_sparse_autotune_picks_a_shape_and_keeps_results(ctx):
+    g = I.ea_lattice(40, 2, 21)
+    inst = ctx.add_csr(*g)
+    ref = ctx.solve(inst, 300, 0.0, 4.0, seed=3)
+    shape, sec = ctx.autotune(inst, 300, 0.0, 4.0, seed=3, repeats=1)
+    assert sec > 0
+    assert shape["sell_rt"] in (1, 2, 4) and shape["sell_threads"] in (512, 1024)
+    assert shape["sell_smem_table"] in (0, 1)
+    assert ctx.get_shape(inst) == shape
+    _same(ctx.solve(inst, 300, 0.0, 4.0, seed=3), ref)
+    for rt in (1, 2, 4):
+        for nt in (512, 1024):
+            for tab in (0, 1):
+                ctx.set_shape(inst, sell_rt=rt, sell_threads=nt, sell_smem_table=tab)
+                _same(ctx.solve(inst, 300, 0.0, 4.0, seed=3), ref)
+    ctx.set_shape(inst)
+    assert set(ctx.get_shape(inst).values()) == {-1}
+    assert ref.best_energy == O.energy(O.Instance.csr(g), ref.best_spins)
+    ctx.free(inst)
+
+
+def test_dense_autotune_and_replicas_per_warp(ctx):
+    n, R = 384, 160
+    J = I.sk_pm1(n, 22)
+    inst = ctx.add_dense(J)
+    m0, t0 = I.replica_inputs(R, n, 0.0, 24.0, 23)
+    kw = dict(m0=m0, t0=t0, precision="bf16", fixed_sweeps=2, c_step=4.0)
+    shape, sec = ctx.autotune(inst, R, 0.0, 24.0, repeats=1, **kw)
+    assert shape["tc_rpw"] in (1, 2, 4) and shape["tc_overlap"] in (0, 1)
+    oi = O.Instance.dense(J)
+    for ov in (0, 1):
+        runs = []
+        for rpw in (1, 2, 4):
+            ctx.set_shape(inst, tc_rpw=rpw, tc_overlap=ov)
+            runs.append(ctx.solve(inst, R, 0.0, 24.0, outputs=("energies", "spins"), **kw))
+        for r in runs[1:]:
+            _same(r, runs[0])
+        assert np.array_equal(runs[0].energies, O.energies(oi, runs[0].spins))
+    ctx.free(inst)
+
+
+def test_shape_validation(ctx):
+    from paper_1907_05124_gb300.mars import MarsError
+    inst = ctx.add_csr(*I.ea_lattice(6, 2, 0))
+    with pytest.raises(MarsError):
+        ctx.set_shape(inst, sell_rt=3)
+    with pytest.raises(MarsError):
+        ctx.set_shape(inst, tc_rpw=8)
+    with pytest.raises(ValueError):
+        ctx.set_shape(inst, tiles=2)
+    with pytest.raises(MarsError):
+        ctx.autotune(inst, 8, 0.0, 4.0, repeats=0)
+    assert set(ctx.get_shape(inst).values()) == {-1}
+    ctx.free(inst)
+
+
+def test_kernel_launch_count(ctx):
+    inst = ctx.add_csr(*I.ea_lattice(10, 2, 1))
+    r = ctx.solve(inst, 16, 0.0, 4.0, seed=0)
+    assert r.kernel_launches == 3  # draw, descent, argmin
+    ctx.free(inst)
+    n = 256
+    d = ctx.add_dense(I.sk_pm1(n, 2))
+    m0, _ = I.replica_inputs(8, n, 0.0, 1.5, 3)
+    t0 = np.full(8, 1.5, np.float32)  # one level (T = 0.5) of three sweeps for every replica
+    r = ctx.solve(d, 8, 0.0, 1.5, m0=m0, t0=t0, precision="bf16", fixed_sweeps=3)
+    # 2 setup kernels, 3 sweeps of (2 panels x {GEMM, chain} + level step + prefix), finalize, argmin
+    assert r.kernel_launches == 2 + 3 * (2 * 2 + 2) + 1 + 1
+    ctx.free(d)

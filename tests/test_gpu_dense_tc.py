@@ -166,3 +166,71 @@ def test_fp32_polish_leaves_fixed_points(ctx):
     assert checked >= R // 2
     assert np.array_equal(g.energies, O.energies(O.Instance.dense(J), g.spins))
     ctx.free(inst)
+
+
+def block_tridiagonal_pm1(n, seed, block=128):
+    rng = np.random.default_rng(seed)
+    u = np.triu(rng.choice(np.array([-1.0, 1.0]), size=(n, n)), 1)
+    b = np.arange(n) // block
+    u *= np.abs(b[:, None] - b[None, :]) <= 1
+    return u + u.T
+
+
+@pytest.mark.parametrize("n,R", [(640, 256), (600, 72)])
+def test_overlapped_panels_block_tridiagonal(ctx, monkeypatch, n, R):
+    """Panel p+1's GEMM leaves panel p out and runs beside panel p's chain,
+    which adds panel p's new spins to panel p+1's fields in FP32.
+
+    With J block-tridiagonal in 128-spin blocks (+-1 inside) and BF16-exact
+    start states, every field of the first sweep is then assembled from exact
+    BF16 products (old spins) and FP32 products (the previous panel's new
+    spins), so in the contracting regime (one level, T in [50, 54), above the
+    spectral edge 2 sqrt(3 * 128) = 39) one sweep equals the FP64 sweep to
+    1e-5. The plain sweep, which passes the previous panel's new spins through
+    the BF16 GEMM, misses that bar (an FP64 emulation of it errs by 2e-4), so
+    the test also shows that the overlapped path ran. The chain must give
+    bit-identical results for 1, 2 and 4 replicas per warp.
+    """
+    J = block_tridiagonal_pm1(n, 3)
+    inst = ctx.add_dense(J)
+    m0 = bf16_exact_m0(R, n, 5)
+    t0 = np.random.default_rng(6).uniform(110.0, 114.0, size=R).astype(np.float32)
+    oi = O.Instance.dense(J)
+    o = O.mars_solve(oi, m0, t0, c_step=60.0, fixed_sweeps=1)
+    assert np.all(o["levels"] == 1)
+    kw = dict(c_step=60.0, fixed_sweeps=1, m0=m0, t0=t0, precision="bf16",
+              outputs=("m_final", "energies", "spins"))
+    monkeypatch.setenv("MARS_TC_OVERLAP", "0")
+    plain = ctx.solve(inst, R, float(t0.min()), float(t0.max()), **kw)
+    assert np.abs(plain.m_final - o["m"]).max() > 1e-5
+    monkeypatch.setenv("MARS_TC_OVERLAP", "1")
+    runs = {}
+    for rpw in (1, 2, 4):
+        monkeypatch.setenv("MARS_TC_RPW", str(rpw))
+        runs[rpw] = ctx.solve(inst, R, float(t0.min()), float(t0.max()), **kw)
+    err = np.abs(runs[1].m_final - o["m"]).max()
+    assert err <= 1e-5, err
+    for rpw in (2, 4):
+        assert np.array_equal(runs[rpw].m_final, runs[1].m_final), rpw
+        assert np.array_equal(runs[rpw].energies, runs[1].energies)
+    assert np.array_equal(runs[1].energies, O.energies(oi, runs[1].spins))
+    ctx.free(inst)
+
+
+def test_overlap_and_plain_sweeps_reach_the_same_quality(ctx, monkeypatch):
+    """The overlapped sweep (previous panel in FP32) and the plain one (all of
+    J through the BF16 GEMM) are two roundings of the same method: on an SK
+    instance both return exact energies and best energies within 1 % of the
+    oracle's."""
+    n, R = 512, 256
+    J = I.sk_pm1(n, 12)
+    inst = ctx.add_dense(J)
+    m0, t0 = I.replica_inputs(R, n, 0.0, 48.0, 13)
+    oi = O.Instance.dense(J)
+    o = O.mars_solve(oi, m0, t0, nthreads=8, want_m=False)
+    for ov in ("0", "1"):
+        monkeypatch.setenv("MARS_TC_OVERLAP", ov)
+        g = ctx.solve(inst, R, 0.0, 48.0, m0=m0, t0=t0, precision="bf16", outputs=("energies", "spins"))
+        assert np.array_equal(g.energies, O.energies(oi, g.spins))
+        assert abs(g.best_energy - o["energy"].min()) <= 0.01 * abs(o["energy"].min()), ov
+    ctx.free(inst)
