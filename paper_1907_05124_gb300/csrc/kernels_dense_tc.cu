@@ -152,55 +152,42 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) tc::tmem_dealloc(tmem, BN);
 }
 
-// Compensated accumulate: (s, c) += a * b with the product's and the sum's
-// rounding errors carried in c (TwoProduct by FMA, TwoSum; Ogita, Rump,
-// Oishi 2005). Used where a panel's field is assembled from its split-K
-// partial sums and the field h. The in-panel corrections use plain FMAs:
-// beside a BF16 GEMM their FP32 rounding is immaterial.
-__device__ __forceinline__ void acc2(float& s, float& c, float a, float b)
-{
-    const float p = __fmul_rn(a, b);
-    const float pe = __fmaf_rn(a, b, -p);
-    const float t = __fadd_rn(s, p);
-    const float z = __fsub_rn(t, s);
-    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(e, pe));
-}
-
-// Per spin of the panel and replica: its field (high and low parts of the
-// compensated sum of the split-K partials, the previous panel's FP32 part
-// and h) and its old FP32 and BF16 values.
+// Per spin of the panel and replica: its field (the split-K partials in
+// split order, the previous panel's FP32 part and h, summed in FP32: beside
+// the BF16 products their rounding is immaterial, and BF16-exact operands
+// sum exactly) and its old FP32 and BF16 values.
 struct ChainSpin {
-    float g, gc, s_old, s_old_bf;
+    float g, s_old, s_old_bf, unused;
 };
-constexpr int kMaxSplit = 8;
 
 // Shared memory of the chain: the FP32 block J[p][p] (and J[p][p+1] when the
-// chain feeds the next panel), the CTA's ChainSpin rows, J[a-1][a] per spin,
-// and the mbarrier of the bulk copies.
+// chain feeds the next panel), the CTA's ChainSpin rows and the mbarrier of
+// the bulk copies.
 template <int RPW, bool NEXT>
 struct ChainSmem {
     static constexpr int kJ = kBM * kBM * (int)sizeof(float);
     static constexpr int kBlocks = NEXT ? 2 : 1;
     static constexpr int kCs = kChainWarps * RPW * kBM * (int)sizeof(ChainSpin);
-    static constexpr int kBytes = kBlocks * kJ + kCs + kBM * (int)sizeof(float) + 16;
+    static constexpr int kBytes = kBlocks * kJ + kCs + 16;
 };
 
 // The panel's spins in sequence for RPW replicas per warp, 32/RPW lanes per
 // replica; lane j of a replica's group owns the spins j + (32/RPW) q.
 //
-// Prologue: one thread starts bulk copies of the J blocks; meanwhile the
-// CTA assembles every field of its replicas with coalesced 16-byte loads.
+// Prologue: one thread starts bulk copies of the J blocks; meanwhile every
+// thread issues all loads for its RPW four-spin pieces of the CTA's fields
+// (at most kChainMaxSplit / RPW split-K partials each) in one round trip.
 //
 // One step of lookahead: every lane of the group computes the update of the
 // current spin a itself, from g_a as it stood before the last change
 // (broadcast during the previous step) plus J[a-1][a] * delta_{a-1}, and the
 // owners fold delta_a into the fields of the panel's later spins. The
-// broadcast of g_{a+1} thus overlaps the update of spin a: a step's critical
-// path is one FMA, the tanh and one subtraction, with no divergence.
-// Operations and their order are those of the plain chain (the owner of
-// spin a would apply the same FMAs), so the fields are bit-identical to it.
+// broadcast of g_{a+1} thus overlaps the update of spin a, and with the
+// constants of the step folded (below) a step's critical path is one FMA,
+// ex2, one add, rcp, one FMA and two selects, with no divergence. The
+// owners' FMAs are those of the plain chain in its order; the folding
+// reassociates the last term of each field, an FP32 rounding difference.
+// Every replicas-per-warp choice computes bit-identical results.
 //
 // NEXT: the GEMM of the next panel left this panel's K range out, so that it
 // could run beside this chain; each new s_a goes into the next panel's
@@ -213,66 +200,85 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
 {
     using L = ChainSmem<RPW, NEXT>;
     constexpr int LPR = 32 / RPW, SPL = kBM / LPR, RPC = kChainWarps * RPW;
+    constexpr int kSplitCap = kChainMaxSplit / RPW;
     extern __shared__ __align__(16) unsigned char chain_smem[];
     float* Jb = reinterpret_cast<float*>(chain_smem);  // J[p][p] (symmetric)
     float* Jn = Jb + kBM * kBM;                         // NEXT: J[p][p+1], row a = this panel's spin
     ChainSpin* cs_all = reinterpret_cast<ChainSpin*>(chain_smem + L::kBlocks * L::kJ);
-    float* jprev = reinterpret_cast<float*>(chain_smem + L::kBlocks * L::kJ + L::kCs);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(jprev + kBM);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(chain_smem + L::kBlocks * L::kJ + L::kCs);
     __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int slot0 = blockIdx.x * RPC;
     const int p0 = p * kBM;
-    const float* Jdiag = t.Jdiag + (size_t)p * kBM * kBM;
-    if (tid == 0) {
-        tc::mbar_init(bar, 1);
-        tc::fence_barrier_init();
-        tc::mbar_arrive_expect_tx(bar, L::kBlocks * L::kJ);
-        tc::bulk_load(Jb, Jdiag, L::kJ, bar);
-        if (NEXT) tc::bulk_load(Jn, t.Jsup + (size_t)p * kBM * kBM, L::kJ, bar);
-    }
-    // The fields of RPC replicas x 128 spins, four spins per thread and pass:
-    // split-K partials in split order, the previous panel's part, then h.
-    for (int e = tid; e < RPC * (kBM / 4); e += blockDim.x) {
-        const int r = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
-        const int sl = slot0 + r < t.R ? slot0 + r : 0;
-        float4 gp[kMaxSplit];
-#pragma unroll
-        for (int sp = 0; sp < kMaxSplit; ++sp)
-            gp[sp] = sp < t.splitk ? *reinterpret_cast<const float4*>(G + ((size_t)sp * t.R_pad + sl) * kBM + a4)
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 gx = gx_in ? *reinterpret_cast<const float4*>(gx_in + (size_t)sl * kBM + a4)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-        const size_t idx = (size_t)sl * t.n_pad + p0 + a4;
-        const float4 so = *reinterpret_cast<const float4*>(t.S + idx);
-        const uint2 sbw = *reinterpret_cast<const uint2*>(t.Sb + idx);  // four BF16
-        const float sob[4] = {__uint_as_float(sbw.x << 16), __uint_as_float(sbw.x & 0xffff0000u),
-                              __uint_as_float(sbw.y << 16), __uint_as_float(sbw.y & 0xffff0000u)};
-        const float sof[4] = {so.x, so.y, so.z, so.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float acc = 0.f, accc = 0.f;
-#pragma unroll
-            for (int sp = 0; sp < kMaxSplit; ++sp) {
-                const float v = i == 0 ? gp[sp].x : i == 1 ? gp[sp].y : i == 2 ? gp[sp].z : gp[sp].w;
-                if (sp < t.splitk) acc2(acc, accc, v, 1.0f);
-            }
-            if (gx_in) acc2(acc, accc, i == 0 ? gx.x : i == 1 ? gx.y : i == 2 ? gx.z : gx.w, 1.0f);
-            if (t.h && p0 + a4 + i < t.n) acc2(acc, accc, __ldg(t.h + p0 + a4 + i), 1.0f);
-            cs_all[r * kBM + a4 + i] = ChainSpin{acc, accc, sof[i], sob[i]};
-        }
-    }
-    if (tid < kBM) jprev[tid] = tid > 0 ? __ldg(Jdiag + (tid - 1) * kBM + tid) : 0.f;
-    if (tid == 0) s_ok = tc::mbar_wait(bar, 0, t.counters + 2) ? 1 : 0;
-    __syncthreads();
-    if (!s_ok) return;  // the error flag is set; the host reports it
-
     const int grp = lane / LPR, j = lane % LPR;
     const int r = warp * RPW + grp;
     const int slot = slot0 + r;
     const bool valid = slot < t.R && t.active[slot];
-    if (!__any_sync(0xffffffffu, valid)) return;  // the whole warp idle
     const float invT = valid ? t.invT[slot] : 0.f;  // idle groups compute and store nothing
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_barrier_init();
+        tc::mbar_arrive_expect_tx(bar, L::kBlocks * L::kJ);
+        tc::bulk_load(Jb, t.Jdiag + (size_t)p * kBM * kBM, L::kJ, bar);
+        if (NEXT) tc::bulk_load(Jn, t.Jsup + (size_t)p * kBM * kBM, L::kJ, bar);
+    }
+    // RPC replicas x 32 four-spin pieces = RPW pieces per thread.
+    static_assert(RPC * (kBM / 4) == RPW * kChainWarps * 32, "one piece per thread and replica slot");
+    float4 part[RPW][kSplitCap], gx[RPW], so[RPW];
+    uint2 sbw[RPW];
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int e = tid + k * kChainWarps * 32;
+        const int rr = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
+        const int sl = slot0 + rr < t.R ? slot0 + rr : 0;
+#pragma unroll
+        for (int sp = 0; sp < kSplitCap; ++sp)
+            part[k][sp] = sp < t.splitk
+                              ? *reinterpret_cast<const float4*>(G + ((size_t)sp * t.R_pad + sl) * kBM + a4)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        gx[k] = gx_in ? *reinterpret_cast<const float4*>(gx_in + (size_t)sl * kBM + a4)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        const size_t idx = (size_t)sl * t.n_pad + p0 + a4;
+        so[k] = *reinterpret_cast<const float4*>(t.S + idx);
+        sbw[k] = *reinterpret_cast<const uint2*>(t.Sb + idx);  // four BF16
+    }
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int e = tid + k * kChainWarps * 32;
+        const int rr = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
+        float4 f = part[k][0];
+#pragma unroll
+        for (int sp = 1; sp < kSplitCap; ++sp) {
+            if (sp < t.splitk) {
+                f.x += part[k][sp].x;
+                f.y += part[k][sp].y;
+                f.z += part[k][sp].z;
+                f.w += part[k][sp].w;
+            }
+        }
+        if (gx_in) {
+            f.x += gx[k].x;
+            f.y += gx[k].y;
+            f.z += gx[k].z;
+            f.w += gx[k].w;
+        }
+        if (t.h) {
+            const int a = p0 + a4;
+            if (a + 0 < t.n) f.x += __ldg(t.h + a + 0);
+            if (a + 1 < t.n) f.y += __ldg(t.h + a + 1);
+            if (a + 2 < t.n) f.z += __ldg(t.h + a + 2);
+            if (a + 3 < t.n) f.w += __ldg(t.h + a + 3);
+        }
+        ChainSpin* d = cs_all + rr * kBM + a4;
+        d[0] = ChainSpin{f.x, so[k].x, __uint_as_float(sbw[k].x << 16), 0.f};
+        d[1] = ChainSpin{f.y, so[k].y, __uint_as_float(sbw[k].x & 0xffff0000u), 0.f};
+        d[2] = ChainSpin{f.z, so[k].z, __uint_as_float(sbw[k].y << 16), 0.f};
+        d[3] = ChainSpin{f.w, so[k].w, __uint_as_float(sbw[k].y & 0xffff0000u), 0.f};
+    }
+    if (tid == 0) s_ok = tc::mbar_wait(bar, 0, t.counters + 2) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) return;  // the error flag is set; the host reports it
+    if (!__any_sync(0xffffffffu, valid)) return;  // the whole warp idle
     const ChainSpin* cs = cs_all + r * kBM;
     float g[SPL], sf[SPL], gn[NEXT ? SPL : 1];
 #pragma unroll
@@ -282,26 +288,49 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
         if (NEXT) gn[q] = 0.f;
     }
     const int g0 = grp * LPR;  // the group's first lane
-    float ghat = __shfl_sync(0xffffffffu, g[0], g0);
-    // -0 * 0 + ghat == ghat for every ghat, so the first step's FMA is exact
-    float dprev = -0.f, dloc = 0.f;
+    // The step's argument in ex2 units, z_a = 2 log2(e) y_a with
+    // y_a = (g_a + J[a-1][a] (s_{a-1} - sb_{a-1})) / T, is one FMA of the
+    // previous step's new s: z_a = cz_a s_{a-1} + bz_a, where
+    // cz_a = K J[a-1][a] / T and bz_a = K (g_a - J[a-1][a] sb_{a-1}) / T are
+    // formed while the previous step's tanh is in flight.
+    constexpr float kK = 2.8853900817779268f;     // 2 log2(e)
+    constexpr float kKinv = 0.34657359027997264f;  // 1 / K
+    constexpr float kSmallZ = 4e-3f * kK;          // |y| < 4e-3: tanh(y) = y to 2.2e-8
+    const float kinv = kK * invT;
+    ChainSpin c = cs[0];
+    float cz = 0.f;  // J[-1][0] = 0
+    float bz = kinv * __shfl_sync(0xffffffffu, g[0], g0);
+    float snprev = 0.f, dloc = 0.f;
 #pragma unroll
     for (int qa = 0; qa < SPL; ++qa) {
 #pragma unroll 2
         for (int l = 0; l < LPR; ++l) {
             const int a = qa * LPR + l;
-            const ChainSpin c = cs[a];
-            const float x = fmaf(jprev[a], dprev, ghat);
-            const float sn = -tanh_sfu((x + c.gc) * invT);
-            dloc = fmaxf(dloc, fabsf(sn - c.s_old));
-            const float delta = sn - c.s_old_bf;
-            if (j == l) sf[qa] = sn;
-            // g_{a+1} before delta_a reaches it; its owner applies delta_a below
+            const int an = a + 1 < kBM ? a + 1 : a;
+            // What does not wait for this step's tanh: the broadcast of
+            // g_{a+1} (before delta_a reaches it; its owner applies delta_a
+            // below), the next step's operands and this step's J row.
             const float gsrc = l < LPR - 1 ? g[qa] : g[qa < SPL - 1 ? qa + 1 : SPL - 1];
-            ghat = __shfl_sync(0xffffffffu, gsrc, g0 + (l + 1) % LPR);
+            const float ghat_n = __shfl_sync(0xffffffffu, gsrc, g0 + (l + 1) % LPR);
+            const ChainSpin c_n = cs[an];
+            const float jp_n = Jb[a * kBM + an];  // J[a][a+1]
             const float* Jrow = Jb + a * kBM;
+            float jr[SPL];
 #pragma unroll
-            for (int q = qa; q < SPL; ++q) g[q] = fmaf(Jrow[j + LPR * q], delta, g[q]);
+            for (int q = qa; q < SPL; ++q) jr[q] = Jrow[j + LPR * q];
+            // The critical path: s_a = -tanh(y_a) = -sign(z) (1 - 2 / (1 + 2^|z|)),
+            // SFU ex2 and rcp; -y_a itself below |y| = 4e-3.
+            const float z = fmaf(cz, snprev, bz);
+            float e, rc;
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fabsf(z)));
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rc) : "f"(1.0f + e));
+            const float big = copysignf(fmaf(-2.0f, rc, 1.0f), -z);
+            const float sn = fabsf(z) < kSmallZ ? -kKinv * z : big;
+            const float delta = sn - c.s_old_bf;
+            dloc = fmaxf(dloc, fabsf(sn - c.s_old));
+            if (j == l) sf[qa] = sn;
+#pragma unroll
+            for (int q = qa; q < SPL; ++q) g[q] = fmaf(jr[q], delta, g[q]);
             if (NEXT) {
                 const float4* Jnr = reinterpret_cast<const float4*>(Jn + a * kBM);
 #pragma unroll
@@ -313,7 +342,10 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
                     gn[4 * u + 3] = fmaf(w.w, sn, gn[4 * u + 3]);
                 }
             }
-            dprev = delta;
+            cz = kinv * jp_n;
+            bz = kinv * fmaf(-jp_n, c.s_old_bf, ghat_n);
+            snprev = sn;
+            c = c_n;
         }
     }
     if (!valid) return;
@@ -509,7 +541,7 @@ cudaError_t launch_chain_as(const TcState& t, int p, const float* G, const float
 cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, const float* gx_in,
                             float* gx_out, cudaStream_t st)
 {
-    if (t.splitk < 1 || t.splitk > kMaxSplit) return cudaErrorInvalidValue;
+    if (t.splitk < 1 || t.splitk > kChainMaxSplit / rpw) return cudaErrorInvalidValue;
     // the CTA's slots must lie inside G's R_pad rows (R_pad is a multiple of 128)
     if (t.R_pad % (kChainWarps * rpw) != 0) return cudaErrorInvalidValue;
     const bool next = gx_out != nullptr;

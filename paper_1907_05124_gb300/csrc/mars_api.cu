@@ -414,19 +414,29 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     const int32_t R_pad = (R + kTcBN - 1) / kTcBN * kTcBN;
     run->P = n_pad / 128;
     run->ntiles = R_pad / kTcBN;
-    // Split K until the panel GEMM fills the SMs in one wave (one CTA per SM).
-    int splitk = 1;
-    while (splitk < 8 && run->ntiles * splitk * 2 <= c->sms && (n_pad / 64) % (splitk * 2) == 0)
-        splitk *= 2;
-    run->splitk = splitk;
     // Replicas per chain warp: several per warp cut the chain's issued
-    // instructions per replica and leave SMs to the overlapped GEMM.
+    // instructions per replica and leave SMs to the overlapped GEMM. The
+    // defaults are the fastest shapes measured on a GB300 at N = 8192 (ms per
+    // sweep): R = 1024, overlap with 2 per warp 1.04 (plain sweep, 1 per warp,
+    // 1.26); R = 4096, plain sweep with 4 per warp 2.06 (overlap 2.51: the
+    // chain and the GEMM then compete for SMs). mars_autotune picks per
+    // instance.
     const LaunchShape& sh = d.shape;
-    int rpw = sh.tc_rpw >= 0 ? sh.tc_rpw : env_flag("MARS_TC_RPW", R >= 1024 ? 4 : R >= 256 ? 2 : 1);
+    int rpw = sh.tc_rpw >= 0 ? sh.tc_rpw : env_flag("MARS_TC_RPW", R >= 2048 ? 4 : R >= 512 ? 2 : 1);
     if (rpw != 1 && rpw != 2 && rpw != 4) rpw = 1;
     run->rpw = rpw;
-    const int ov = sh.tc_overlap >= 0 ? sh.tc_overlap : env_flag("MARS_TC_OVERLAP", 1);
+    const int ov = sh.tc_overlap >= 0 ? sh.tc_overlap
+                                      : env_flag("MARS_TC_OVERLAP", R >= 512 && R < 2048 ? 1 : 0);
     run->overlap = run->P >= 2 && ov != 0;
+    // Split K until the panel GEMM fills the SMs in one wave (one CTA per SM):
+    // a short GEMM is bound by each CTA's pipeline fill and TMA bytes in
+    // flight, so more, shorter CTAs finish sooner.
+    int splitk = 1;
+    const int split_max = env_flag("MARS_TC_SPLITK_MAX", 16);
+    while (splitk < split_max && splitk * 2 <= kChainMaxSplit / rpw && run->ntiles * splitk * 2 <= c->sms &&
+           (n_pad / 64) % (splitk * 2) == 0)
+        splitk *= 2;
+    run->splitk = splitk;
     t.R = R;
     t.R_pad = R_pad;
     t.n = n;

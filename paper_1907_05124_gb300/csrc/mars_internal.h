@@ -182,6 +182,9 @@ struct TcState {
 size_t tc_gemm_smem(int bn);
 cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g,
                                  int bn, int n_tiles, int splitk, cudaStream_t st);
+// Split-K partials a chain with one replica per warp sums; with rpw replicas
+// per warp the split must not exceed kChainMaxSplit / rpw.
+constexpr int kChainMaxSplit = 16;
 // In-panel chain of panel p for rpw (1, 2 or 4) replicas per warp, on the
 // split-K fields G; gx_in (nullable) holds the previous panel's FP32 part
 // of the fields, and with gx_out (nullable) the chain writes this panel's
