@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip mars_autotune before the warm-up (library default launch shape)")
     ap.add_argument("--workload", default="ea2d", choices=["ea2d", "sk8192", "serve"],
                     help="ea2d: the 2-D lattice (default); sk8192: dense SK on tensor cores; "
                          "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
@@ -275,6 +277,16 @@ class Workload:
     def add(self, ctx):
         return ctx.add_csr(*self.csr) if self.csr is not None else ctx.add_dense(self.J)
 
+    def autotune(self, ctx, inst):
+        """mars_autotune on this workload's replicas: the full solve for the
+        lattice (milliseconds), a two-level fixed-sweep schedule for the dense
+        instance (its full solve takes minutes). Untimed, before the warm-up."""
+        if self.csr is not None:
+            return ctx.autotune(inst, self.R, T_MIN, self.t_max, repeats=2, c_step=self.c_step,
+                                d_min=D_MIN, k_max=K_MAX, seed=7, stream=self.rank)
+        return ctx.autotune(inst, self.R, 0.0, 2.0 * self.c_step, repeats=1, c_step=self.c_step,
+                            fixed_sweeps=4, seed=7, stream=self.rank, precision=self.precision)
+
     def solve(self, ctx, inst, seed):
         return ctx.solve(inst, self.R, T_MIN, self.t_max, c_step=self.c_step, d_min=D_MIN,
                          k_max=K_MAX, seed=seed, stream=self.rank, precision=self.precision,
@@ -302,6 +314,10 @@ def run_mars(args, world, rank, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     stream = ctx.torch_stream  # the stream every library call is ordered on
 
+    shape = None
+    if not args.no_autotune:
+        shape, _ = wl.autotune(ctx, inst)
+        wl.config = dict(wl.config, launch_shape=shape, launch_shape_by="mars_autotune")
     for w in range(max(args.warmup, 0)):
         wl.solve(ctx, inst, 10_000 + w)
     if world > 1:
@@ -311,7 +327,7 @@ def run_mars(args, world, rank, local):
     sampler.start()
     time.sleep(0.3)
     step_ms, descent_s, updates, best = [], [], 0, []
-    gemm_s, gemm_flops, gemm_launches = 0.0, 0.0, 0
+    gemm_s, gemm_flops, gemm_launches, launches = 0.0, 0.0, 0, 0
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()  # L2 flush between timed steps, outside the events
@@ -328,6 +344,7 @@ def run_mars(args, world, rank, local):
         gemm_s += res.gemm_seconds
         gemm_flops += res.gemm_flops
         gemm_launches += res.gemm_launches
+        launches += res.kernel_launches
     clocks = sampler.stop()
     torch.cuda.synchronize()
     tot_ms = sum(step_ms)
@@ -346,6 +363,8 @@ def run_mars(args, world, rank, local):
         torch.cuda.synchronize()
         t = time.perf_counter()
         i2 = wl.add(ctx)
+        if shape is not None:
+            ctx.set_shape(i2, **shape)
         r2 = wl.solve(ctx, i2, k)
         ctx.free(i2)
         e2e_t += time.perf_counter() - t
@@ -365,11 +384,21 @@ def run_mars(args, world, rank, local):
         # retires 32 ex2 or 16 rcp per clock (measured with a throughput
         # microbenchmark), i.e. 1 / (1/32 + 1/16) = 10.67 updates per clock.
         sfu_updates_per_clk = 1.0 / (1.0 / 32.0 + 1.0 / 16.0)
+        sh = shape or {}
+        rt_used = sh.get("sell_rt", -1) if sh.get("sell_rt", -1) > 0 else 2
+        nt_used = sh.get("sell_threads", -1) if sh.get("sell_threads", -1) > 0 else 1024
+        tab_used = sh.get("sell_smem_table", -1) != 0
         achieved = upd_per_launch / d_mean
         peak = 152 * sfu_updates_per_clk * sm_clock_ghz * 1e9
+        # DRAM bytes per launch (read + write) from one ncu capture of the
+        # default shape (2 slots, 1024 threads, table in shared memory); null
+        # for another shape, whose counters were not taken.
+        default_shape = rt_used == 2 and nt_used == 1024 and tab_used
+        traffic = 1.012480e6 + 8.192e3 if default_shape else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
-                    "unit": "spin-updates/s (SFU-bound)", "frac": achieved / peak, "traffic": None,
-                    "kernel": "sparse_sell_kernel<RT=2, 1024 threads, halfword couplings, degree 4>",
+                    "unit": "spin-updates/s (SFU-bound)", "frac": achieved / peak, "traffic": traffic,
+                    "kernel": "sparse_sell_kernel<RT={}, {} threads, halfword couplings{}, degree 4>".format(
+                        rt_used, nt_used, " in shared memory" if tab_used else " through L1"),
                     "peak_source": "152 SMs x (1/32 + 1/16 SFU clocks per tanh)^-1 x SM clock",
                     "descent_ms_mean": 1e3 * d_mean}
     else:
@@ -393,7 +422,7 @@ def run_mars(args, world, rank, local):
                            parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
             "e2e": {"value": e2e_u / e2e_t, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": 3 * args.steps if wl.name == "ea2d" else None,
+            "gpu_launches": launches,
             "roofline": roofline,
             "cpu_baseline": base,
             "clocks": clocks,
