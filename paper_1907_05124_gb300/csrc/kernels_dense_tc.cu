@@ -21,12 +21,13 @@
 #include "tc_primitives.cuh"
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 namespace mars {
 namespace {
 
 constexpr int kBM = 128;     // panel rows = MMA M
-constexpr int kBK = 64;      // K per pipeline stage: one 128-byte swizzle row of BF16
+constexpr int kBK = 64;      // K per pipeline stage: one 128-byte swizzle row of BF16 (128 of E4M3)
 constexpr int kStages = 4;
 constexpr int kChainWarps = 8;
 
@@ -52,12 +53,16 @@ struct GemmSmem {
 };
 
 // G_part[split][slot][a] = sum over this split's K range of J[p0 + a][k] S[slot][k].
-template <int BN>
+// FP8: E4M3 operands (kind::f8f6f4); a stage's 128-byte rows then hold 128
+// K values instead of 64, and a 128-spin panel is one K block instead of two.
+template <int BN, bool FP8>
 __global__ void __launch_bounds__(128, 1)
     panel_gemm_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmS,
                       TcPanel g)
 {
     using L = GemmSmem<BN>;
+    constexpr int kKE = FP8 ? 2 * kBK : kBK;  // K values per stage
+    constexpr int kSkipN = kBM / kKE;         // K blocks of one panel
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
@@ -74,7 +79,9 @@ __global__ void __launch_bounds__(128, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // K blocks [skip_kb, skip_kb + 2), one 128-spin panel, may be left out;
     // every thread counts the blocks this split keeps.
-    auto skipped = [&](int kb) { return g.skip_kb >= 0 && kb0 + kb >= g.skip_kb && kb0 + kb < g.skip_kb + 2; };
+    auto skipped = [&](int kb) {
+        return g.skip_kb >= 0 && kb0 + kb >= g.skip_kb && kb0 + kb < g.skip_kb + kSkipN;
+    };
     int issued = 0;
     for (int kb = 0; kb < g.kblocks; ++kb) issued += skipped(kb) ? 0 : 1;
 
@@ -102,13 +109,14 @@ __global__ void __launch_bounds__(128, 1)
             const int s = it % kStages;
             if (it >= kStages && !tc::mbar_wait(&empty[s], ((it / kStages) - 1) & 1, g.err)) break;
             tc::mbar_arrive_expect_tx(&full[s], L::kA + L::kB);
-            tc::tma_load_2d(sA + s * L::kA, &tmJ, &full[s], (kb0 + kb) * kBK, g.p0);
-            tc::tma_load_2d(sB + s * L::kB, &tmS, &full[s], (kb0 + kb) * kBK, n0);
+            tc::tma_load_2d(sA + s * L::kA, &tmJ, &full[s], (kb0 + kb) * kKE, g.p0);
+            tc::tma_load_2d(sB + s * L::kB, &tmS, &full[s], (kb0 + kb) * kKE, n0);
             ++it;
         }
     } else if (issued > 0 && warp == 1 && lane == 0) {
-        // MMA issuer: four K=16 steps per stage, accumulator in TMEM.
-        constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+        // MMA issuer: four 32-byte K steps per stage (K = 16 BF16 or 32 E4M3),
+        // accumulator in TMEM.
+        constexpr uint32_t idesc = FP8 ? tc::idesc_e4m3_f32(kBM, BN) : tc::idesc_bf16_f32(kBM, BN);
         int it = 0;
         for (int kb = 0; kb < g.kblocks; ++kb) {
             if (skipped(kb)) continue;
@@ -117,9 +125,14 @@ __global__ void __launch_bounds__(128, 1)
             tc::tc_fence_after();
             const uint32_t a0 = tc::smem_addr(sA + s * L::kA), b0 = tc::smem_addr(sB + s * L::kB);
 #pragma unroll
-            for (int k = 0; k < kBK / 16; ++k)
-                tc::mma_bf16(tmem, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
-                             idesc, (it | k) != 0);
+            for (int k = 0; k < 4; ++k) {
+                if (FP8)
+                    tc::mma_e4m3(tmem, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
+                                 idesc, (it | k) != 0);
+                else
+                    tc::mma_bf16(tmem, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
+                                 idesc, (it | k) != 0);
+            }
             tc::mma_commit(&empty[s]);
             ++it;
         }
@@ -193,7 +206,7 @@ struct ChainSmem {
 // could run beside this chain; each new s_a goes into the next panel's
 // fields here instead, in FP32 (gx_out), from the block J[p][p+1]. Lane j
 // owns next-panel spins 4 (32/RPW) u + 4 j + i, read as float4.
-template <int RPW, bool NEXT>
+template <int RPW, bool NEXT, bool FP8>
 __global__ void __launch_bounds__(kChainWarps * 32, 1)
     panel_chain_kernel(TcState t, int p, const float* __restrict__ G, const float* __restrict__ gx_in,
                        float* __restrict__ gx_out)
@@ -225,7 +238,7 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
     // RPC replicas x 32 four-spin pieces = RPW pieces per thread.
     static_assert(RPC * (kBM / 4) == RPW * kChainWarps * 32, "one piece per thread and replica slot");
     float4 part[RPW][kSplitCap], gx[RPW], so[RPW];
-    uint2 sbw[RPW];
+    uint2 sbw[RPW];  // the four spins' low-precision copies (BF16, or E4M3 in .x)
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
         const int e = tid + k * kChainWarps * 32;
@@ -240,7 +253,10 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
                       : make_float4(0.f, 0.f, 0.f, 0.f);
         const size_t idx = (size_t)sl * t.n_pad + p0 + a4;
         so[k] = *reinterpret_cast<const float4*>(t.S + idx);
-        sbw[k] = *reinterpret_cast<const uint2*>(t.Sb + idx);  // four BF16
+        if (FP8)
+            sbw[k] = make_uint2(*reinterpret_cast<const uint32_t*>(t.S8 + idx), 0u);  // four E4M3
+        else
+            sbw[k] = *reinterpret_cast<const uint2*>(t.Sb + idx);  // four BF16
     }
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
@@ -269,11 +285,25 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
             if (a + 2 < t.n) f.z += __ldg(t.h + a + 2);
             if (a + 3 < t.n) f.w += __ldg(t.h + a + 3);
         }
+        float lo[4];
+        if (FP8) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                __nv_fp8_e4m3 v;
+                v.__x = (__nv_fp8_storage_t)((sbw[k].x >> (8 * i)) & 0xffu);
+                lo[i] = float(v);
+            }
+        } else {
+            lo[0] = __uint_as_float(sbw[k].x << 16);
+            lo[1] = __uint_as_float(sbw[k].x & 0xffff0000u);
+            lo[2] = __uint_as_float(sbw[k].y << 16);
+            lo[3] = __uint_as_float(sbw[k].y & 0xffff0000u);
+        }
         ChainSpin* d = cs_all + rr * kBM + a4;
-        d[0] = ChainSpin{f.x, so[k].x, __uint_as_float(sbw[k].x << 16), 0.f};
-        d[1] = ChainSpin{f.y, so[k].y, __uint_as_float(sbw[k].x & 0xffff0000u), 0.f};
-        d[2] = ChainSpin{f.z, so[k].z, __uint_as_float(sbw[k].y << 16), 0.f};
-        d[3] = ChainSpin{f.w, so[k].w, __uint_as_float(sbw[k].y & 0xffff0000u), 0.f};
+        d[0] = ChainSpin{f.x, so[k].x, lo[0], 0.f};
+        d[1] = ChainSpin{f.y, so[k].y, lo[1], 0.f};
+        d[2] = ChainSpin{f.z, so[k].z, lo[2], 0.f};
+        d[3] = ChainSpin{f.w, so[k].w, lo[3], 0.f};
     }
     if (tid == 0) s_ok = tc::mbar_wait(bar, 0, t.counters + 2) ? 1 : 0;
     __syncthreads();
@@ -355,7 +385,10 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
         if (p0 + a < t.n) {
             const size_t idx = (size_t)slot * t.n_pad + p0 + a;
             t.S[idx] = sf[q];
-            t.Sb[idx] = __float2bfloat16_rn(sf[q]);
+            if (FP8)
+                t.S8[idx] = __nv_fp8_e4m3(sf[q]).__x;
+            else
+                t.Sb[idx] = __float2bfloat16_rn(sf[q]);
         }
     }
     if (NEXT) {
@@ -382,7 +415,10 @@ __global__ void tc_init_kernel(TcState t)
             v = t.m0 ? __ldg(t.m0 + (size_t)r * t.n + o) : draw_m0(t.seed, t.stream, r, o);
         }
         t.S[idx] = v;
-        t.Sb[idx] = __float2bfloat16_rn(v);
+        if (t.S8)
+            t.S8[idx] = __nv_fp8_e4m3(v).__x;
+        else
+            t.Sb[idx] = __float2bfloat16_rn(v);
     }
     for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < t.R; slot += gridDim.x * blockDim.x) {
         const double T = (double)t.t0[t.rep[slot]] - t.c_step;
@@ -514,7 +550,10 @@ size_t tc_gemm_smem(int bn) { return bn == 64 ? GemmSmem<64>::kBytes : GemmSmem<
 cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g,
                                  int bn, int n_tiles, int splitk, cudaStream_t st)
 {
-    const void* k = bn == 64 ? (const void*)panel_gemm_kernel<64> : (const void*)panel_gemm_kernel<128>;
+    const void* k = g.fp8 ? (bn == 64 ? (const void*)panel_gemm_kernel<64, true>
+                                      : (const void*)panel_gemm_kernel<128, true>)
+                          : (bn == 64 ? (const void*)panel_gemm_kernel<64, false>
+                                      : (const void*)panel_gemm_kernel<128, false>);
     const size_t smem = tc_gemm_smem(bn);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -524,37 +563,46 @@ cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS,
     return cudaLaunchKernel(k, dim3(n_tiles, splitk), dim3(128), args, smem, st);
 }
 
-template <int RPW, bool NEXT>
+template <int RPW, bool NEXT, bool FP8>
 cudaError_t launch_chain_as(const TcState& t, int p, const float* G, const float* gx_in, float* gx_out,
                             cudaStream_t st)
 {
     constexpr int smem = ChainSmem<RPW, NEXT>::kBytes;
-    cudaError_t e = cudaFuncSetAttribute(panel_chain_kernel<RPW, NEXT>,
+    cudaError_t e = cudaFuncSetAttribute(panel_chain_kernel<RPW, NEXT, FP8>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int per_cta = kChainWarps * RPW;
-    panel_chain_kernel<RPW, NEXT><<<(t.R + per_cta - 1) / per_cta, kChainWarps * 32, smem, st>>>(
+    panel_chain_kernel<RPW, NEXT, FP8><<<(t.R + per_cta - 1) / per_cta, kChainWarps * 32, smem, st>>>(
         t, p, G, gx_in, gx_out);
     return cudaGetLastError();
+}
+
+template <bool FP8>
+cudaError_t launch_chain_lo(const TcState& t, int p, int rpw, bool next, const float* G, const float* gx_in,
+                            float* gx_out, cudaStream_t st)
+{
+    switch (rpw * 2 + (next ? 1 : 0)) {
+    case 2: return launch_chain_as<1, false, FP8>(t, p, G, gx_in, gx_out, st);
+    case 3: return launch_chain_as<1, true, FP8>(t, p, G, gx_in, gx_out, st);
+    case 4: return launch_chain_as<2, false, FP8>(t, p, G, gx_in, gx_out, st);
+    case 5: return launch_chain_as<2, true, FP8>(t, p, G, gx_in, gx_out, st);
+    case 8: return launch_chain_as<4, false, FP8>(t, p, G, gx_in, gx_out, st);
+    case 9: return launch_chain_as<4, true, FP8>(t, p, G, gx_in, gx_out, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, const float* gx_in,
                             float* gx_out, cudaStream_t st)
 {
+    if (rpw != 1 && rpw != 2 && rpw != 4) return cudaErrorInvalidValue;
     if (t.splitk < 1 || t.splitk > kChainMaxSplit / rpw) return cudaErrorInvalidValue;
     // the CTA's slots must lie inside G's R_pad rows (R_pad is a multiple of 128)
     if (t.R_pad % (kChainWarps * rpw) != 0) return cudaErrorInvalidValue;
     const bool next = gx_out != nullptr;
     if (next && !t.Jsup) return cudaErrorInvalidValue;
-    switch (rpw * 2 + (next ? 1 : 0)) {
-    case 2: return launch_chain_as<1, false>(t, p, G, gx_in, gx_out, st);
-    case 3: return launch_chain_as<1, true>(t, p, G, gx_in, gx_out, st);
-    case 4: return launch_chain_as<2, false>(t, p, G, gx_in, gx_out, st);
-    case 5: return launch_chain_as<2, true>(t, p, G, gx_in, gx_out, st);
-    case 8: return launch_chain_as<4, false>(t, p, G, gx_in, gx_out, st);
-    case 9: return launch_chain_as<4, true>(t, p, G, gx_in, gx_out, st);
-    default: return cudaErrorInvalidValue;
-    }
+    return t.S8 ? launch_chain_lo<true>(t, p, rpw, next, G, gx_in, gx_out, st)
+                : launch_chain_lo<false>(t, p, rpw, next, G, gx_in, gx_out, st);
 }
 
 cudaError_t launch_tc_init(const TcState& t, cudaStream_t st)

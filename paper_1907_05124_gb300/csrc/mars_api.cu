@@ -6,6 +6,7 @@
 #include "mars_internal.h"
 
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cmath>
@@ -334,18 +335,20 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 
 // Row-major [outer][inner] BF16 matrix, boxes of box_inner x box_outer with the
 // 128-byte swizzle (box_inner = 64 BF16 = 128 bytes).
-bool encode_bf16_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
-                    uint32_t box_inner, uint32_t box_outer)
+// 2-D K-major operand map: inner (K) extent `inner` elements of `elem` bytes,
+// `outer` rows, 128-byte swizzled boxes of box_inner x box_outer.
+bool encode_2d(CUtensorMap* m, CUtensorMapDataType dt, uint32_t elem, const void* base, uint64_t inner,
+               uint64_t outer, uint32_t box_inner, uint32_t box_outer)
 {
     PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
     if (!fn) return false;
     const cuuint64_t dims[2] = {inner, outer};
-    const cuuint64_t strides[1] = {inner * 2};
+    const cuuint64_t strides[1] = {inner * elem};
     const cuuint32_t box[2] = {box_inner, box_outer};
     const cuuint32_t es[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // The dense descent on tensor cores: slots in start-temperature order, a
@@ -406,7 +409,7 @@ constexpr int kTcBN = 128;
 // blocking path (Scratch) and the serving engine (per-request lists) can own them.
 template <typename Get>
 int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t* rep_dev,
-             float t0_max, cudaStream_t st, Get&& get, TcRun* run)
+             float t0_max, bool fp8, cudaStream_t st, Get&& get, TcRun* run)
 {
     int rc;
     TcState& t = run->t;
@@ -434,7 +437,7 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     int splitk = 1;
     const int split_max = env_flag("MARS_TC_SPLITK_MAX", 16);
     while (splitk < split_max && splitk * 2 <= kChainMaxSplit / rpw && run->ntiles * splitk * 2 <= c->sms &&
-           (n_pad / 64) % (splitk * 2) == 0)
+           (n_pad / (fp8 ? 128 : 64)) % (splitk * 2) == 0)
         splitk *= 2;
     run->splitk = splitk;
     t.R = R;
@@ -456,7 +459,12 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     t.fixed_sweeps = s.fixed_sweeps;
     t.rep = rep_dev;
     if ((rc = get((size_t)R * n_pad * sizeof(float), (void**)&t.S))) return rc;
-    if ((rc = get((size_t)R_pad * n_pad * sizeof(__nv_bfloat16), (void**)&t.Sb))) return rc;
+    if (fp8 && !d.J8) return fail(c, MARS_EINVAL, "FP8 needs couplings exact in E4M3");
+    if (fp8) {
+        if ((rc = get((size_t)R_pad * n_pad, (void**)&t.S8))) return rc;
+    } else if ((rc = get((size_t)R_pad * n_pad * sizeof(__nv_bfloat16), (void**)&t.Sb))) {
+        return rc;
+    }
     const size_t g_floats = (size_t)splitk * R_pad * 128;
     if ((rc = get(2 * g_floats * sizeof(float), (void**)&t.G))) return rc;
     run->Gbuf[0] = t.G;
@@ -479,14 +487,21 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.sweeps))) return rc;
     if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.capped))) return rc;
     if ((rc = get(4 * sizeof(int32_t), (void**)&t.counters))) return rc;
-    MARS_CUDA(c, cudaMemsetAsync(t.Sb, 0, (size_t)R_pad * n_pad * sizeof(__nv_bfloat16), st));
+    if (fp8)
+        MARS_CUDA(c, cudaMemsetAsync(t.S8, 0, (size_t)R_pad * n_pad, st));
+    else
+        MARS_CUDA(c, cudaMemsetAsync(t.Sb, 0, (size_t)R_pad * n_pad * sizeof(__nv_bfloat16), st));
     MARS_CUDA(c, cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), st));
-    if (!encode_bf16_2d(&run->tmJ, d.Jbf, n_pad, n_pad, 64, 128) ||
-        !encode_bf16_2d(&run->tmS, t.Sb, n_pad, R_pad, 64, kTcBN))
-        return fail(c, MARS_EDEVICE, "tensor map encoding failed");
+    const bool maps_ok =
+        fp8 ? encode_2d(&run->tmJ, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.J8, n_pad, n_pad, 128, 128) &&
+                  encode_2d(&run->tmS, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, t.S8, n_pad, R_pad, 128, kTcBN)
+            : encode_2d(&run->tmJ, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, d.Jbf, n_pad, n_pad, 64, 128) &&
+                  encode_2d(&run->tmS, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t.Sb, n_pad, R_pad, 64, kTcBN);
+    if (!maps_ok) return fail(c, MARS_EDEVICE, "tensor map encoding failed");
     MARS_CUDA(c, launch_tc_init(t, st));
     MARS_CUDA(c, launch_tc_prefix(t, st));
-    run->g.kblocks = n_pad / 64 / splitk;
+    run->g.kblocks = n_pad / (fp8 ? 128 : 64) / splitk;
+    run->g.fp8 = fp8 ? 1 : 0;
     run->g.R_pad = R_pad;
     run->g.G = t.G;
     run->g.active_prefix = t.counters;
@@ -517,7 +532,7 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
         TcPanel g = run->g;
         g.p0 = pp * 128;
         g.G = run->Gbuf[pp & 1];
-        g.skip_kb = ov && pp > 0 ? 2 * (pp - 1) : -1;
+        g.skip_kb = ov && pp > 0 ? (g.fp8 ? 1 : 2) * (pp - 1) : -1;  // panel pp-1's K blocks
         if (ov && pp >= 2) MARS_CUDA(c, cudaStreamWaitEvent(gs, run->ev[2 + 2 * (pp - 2)], 0));
         if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp], gs));
         MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->ntiles, run->splitk, gs));
@@ -603,7 +618,7 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
         *out = q;
         return r;
     };
-    if ((rc = tc_setup(c, in->dev, s, rep, t0_max, st, get, &run))) return rc;
+    if ((rc = tc_setup(c, in->dev, s, rep, t0_max, p->precision == MARS_FP8, st, get, &run))) return rc;
     prof->launches += 2;  // start states, active prefix
     int32_t* pinned = nullptr;
     MARS_CUDA(c, cudaMallocHost((void**)&pinned, 4 * sizeof(int32_t)));
@@ -759,7 +774,7 @@ size_t serve_footprint(const DevInstance& d, const mars_params& p, int sms)
 {
     const size_t R = (size_t)p.replicas, n = (size_t)d.n;
     size_t b = R * n + R * (4 + 8 + 8 + 12 + 4 + 4) + 4096 + n;
-    if (d.dense && p.precision == MARS_BF16) {
+    if (d.dense && (p.precision == MARS_BF16 || p.precision == MARS_FP8)) {
         const size_t np = (size_t)d.n_pad, Rp = (R + 127) / 128 * 128;
         b += R * np * 4 + Rp * np * 2 + 8 * Rp * 128 * 4 + R * 32;
     } else if (!d.dense) {
@@ -840,7 +855,7 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
     s.status = s.work_counter + 1;
     if ((rc = get(sizeof(DevResult), (void**)&q->dres))) return rc;
     if ((rc = get((size_t)n, (void**)&q->dbest))) return rc;
-    const bool tc = q->dev.dense && p.precision == MARS_BF16;
+    const bool tc = q->dev.dense && (p.precision == MARS_BF16 || p.precision == MARS_FP8);
     int rt = 1;
     SparsePlan sp;
     DensePlan dp;
@@ -870,7 +885,8 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
         q->tc.reset(new TcRun());
         TcRun* run = q->tc.get();
         const float t0_max = (float)std::max(p.t_max, 0.0);
-        if ((rc = tc_setup(c, q->dev, s, queue, p.t0 ? 1e6f * (float)p.c_step : t0_max, st, get, run)))
+        if ((rc = tc_setup(c, q->dev, s, queue, p.t0 ? 1e6f * (float)p.c_step : t0_max,
+                           p.precision == MARS_FP8, st, get, run)))
             return rc;
         run->h_counters = pinned_view(q->pinned).counters;
         if ((rc = tc_enqueue_batch(c, run, st))) return rc;
@@ -1144,6 +1160,24 @@ int mars_instance_dense(mars_ctx* c, int32_t n, const void* J, int32_t jt, const
             else if (b / 128 == a / 128 + 1)
                 Jsup[((size_t)(a / 128) * 128 + a % 128) * 128 + b % 128] = v;
         }
+    // E4M3 copy for FP8 descents, when every coupling is exact in E4M3
+    // (integers up to 16, and coarser ones up to 448).
+    std::vector<uint8_t> J8;
+    if (integer) {
+        J8.assign((size_t)n_pad * n_pad, 0);
+        bool exact = true;
+        for (int32_t a = 0; a < n && exact; ++a)
+            for (int32_t b = 0; b < n; ++b) {
+                const float v = Jf[(size_t)a * n + b];
+                const __nv_fp8_e4m3 q(v);
+                if (float(q) != v) {
+                    exact = false;
+                    break;
+                }
+                J8[(size_t)a * n_pad + b] = (uint8_t)q.__x;
+            }
+        if (!exact) J8.clear();
+    }
     DevInstance& d = in->dev;
     d.n = n;
     d.dense = 1;
@@ -1158,6 +1192,7 @@ int mars_instance_dense(mars_ctx* c, int32_t n, const void* J, int32_t jt, const
         d.Jbf = (const __nv_bfloat16*)jb;
         if ((rc = upload(c, in.get(), Jdiag, &d.Jdiag))) return rc;
         if ((rc = upload(c, in.get(), Jsup, &d.Jsup))) return rc;
+        if (!J8.empty() && (rc = upload(c, in.get(), J8, &d.J8))) return rc;
     }
     if ((rc = upload(c, in.get(), Jf, &d.Jf))) return rc;
     if ((rc = upload(c, in.get(), Ji, &d.J_i8))) return rc;
@@ -1446,10 +1481,12 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     if (p->k_max < 1 || p->fixed_sweeps < 0) return fail(c, MARS_EINVAL, "k_max >= 1, fixed_sweeps >= 0");
     if (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI)
         return fail(c, MARS_EINVAL, "unknown update rule %d", p->update);
-    const bool tc = p->precision == MARS_BF16;
+    const bool tc = p->precision == MARS_BF16 || p->precision == MARS_FP8;
     if (p->precision != MARS_FP32 && !(tc && in->dev.dense && p->update == MARS_UPDATE_GS))
         return fail(c, MARS_EINVAL, "precision %d is not available for this instance and update rule",
                     p->precision);
+    if (p->precision == MARS_FP8 && !in->dev.J8)
+        return fail(c, MARS_EINVAL, "FP8 needs integer couplings exactly representable in E4M3");
     if ((size_t)R * n > ((size_t)1 << 40)) return fail(c, MARS_EINVAL, "R*n too large");
     DeviceGuard g(c->device);
     cudaStream_t st = c->stream;
@@ -1823,7 +1860,7 @@ int mars_autotune(mars_ctx* c, int32_t id, const mars_params* p, int32_t repeats
     if (repeats < 1 || repeats > 100) return fail(c, MARS_EINVAL, "repeats must be in [1, 100]");
     const DevInstance& d = in->dev;
     std::vector<LaunchShape> cands;
-    if (d.dense && p->precision == MARS_BF16) {
+    if (d.dense && (p->precision == MARS_BF16 || p->precision == MARS_FP8)) {
         for (int ov = 1; ov >= 0; --ov)
             for (int rpw : {1, 2, 4}) {
                 LaunchShape sh;
@@ -1889,9 +1926,11 @@ int mars_submit(mars_ctx* c, int32_t id, const mars_params* p, int64_t* req)
         p->k_max < 1 || p->fixed_sweeps < 0 ||
         (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI))
         return fail(c, MARS_EINVAL, "bad parameters");
-    const bool tc = p->precision == MARS_BF16;
+    const bool tc = p->precision == MARS_BF16 || p->precision == MARS_FP8;
     if (p->precision != MARS_FP32 && !(tc && in->dev.dense && p->update == MARS_UPDATE_GS))
         return fail(c, MARS_EINVAL, "precision %d is not available for this instance", p->precision);
+    if (p->precision == MARS_FP8 && !in->dev.J8)
+        return fail(c, MARS_EINVAL, "FP8 needs integer couplings exactly representable in E4M3");
     if ((p->m0 || p->t0) && !(p->flags & MARS_DEVICE_PTR))
         return fail(c, MARS_EINVAL, "served requests take m0/t0 as device pointers");
     if (tc && p->t0) return fail(c, MARS_EINVAL, "served tensor-core requests draw t0 themselves");

@@ -49,6 +49,7 @@ struct DevInstance {
     const __nv_bfloat16* Jbf = nullptr;  // n_pad*n_pad BF16, zero padded (tensor-core operand)
     const float* Jdiag = nullptr;        // (n_pad/128) FP32 128x128 diagonal blocks
     const float* Jsup = nullptr;         // (n_pad/128) FP32 128x128 blocks J[p][p+1] (last: zero)
+    const uint8_t* J8 = nullptr;         // n_pad x n_pad E4M3 copy when every J_ij is exact in E4M3
     LaunchShape shape;                   // host-side choice; kernels ignore it
     const float* Jf = nullptr;
     const int8_t* J_i8 = nullptr;
@@ -148,7 +149,8 @@ struct TcPanel {
     int32_t kblocks = 0;     // 64-wide K blocks per split
     int32_t R_pad = 0;
     float* G = nullptr;      // [split][R_pad][128]
-    int32_t skip_kb = -1;    // first of two 64-wide K blocks left out (-1: none)
+    int32_t skip_kb = -1;    // first K block of the panel left out (-1: none)
+    int32_t fp8 = 0;         // E4M3 operands (K blocks of 128) instead of BF16 (64)
     const int32_t* active_prefix = nullptr;
     int32_t* err = nullptr;
 };
@@ -157,6 +159,7 @@ struct TcState {
     float* G = nullptr;
     float* S = nullptr;            // [R][n_pad] FP32 magnetisations, slot order
     __nv_bfloat16* Sb = nullptr;   // [R_pad][n_pad] BF16 shadow (tensor-core operand)
+    uint8_t* S8 = nullptr;         // [R_pad][n_pad] E4M3 shadow instead, for FP8 descents
     const float* Jdiag = nullptr;
     const float* Jsup = nullptr;       // [P][128][128] FP32 blocks J[p][p+1]
     const float* h = nullptr;
