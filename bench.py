@@ -51,6 +51,17 @@ SK_WORKLOAD = {
     "d_min": D_MIN, "k_max": K_MAX, "precision": "bf16",
 }
 
+# The FP8 variant: dense SK with +-1 couplings (exact in E4M3) on E4M3 tensor
+# cores; the same schedule in units of the couplings' scale sqrt(N).
+SK8_TMAX = 2.0 * SK_N ** 0.5
+SK8_WORKLOAD = {
+    "workload": "dense SK N=8192, J_ij uniform in {-1,+1}, R=4096 replicas, T0~U(0,2 sqrt(N)), "
+                "C_step=1, d_min=1e-4, k_max=1000, sequential sweeps with FP8 (E4M3) "
+                "tcgen05 panel GEMMs",
+    "n_spins": SK_N, "replicas": SK_R, "t_range": [0.0, SK8_TMAX], "c_step": 1.0,
+    "d_min": D_MIN, "k_max": K_MAX, "precision": "fp8",
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -63,7 +74,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip mars_autotune before the warm-up (library default launch shape)")
-    ap.add_argument("--workload", default="ea2d", choices=["ea2d", "sk8192", "serve"],
+    ap.add_argument("--workload", default="ea2d", choices=["ea2d", "sk8192", "sk8192pm1", "serve"],
                     help="ea2d: the 2-D lattice (default); sk8192: dense SK on tensor cores; "
                          "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
@@ -148,11 +159,11 @@ def cpu_baseline(target_s: float, wl=None):
     from paper_1907_05124_gb300 import instances as I
 
     cores = os.cpu_count() or 1
-    if wl is not None and wl.name == "sk8192":
+    if wl is not None and wl.name in ("sk8192", "sk8192pm1"):
         # Dense N=8192 sweeps cost ~0.1 s each on one core: time one sweep per
         # level (fixed-sweep mode) on one replica per core.
         inst = O.Instance.dense(wl.J)
-        m0, t0 = O.draw_replicas(0, cores, SK_N, T_MIN, SK_TMAX)
+        m0, t0 = O.draw_replicas(0, cores, SK_N, T_MIN, wl.t_max)
         t = time.perf_counter()
         out = O.mars_solve(inst, m0, t0, c_step=wl.c_step, d_min=D_MIN, k_max=K_MAX,
                            fixed_sweeps=1, nthreads=cores, want_m=False)
@@ -262,13 +273,20 @@ class Workload:
             self.t_max, self.c_step, self.precision = T_MAX, C_STEP, "fp32"
             self.config = dict(WORKLOAD, replicas=self.R)
             self.dtype = "f32"
-        else:
+        elif self.name == "sk8192":
             self.csr = None
             self.J = instances.sk_gauss(SK_N, 0)
             self.R = args.replicas or SK_R
             self.t_max, self.c_step, self.precision = SK_TMAX, 1.0 / SK_N ** 0.5, "bf16"
             self.config = dict(SK_WORKLOAD, replicas=self.R)
             self.dtype = "bf16"
+        else:
+            self.csr = None
+            self.J = instances.sk_pm1(SK_N, 0)
+            self.R = args.replicas or SK_R
+            self.t_max, self.c_step, self.precision = SK8_TMAX, 1.0, "fp8"
+            self.config = dict(SK8_WORKLOAD, replicas=self.R)
+            self.dtype = "e4m3"
         self.rank = rank
         self.fixed = args.fixed_sweeps
         if self.fixed:
@@ -403,11 +421,15 @@ def run_mars(args, world, rank, local):
                     "descent_ms_mean": 1e3 * d_mean}
     else:
         achieved = gemm_flops / gemm_s / 1e12 if gemm_s > 0 else 0.0
-        peak = peaks["bf16_tflops_sustained"]
+        fp8 = wl.precision == "fp8"
+        # an E4M3 contraction's peak: the measured BF16 peak times the nominal
+        # FP8 / BF16 ratio (4.5 / 2.25 PFLOP/s dense)
+        peak = peaks["bf16_tflops_sustained"] * (2.0 if fp8 else 1.0)
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": "panel_gemm_kernel<128> (tcgen05 BF16, split-K)",
-                    "peak_source": f"bf16 sustained ({peaks['source']})",
+                    "kernel": "panel_gemm_kernel<128, {}> (tcgen05 {}, split-K)".format(
+                        "FP8" if fp8 else "BF16", "kind::f8f6f4 E4M3" if fp8 else "kind::f16 BF16"),
+                    "peak_source": ("2 x bf16 sustained" if fp8 else "bf16 sustained") + f" ({peaks['source']})",
                     "gemm_launches_sampled": gemm_launches,
                     "descent_ms_mean": 1e3 * d_mean}
 
@@ -502,6 +524,7 @@ def run_serve(args, world, rank, local):
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                        "p99": float(np.percentile(lat_ms, 99)),
                        "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
+        "served_by": dict(zip(("persistent_ring_kernel", "own_stream"), ctx.serve_counters())),
     }
     print(json.dumps(line), flush=True)
     ctx.close()

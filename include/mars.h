@@ -320,6 +320,16 @@ int mars_poll(mars_ctx* ctx, int64_t req, int8_t* best_spins, mars_result* resul
 int mars_serve_status(mars_ctx* ctx, int32_t* queued, int32_t* running);
 
 /*
+ * Requests served so far by route: ring_jobs ran as jobs of the persistent
+ * serving kernel (sparse instances with integer couplings whose state fits
+ * on chip: each is published into a device-side ring that the running
+ * kernel's CTAs take work from, so a request that arrives while others run
+ * joins the same launch); stream_jobs ran their own kernels on their own
+ * stream (dense requests and the rest). Either pointer may be NULL.
+ */
+int mars_serve_counters(mars_ctx* ctx, int64_t* ring_jobs, int64_t* stream_jobs);
+
+/*
  * Exact energies (Section 2, Eq. 2, pairs once) of count spin vectors
  * (count*n int8, entries +-1, caller labels). e (count doubles) receives the
  * energy rounded once to the nearest double; e_i64 (nullable) receives it as

@@ -28,7 +28,10 @@ namespace {
 
 constexpr int kBM = 128;     // panel rows = MMA M
 constexpr int kBK = 64;      // K per pipeline stage: one 128-byte swizzle row of BF16 (128 of E4M3)
-constexpr int kStages = 4;
+#ifndef MARS_GEMM_STAGES
+#define MARS_GEMM_STAGES 4
+#endif
+constexpr int kStages = MARS_GEMM_STAGES;  // TMA pipeline depth of the panel GEMM
 constexpr int kChainWarps = 8;
 
 __device__ __forceinline__ float tanh_sfu(float x)

@@ -19,6 +19,7 @@
 // The tile's magnetisations m[i*RT + k] live in shared memory for the whole
 // descent; the dummy row n is zero. Only the sweeps' parallel steps need a
 // block barrier.
+#include "best_reduce.cuh"
 #include "device_common.cuh"
 #include "mars_internal.h"
 
@@ -165,6 +166,7 @@ __device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, Slot
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = in.n;
+    __shared__ int s_last[RT];  // serving ring: this slot finished its job's last replica
     Entry<FMT> ent;
     const int4* slices = in.slices;
     if constexpr (FMT == 0) ent.e = in.sell_gen;
@@ -289,6 +291,7 @@ __device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, Slot
                 const double b = warp_reduce_strided<1>(ef[k], SumOp());
                 if (lane == 0) { s_ei[warp][k] = a; s_ef[warp][k] = b; }
             }
+            if (s.finished) __threadfence();  // this thread's outputs, before the completion count
             __syncthreads();
             if (tid < RT && done[tid]) {
                 const int r = rep[tid];
@@ -300,8 +303,31 @@ __device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, Slot
                 s.sweeps[r] = s_sweeps[tid];
                 s.levels[r] = s_levels[tid];
                 s.capped[r] = s_capped[tid];
+                if (s.finished) {
+                    __threadfence();
+                    s_last[tid] = atomicAdd(s.finished, 1) + 1 == s.R;
+                }
             }
             __syncthreads();
+            if (s.finished) {
+                // The CTA that finishes a served job's last replica selects its
+                // best replica and tells the host (every CTA fenced its outputs
+                // before counting them).
+                bool last = false;
+#pragma unroll
+                for (int k = 0; k < RT; ++k) last |= done[k] && s_last[k] != 0;
+                if (last) {
+                    __threadfence();
+                    best_reduce<kThreads>(s, n, in.integer, s.best_out, s.res);
+                    __threadfence_system();
+                    __syncthreads();
+                    if (tid == 0) *reinterpret_cast<volatile int32_t*>(s.done_flag) = 1;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < RT; ++k)
+                    if (tid == k) s_last[k] = 0;
+            }
             if (tid == 0) {
                 for (int k = 0; k < RT; ++k) {
                     if (!done[k]) continue;
@@ -470,6 +496,63 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_batch_kernel(const 
         if (j < 0) break;
         {
             const int* src = reinterpret_cast<const int*>(jobs + j);
+            int* dst = reinterpret_cast<int*>(&s_jobcopy);
+            for (int w = threadIdx.x; w < (int)(sizeof(BatchJob) / sizeof(int)); w += blockDim.x)
+                dst[w] = src[w];
+        }
+        __syncthreads();
+        const BatchJob& job = s_jobcopy;
+        switch (job.fmt) {
+        case 3: run_job<RT, NT, 3>(job.in, job.s, m, S); break;
+        case 2: run_job<RT, NT, 2>(job.in, job.s, m, S); break;
+        case 1: run_job<RT, NT, 1>(job.in, job.s, m, S); break;
+        default: run_job<RT, NT, 0>(job.in, job.s, m, S); break;
+        }
+        __syncthreads();
+    }
+}
+
+// Persistent serving kernel: CTAs take replicas from the jobs published in the
+// ring, oldest first; when none is left, thread 0 polls the ring's tail
+// (about 2 us apart, at most idle_polls times) and the CTA exits when nothing
+// new arrives. Descriptors written by the host's copies are read through
+// volatile loads (past L1), after the tail that published them.
+template <int RT, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) serve_ring_kernel(ServeRing* ring, int idle_polls)
+{
+    extern __shared__ __align__(16) float m[];
+    __shared__ SlotState<RT, NT / 32> S;
+    __shared__ BatchJob s_jobcopy;
+    __shared__ int s_job;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int found = -1;
+            for (int poll = 0; poll <= idle_polls; ++poll) {
+                int c = *reinterpret_cast<volatile int*>(&ring->cursor);
+                const int tail = *reinterpret_cast<volatile int*>(&ring->tail);
+                __threadfence();
+                while (c < tail) {
+                    const int k = c % kRingCap;
+                    const int taken = *reinterpret_cast<volatile int*>(&ring->slots[k].taken);
+                    const int R = *reinterpret_cast<volatile int*>(&ring->jobs[k].s.R);
+                    if (taken < R) break;
+                    atomicMax(&ring->cursor, c + 1);
+                    ++c;
+                }
+                if (c < tail) {
+                    found = c;
+                    break;
+                }
+                if (*reinterpret_cast<volatile int*>(&ring->stop)) break;
+                __nanosleep(2000);
+            }
+            s_job = found;
+        }
+        __syncthreads();
+        const int j = s_job;
+        if (j < 0) break;
+        {
+            const volatile int* src = reinterpret_cast<const volatile int*>(ring->jobs + j % kRingCap);
             int* dst = reinterpret_cast<int*>(&s_jobcopy);
             for (int w = threadIdx.x; w < (int)(sizeof(BatchJob) / sizeof(int)); w += blockDim.x)
                 dst[w] = src[w];
@@ -659,6 +742,44 @@ cudaError_t launch_sparse_batch(const BatchJob* jobs, int count, int* cursor, co
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&jobs, (void*)&count, (void*)&cursor};
+    return cudaLaunchKernel(k, dim3(p.grid), dim3(p.threads), args, p.smem, st);
+}
+
+bool plan_serve_ring(int device, RingPlan* p)
+{
+    int sms = 1, optin = 48 * 1024;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    p->rt = 2;
+    p->threads = 1024;
+    p->smem = (size_t)optin - 16 * 1024;  // static shared memory and slack
+    const void* k = (const void*)serve_ring_kernel<2, 1024>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess)
+        return false;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, p->threads, p->smem);
+    p->grid = sms * std::max(per_sm, 1);
+    return true;
+}
+
+int ring_job_format(const DevInstance& in, const RingPlan& p)
+{
+    if (in.dense || !in.slices || (!in.sell_pm1 && !in.sell_gen)) return -1;
+    const size_t mb = align16((size_t)(in.n + 1) * p.rt * sizeof(float));
+    if (mb > p.smem) return -1;
+    const size_t table = (size_t)in.nslices * 16 + (size_t)in.sell_len * 2;
+    if (in.sell16 && mb + table <= p.smem) return 2;
+    if (in.sell16) return 3;
+    return in.sell_pm1 ? 1 : 0;
+}
+
+cudaError_t launch_serve_ring(ServeRing* ring, const RingPlan& p, int idle_polls, cudaStream_t st)
+{
+    if (p.rt != 2 || p.threads != 1024) return cudaErrorInvalidValue;
+    const void* k = (const void*)serve_ring_kernel<2, 1024>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&ring, (void*)&idle_polls};
     return cudaLaunchKernel(k, dim3(p.grid), dim3(p.threads), args, p.smem, st);
 }
 

@@ -683,7 +683,7 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
 // its own stream, so its kernels overlap with the others' on the device; a
 // dense tensor-core request advances one batch of sweeps per event.
 // ---------------------------------------------------------------------------
-enum class ReqState { Queued, Running, TcRunning, Finishing, Done, Failed };
+enum class ReqState { Queued, Running, TcRunning, RingRunning, Finishing, Done, Failed };
 
 struct ServeReq {
     int64_t id = 0;
@@ -703,6 +703,7 @@ struct ServeReq {
     cudaEvent_t ev = nullptr;
     std::unique_ptr<TcRun> tc;
     double total_weight = 0.0, err_bound = 0.0;
+    int64_t ring_job = -1;  // serving-ring job index, or -1
 };
 
 struct Serve {
@@ -713,9 +714,93 @@ struct Serve {
     int64_t next_id = 1;
     int max_inflight = 8;
     int inflight = 0;
+    // The serving ring: sparse requests run as jobs of one persistent kernel
+    // (continuous batching: a job published while the kernel runs is picked
+    // up by CTAs as they free up). Descriptors are staged in pinned memory
+    // and copied on one publish stream, so the tail the kernel reads never
+    // runs ahead of the descriptors it covers.
+    bool ring_on = false;
+    RingPlan plan;
+    ServeRing* ring = nullptr;      // device
+    BatchJob* stage_jobs = nullptr; // pinned [kRingCap]
+    RingSlot* stage_slots = nullptr;
+    int32_t* stage_tail = nullptr;
+    int32_t* done = nullptr;        // host-mapped flags [kRingCap]
+    int32_t* done_dev = nullptr;
+    int ring_refs = 0;              // requests that still read their ring slot
+    cudaStream_t pub_st = nullptr, ring_st = nullptr;
+    cudaEvent_t ring_ev = nullptr;
+    bool kernel_live = false;
+    int64_t tail = 0;
+    int64_t ring_jobs = 0;          // jobs served through the ring
+    int64_t stream_jobs = 0;        // jobs served on their own streams
+    int idle_polls = 50;            // about 100 us without work before the kernel exits
 };
 
 void serve_delete(Serve* sv) { delete sv; }
+
+// Set the ring up on first use; false when it is unavailable (then every
+// request takes its own stream).
+bool serve_ring_init(mars_ctx* c, Serve* sv)
+{
+    if (sv->ring) return true;
+    if (!env_flag("MARS_SERVE_RING", 1) || !plan_serve_ring(c->device, &sv->plan)) return false;
+    bool ok = cudaMalloc((void**)&sv->ring, sizeof(ServeRing)) == cudaSuccess &&
+              cudaMemset(sv->ring, 0, sizeof(ServeRing)) == cudaSuccess &&
+              cudaMallocHost((void**)&sv->stage_jobs, sizeof(BatchJob) * kRingCap) == cudaSuccess &&
+              cudaMallocHost((void**)&sv->stage_slots, sizeof(RingSlot) * kRingCap) == cudaSuccess &&
+              cudaMallocHost((void**)&sv->stage_tail, sizeof(int32_t) * kRingCap) == cudaSuccess &&
+              cudaHostAlloc((void**)&sv->done, sizeof(int32_t) * kRingCap, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer((void**)&sv->done_dev, sv->done, 0) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&sv->pub_st, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&sv->ring_st, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&sv->ring_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaDeviceSynchronize() == cudaSuccess;
+    if (ok) std::memset(sv->done, 0, sizeof(int32_t) * kRingCap);
+    sv->ring_on = ok;
+    return ok;
+}
+
+void serve_ring_free(Serve* sv)
+{
+    if (sv->ring) {
+        int32_t one = 1;
+        cudaMemcpyAsync(&sv->ring->stop, &one, sizeof one, cudaMemcpyHostToDevice, sv->pub_st);
+        cudaStreamSynchronize(sv->pub_st);
+        cudaStreamSynchronize(sv->ring_st);
+        cudaFree(sv->ring);
+        sv->ring = nullptr;
+    }
+    if (sv->stage_jobs) cudaFreeHost(sv->stage_jobs);
+    if (sv->stage_slots) cudaFreeHost(sv->stage_slots);
+    if (sv->stage_tail) cudaFreeHost(sv->stage_tail);
+    if (sv->done) cudaFreeHost(sv->done);
+    if (sv->pub_st) cudaStreamDestroy(sv->pub_st);
+    if (sv->ring_st) cudaStreamDestroy(sv->ring_st);
+    if (sv->ring_ev) cudaEventDestroy(sv->ring_ev);
+    sv->stage_jobs = nullptr;
+    sv->stage_slots = nullptr;
+    sv->stage_tail = nullptr;
+    sv->done = nullptr;
+    sv->pub_st = sv->ring_st = nullptr;
+    sv->ring_ev = nullptr;
+    sv->ring_on = false;
+}
+
+// Launch the serving kernel unless one is still running.
+int serve_ring_ensure_kernel(mars_ctx* c, Serve* sv)
+{
+    if (sv->kernel_live) {
+        const cudaError_t e = cudaEventQuery(sv->ring_ev);
+        if (e == cudaErrorNotReady) return MARS_OK;
+        if (e != cudaSuccess) return fail(c, MARS_EDEVICE, "serving kernel: %s", cudaGetErrorString(e));
+        sv->kernel_live = false;
+    }
+    MARS_CUDA(c, launch_serve_ring(sv->ring, sv->plan, sv->idle_polls, sv->ring_st));
+    MARS_CUDA(c, cudaEventRecord(sv->ring_ev, sv->ring_st));
+    sv->kernel_live = true;
+    return MARS_OK;
+}
 
 Serve* serve_get(mars_ctx* c)
 {
@@ -749,6 +834,10 @@ PinnedView pinned_view(unsigned char* base)
 
 void serve_free_req(mars_ctx* c, Serve* sv, ServeReq* q)
 {
+    if (q->ring_job >= 0) {
+        sv->ring_refs -= 1;
+        q->ring_job = -1;
+    }
     if (q->st) {
         for (auto& b : q->bufs) dev_free_on(c, &b, q->st);
         q->bufs.clear();
@@ -783,12 +872,10 @@ size_t serve_footprint(const DevInstance& d, const mars_params& p, int sms)
     return b;
 }
 
-int serve_finish_enqueue(mars_ctx* c, ServeReq* q)
+// The request's results to pinned memory, then its event.
+int serve_copy_results(mars_ctx* c, ServeReq* q)
 {
     cudaStream_t st = q->st;
-    if (!q->dev.integer && q->dev.exact_ok)
-        MARS_CUDA(c, launch_energy(q->dev, q->s.sigma, q->s.R, q->s.energy, nullptr, q->s.status, st));
-    MARS_CUDA(c, launch_best(q->s, q->dev.n, q->dev.integer, q->dbest, q->dres, st));
     PinnedView v = pinned_view(q->pinned);
     MARS_CUDA(c, cudaMemcpyAsync(v.res, q->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, st));
     MARS_CUDA(c, cudaMemcpyAsync(v.status, q->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -796,6 +883,15 @@ int serve_finish_enqueue(mars_ctx* c, ServeReq* q)
     MARS_CUDA(c, cudaEventRecord(q->ev, st));
     q->state = ReqState::Finishing;
     return MARS_OK;
+}
+
+int serve_finish_enqueue(mars_ctx* c, ServeReq* q)
+{
+    cudaStream_t st = q->st;
+    if (!q->dev.integer && q->dev.exact_ok)
+        MARS_CUDA(c, launch_energy(q->dev, q->s.sigma, q->s.R, q->s.energy, nullptr, q->s.status, st));
+    MARS_CUDA(c, launch_best(q->s, q->dev.n, q->dev.integer, q->dbest, q->dres, st));
+    return serve_copy_results(c, q);
 }
 
 // Allocate, enqueue the whole pipeline (or the first batch of a tensor-core
@@ -865,6 +961,52 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
         dp = plan_dense(q->dev, R, s.jacobi, c->device);
         if (dp.scratch_floats && (rc = get(dp.scratch_floats * sizeof(float), (void**)&s.m_scratch))) return rc;
     } else {
+        // the serving ring: one persistent kernel for every sparse request
+        // (integer couplings: the kernel's fused int64 energies are final, so
+        // the job needs no kernel after the serving kernel)
+        const int fmt =
+            !s.jacobi && q->dev.integer && serve_ring_init(c, sv) ? ring_job_format(q->dev, sv->plan) : -1;
+        const int k = (int)sv->tail;
+        if (fmt >= 0 && sv->tail < kRingCap) {
+            const int32_t rr = sv->plan.rt;
+            const int32_t ntiles = (R + rr - 1) / rr;
+            int32_t* queue = nullptr;
+            if ((rc = get((size_t)ntiles * rr * sizeof(int32_t), (void**)&queue))) return rc;
+            MARS_CUDA(c, launch_queue_identity(queue, ntiles * rr, R, s.work_counter, st));
+            s.tile_rep = queue;
+            s.ntiles = ntiles;
+            s.rt = rr;
+            // the job's counters and flag live in the ring
+            s.work_counter = &sv->ring->slots[k].taken;
+            s.status = &sv->ring->slots[k].status;
+            s.finished = &sv->ring->slots[k].finished;
+            s.done_flag = sv->done_dev + k;
+            s.res = q->dres;
+            s.best_out = q->dbest;
+            sv->done[k] = 0;
+            BatchJob job;
+            job.in = q->dev;
+            job.s = s;
+            job.fmt = fmt;
+            sv->stage_jobs[k] = job;
+            sv->stage_slots[k] = RingSlot{};
+            sv->stage_tail[k] = (int32_t)(sv->tail + 1);
+            // publish after the request's own set-up (start temperatures, queue)
+            MARS_CUDA(c, cudaEventRecord(q->ev, st));
+            MARS_CUDA(c, cudaStreamWaitEvent(sv->pub_st, q->ev, 0));
+            MARS_CUDA(c, cudaMemcpyAsync(&sv->ring->jobs[k], &sv->stage_jobs[k], sizeof(BatchJob),
+                                         cudaMemcpyHostToDevice, sv->pub_st));
+            MARS_CUDA(c, cudaMemcpyAsync(&sv->ring->slots[k], &sv->stage_slots[k], sizeof(RingSlot),
+                                         cudaMemcpyHostToDevice, sv->pub_st));
+            MARS_CUDA(c, cudaMemcpyAsync(&sv->ring->tail, &sv->stage_tail[k], sizeof(int32_t),
+                                         cudaMemcpyHostToDevice, sv->pub_st));
+            q->ring_job = sv->tail;
+            sv->ring_refs += 1;
+            sv->tail += 1;
+            sv->ring_jobs += 1;
+            q->state = ReqState::RingRunning;
+            return serve_ring_ensure_kernel(c, sv);
+        }
         if (s.jacobi || !plan_sparse_sell(q->dev, R, c->device, &sp))
             sp = plan_sparse(q->dev, R, s.jacobi, c->device);
         rt = sp.rt;
@@ -889,11 +1031,13 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
                            p.precision == MARS_FP8, st, get, run)))
             return rc;
         run->h_counters = pinned_view(q->pinned).counters;
+        sv->stream_jobs += 1;
         if ((rc = tc_enqueue_batch(c, run, st))) return rc;
         MARS_CUDA(c, cudaEventRecord(q->ev, st));
         q->state = ReqState::TcRunning;
         return MARS_OK;
     }
+    sv->stream_jobs += 1;
     if (q->dev.dense) {
         MARS_CUDA(c, launch_dense(q->dev, s, dp, st));
     } else if (sp.sell) {
@@ -916,8 +1060,19 @@ void serve_progress(mars_ctx* c)
 {
     Serve* sv = serve_get(c);
     // collect
+    bool ring_pending = false;
     for (auto& kv : sv->reqs) {
         ServeReq* q = kv.second.get();
+        if (q->state == ReqState::RingRunning) {
+            const int k = (int)q->ring_job;
+            if (*reinterpret_cast<volatile int32_t*>(sv->done + k)) {
+                const int rc = serve_copy_results(c, q);  // the kernel already selected the best
+                if (rc) serve_mark_failed(c, sv, q, rc);
+            } else {
+                ring_pending = true;
+            }
+            continue;
+        }
         if (q->state != ReqState::TcRunning && q->state != ReqState::Finishing) continue;
         const cudaError_t e = cudaEventQuery(q->ev);
         if (e == cudaErrorNotReady) continue;
@@ -949,12 +1104,36 @@ void serve_progress(mars_ctx* c)
             continue;
         }
         q->state = ReqState::Done;
+        if (q->ring_job >= 0) {
+            sv->ring_refs -= 1;
+            q->ring_job = -1;
+        }
         for (auto& b : q->bufs) dev_free_on(c, &b, q->st);
         q->bufs.clear();
         if (q->slot >= 0) {
             sv->free_slots.push_back(q->slot);
             sv->inflight -= 1;
             q->slot = -1;
+        }
+    }
+    // a published job is always taken up: relaunch the serving kernel if it
+    // went idle and exited before the job's tail reached it
+    if (ring_pending) {
+        const int rc = serve_ring_ensure_kernel(c, sv);
+        if (rc) {
+            for (auto& kv : sv->reqs)
+                if (kv.second->state == ReqState::RingRunning) serve_mark_failed(c, sv, kv.second.get(), rc);
+        }
+    }
+    // reset the ring once its kernel has exited and no request reads a slot
+    if (sv->ring && sv->tail > 0 && sv->ring_refs == 0) {
+        const bool live = sv->kernel_live && cudaEventQuery(sv->ring_ev) == cudaErrorNotReady;
+        if (!live) {
+            sv->kernel_live = false;
+            if (cudaMemsetAsync(sv->ring, 0, sizeof(ServeRing), sv->pub_st) == cudaSuccess) {
+                std::memset(sv->done, 0, sizeof(int32_t) * kRingCap);
+                sv->tail = 0;
+            }
         }
     }
     // admit, in arrival order
@@ -990,6 +1169,7 @@ void serve_release(mars_ctx* c)
 {
     if (!c->serve) return;
     Serve* sv = c->serve.get();
+    serve_ring_free(sv);
     for (cudaStream_t st : sv->streams) cudaStreamSynchronize(st);
     for (auto& kv : sv->reqs) serve_free_req(c, sv, kv.second.get());
     sv->reqs.clear();
@@ -1995,6 +2175,15 @@ int mars_serve_status(mars_ctx* c, int32_t* queued, int32_t* running)
     Serve* sv = c->serve.get();
     if (queued) *queued = sv ? (int32_t)sv->queue.size() : 0;
     if (running) *running = sv ? sv->inflight : 0;
+    return MARS_OK;
+}
+
+int mars_serve_counters(mars_ctx* c, int64_t* ring_jobs, int64_t* stream_jobs)
+{
+    if (!c) return MARS_EINVAL;
+    const Serve* sv = c->serve.get();
+    if (ring_jobs) *ring_jobs = sv ? sv->ring_jobs : 0;
+    if (stream_jobs) *stream_jobs = sv ? sv->stream_jobs : 0;
     return MARS_OK;
 }
 

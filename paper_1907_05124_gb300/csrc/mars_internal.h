@@ -64,6 +64,17 @@ struct DevInstance {
     const int32_t* new2old = nullptr;  // n
 };
 
+struct DevResult {
+    double best_energy;
+    long long best_energy_i64;
+    int32_t best_replica;
+    int32_t hits;
+    double sum_energy;
+    long long sweeps;
+    long long levels;
+    long long capped;
+};
+
 // One solve's replica state and outputs (all device pointers).
 struct DevSolve {
     int32_t R = 0;
@@ -94,6 +105,12 @@ struct DevSolve {
     int32_t* capped = nullptr;         // R
     int32_t* work_counter = nullptr;   // 1
     int32_t* status = nullptr;         // 1
+    // serving ring only: replicas finished, and a host-mapped flag raised once
+    // all R have finished (both null elsewhere)
+    int32_t* finished = nullptr;
+    int32_t* done_flag = nullptr;
+    DevResult* res = nullptr;          // serving ring: the finishing CTA's argmin goes here
+    int8_t* best_out = nullptr;        // and the best replica's spins here
 };
 
 // One instance of a batched launch (kernels_sparse_sell.cu).
@@ -103,6 +120,42 @@ struct BatchJob {
     int32_t fmt = 0;
     int32_t pad = 0;
 };
+// The serving ring: job descriptors the host publishes while the persistent
+// serving kernel runs. A job's counters live in the ring (never in request
+// buffers), and the host reuses no slot while the kernel lives (it resets the
+// ring once the kernel has exited), so a CTA leaving a finished job never
+// touches freed memory or another job's counters.
+constexpr int kRingCap = 1024;
+struct RingSlot {
+    int32_t taken = 0;     // replicas taken from the job's queue
+    int32_t status = 0;    // device-side error code
+    int32_t finished = 0;  // replicas finished
+    int32_t pad = 0;
+};
+struct ServeRing {
+    BatchJob jobs[kRingCap];
+    RingSlot slots[kRingCap];
+    int32_t tail;    // jobs published (job j sits in slot j % kRingCap)
+    int32_t cursor;  // first job that may still have replicas to take
+    int32_t stop;    // exit once idle
+    int32_t pad;
+};
+// Launch shape of the serving kernel: RT slots, `threads`, dynamic shared
+// memory `smem` (the most a job may use) and the grid.
+struct RingPlan {
+    int rt = 2;
+    int threads = 1024;
+    size_t smem = 0;
+    int grid = 1;
+};
+bool plan_serve_ring(int device, RingPlan* p);
+// Coupling format a job uses under the ring's shared memory, or -1 when the
+// job's magnetisations do not fit on chip.
+int ring_job_format(const DevInstance& in, const RingPlan& p);
+// Persistent serving kernel: runs published jobs and exits after about
+// idle_polls x 2 us without new work (or when ring->stop is set).
+cudaError_t launch_serve_ring(ServeRing* ring, const RingPlan& p, int idle_polls, cudaStream_t st);
+
 struct BatchPlan {
     int rt = 1;
     int threads = 1024;
@@ -113,16 +166,7 @@ bool plan_sparse_batch(const DevInstance* ins, int count, int device, BatchPlan*
 cudaError_t launch_sparse_batch(const BatchJob* jobs, int count, int* cursor, const BatchPlan& p,
                                 cudaStream_t st);
 
-struct DevResult {
-    double best_energy;
-    long long best_energy_i64;
-    int32_t best_replica;
-    int32_t hits;
-    double sum_energy;
-    long long sweeps;
-    long long levels;
-    long long capped;
-};
+
 
 // Launchers (return cudaError_t of the launch).
 struct SparsePlan {

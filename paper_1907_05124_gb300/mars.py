@@ -104,6 +104,7 @@ SIGNATURES = {
     "mars_submit": (ctypes.c_int, [P, ctypes.c_int32, P, P]),
     "mars_poll": (ctypes.c_int, [P, ctypes.c_int64, P, P]),
     "mars_serve_status": (ctypes.c_int, [P, P, P]),
+    "mars_serve_counters": (ctypes.c_int, [P, P, P]),
     "mars_set_shape": (ctypes.c_int, [P, ctypes.c_int32, P]),
     "mars_get_shape": (ctypes.c_int, [P, ctypes.c_int32, P]),
     "mars_autotune": (ctypes.c_int, [P, ctypes.c_int32, P, ctypes.c_int32, P, P]),
@@ -462,6 +463,12 @@ class Context:
             spin_updates=r.spin_updates, levels=r.levels, capped_levels=r.capped_levels,
             gpu_seconds=r.gpu_seconds, descent_seconds=r.descent_seconds,
             energy_err_bound=r.energy_err_bound, integer=bool(r.integer), best_spins=best)
+
+    def serve_counters(self):
+        """(requests served by the persistent serving kernel, requests on their own streams)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.mars_serve_counters(self._ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def serve_status(self):
         q, rn = ctypes.c_int32(), ctypes.c_int32()

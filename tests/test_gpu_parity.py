@@ -258,6 +258,31 @@ def test_convergence_rule_sparse_agrees_with_oracle(ctx):
     ctx.free(inst)
 
 
+def test_best_energy_over_seeds_matches_oracle(ctx):
+    """Best energies over independent seeds: the library draws every seed's
+    start states on the device and the oracle draws the same replicas from the
+    published generator; the per-seed best energies must be distributed alike
+    (and, the trajectories agreeing, mostly identical)."""
+    from scipy import stats
+    csr = I.er_graph(400, 8, 41, "pm1")
+    inst = ctx.add_csr(*csr)
+    order = ctx.order(inst)
+    oi = O.Instance.csr(csr)
+    R, tmax, seeds = 24, 5.0, range(16)
+    gpu, ora = [], []
+    for sd in seeds:
+        g = ctx.solve(inst, R, 0.0, tmax, seed=sd)
+        m0, t0 = O.draw_replicas(sd, R, csr.n, 0.0, tmax)
+        o = O.mars_solve(oi, m0, t0, order=order, nthreads=8, want_m=False)
+        gpu.append(g.best_energy)
+        ora.append(float(o["energy"].min()))
+        assert g.best_energy == O.energy(oi, g.best_spins)
+    gpu, ora = np.array(gpu), np.array(ora)
+    assert np.mean(gpu == ora) >= 0.75, (gpu, ora)
+    assert stats.ks_2samp(gpu, ora).pvalue > 0.05
+    ctx.free(inst)
+
+
 def test_sk64_config_best_matches_oracle(ctx):
     """Dense SK +-1, N = 64, R = 256, T0 ~ U(0, 16), c_step 1, d_min 1e-4."""
     J = I.sk_pm1(64, 0)

@@ -103,3 +103,39 @@ def test_poll_unknown_request(ctx):
     ctx._req_n[123456] = 4
     with pytest.raises(MarsError):
         ctx.poll(123456)
+
+
+def test_ring_joins_running_launch_and_matches_blocking(ctx):
+    """Continuous batching into the persistent kernel: sparse integer requests
+    are published into the serving ring; requests submitted while a long one
+    runs join the same launch. Every result equals the blocking solve's."""
+    big = ctx.add_csr(*I.ea_lattice(60, 2, 11))
+    smalls = [ctx.add_csr(*g) for g in (I.er_graph(700, 6, 12, "pm1"), I.ea_lattice(20, 2, 13),
+                                          I.er_graph(1500, 10, 14, "one"), I.ea_lattice(8, 3, 15))]
+    ring0, _ = ctx.serve_counters()
+    reqs = {ctx.submit(big, 2048, 0.0, 4.0, seed=21): (big, 2048, 4.0, 21)}
+    time.sleep(0.002)  # the big job is on the GPU when the next ones arrive
+    for j, inst in enumerate(smalls):
+        for rep in range(3):
+            sd = 100 + 10 * j + rep
+            reqs[ctx.submit(inst, 96 + 32 * rep, 0.0, 5.0, seed=sd)] = (inst, 96 + 32 * rep, 5.0, sd)
+    out = _wait(ctx, list(reqs))
+    ring1, _ = ctx.serve_counters()
+    assert ring1 - ring0 == len(reqs)  # every one of these went through the ring
+    for r, (inst, R, tmax, sd) in reqs.items():
+        _same(out[r], ctx.solve(inst, R, 0.0, tmax, seed=sd))
+    for inst in [big] + smalls:
+        ctx.free(inst)
+
+
+def test_ring_kernel_relaunches_after_idle_exit(ctx):
+    """The serving kernel exits after about 100 us without work; a request
+    submitted later starts it again, and the ring resets once it is idle."""
+    inst = ctx.add_csr(*I.ea_lattice(16, 2, 17))
+    for wave in range(3):
+        reqs = [ctx.submit(inst, 64, 0.0, 4.0, seed=wave * 10 + k) for k in range(4)]
+        out = _wait(ctx, reqs)
+        for k, r in enumerate(reqs):
+            _same(out[r], ctx.solve(inst, 64, 0.0, 4.0, seed=wave * 10 + k))
+        time.sleep(0.05)
+    ctx.free(inst)
