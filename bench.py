@@ -74,7 +74,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip mars_autotune before the warm-up (library default launch shape)")
-    ap.add_argument("--workload", default="ea2d", choices=["ea2d", "sk8192", "sk8192pm1", "serve"],
+    ap.add_argument("--workload", default="ea2d",
+                    choices=["ea2d", "sk8192", "sk8192pm1", "serve", "ttt"],
                     help="ea2d: the 2-D lattice (default); sk8192: dense SK on tensor cores; "
                          "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
@@ -530,6 +531,61 @@ def run_serve(args, world, rank, local):
     ctx.close()
 
 
+def run_ttt(args, world, rank, local):
+    """Time to target energy of the tensor-core paths against the plain FP32 path.
+
+    Dense SK with +-1 couplings (N=4096, R=512, T0 ~ U(0, 2 sqrt(N)), C_step 1):
+    the same replicas (seed) run on the FP32 SIMT path, the BF16 tcgen05 path
+    and the FP8 (E4M3) tcgen05 path. The target is the FP32 path's
+    10th-percentile replica energy; a path whose fraction p of replicas reach
+    it in a solve of T seconds needs T ln(0.01) / ln(1 - p) to reach it with
+    probability 0.99 (independent repeats of the solve).
+    """
+    import numpy as np
+    import torch
+
+    from paper_1907_05124_gb300 import build, instances, mars
+    torch.cuda.set_device(local)
+    build.build()
+    n, R = 4096, args.replicas or 512
+    ctx = mars.Context(local)
+    inst = ctx.add_dense(instances.sk_pm1(n, 0))
+    tmax = 2.0 * n ** 0.5
+    runs = {}
+    for prec in ("fp32", "bf16", "fp8"):
+        kw = dict(c_step=1.0, d_min=D_MIN, k_max=K_MAX, seed=1, precision=prec, outputs=("energies",))
+        ctx.solve(inst, R, 0.0, tmax, **dict(kw, seed=2))  # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = ctx.solve(inst, R, 0.0, tmax, **kw)
+        runs[prec] = (time.perf_counter() - t, res)
+    target = float(np.percentile(runs["fp32"][1].energies, 10))
+    paths = {}
+    for prec, (sec, res) in runs.items():
+        p = float(np.mean(res.energies <= target))
+        ttt = sec * np.log(0.01) / np.log1p(-p) if 0 < p < 1 else (sec if p >= 1 else float("inf"))
+        paths[prec] = {"solve_s": sec, "p_target": p, "ttt99_s": ttt, "best_energy": res.best_energy,
+                       "spin_updates_per_s": res.spin_updates / sec}
+    base = paths["fp32"]["ttt99_s"]
+    for prec in paths:
+        paths[prec]["speedup_vs_fp32"] = base / paths[prec]["ttt99_s"]
+    best_tc = min(("bf16", "fp8"), key=lambda k: paths[k]["ttt99_s"])
+    line = {
+        "metric": "time to target energy (p = 0.99)", "value": paths[best_tc]["ttt99_s"], "unit": "s",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * runs[best_tc][0],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": best_tc,
+        "data": "synthetic (seeded instance, Philox start states on device)",
+        "config": {"workload": f"dense SK N={n}, J_ij uniform in {{-1,+1}}, R={R}, T0~U(0,2 sqrt(N)), "
+                               "C_step=1, d_min=1e-4, k_max=1000; target = FP32 path's "
+                               "10th-percentile energy", "n_spins": n, "replicas": R,
+                   "target_energy": target},
+        "paths": paths,
+        "speedup_vs_fp32_at_equal_ttt": paths[best_tc]["speedup_vs_fp32"],
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -538,6 +594,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, world, rank, local)
+        return
+    if args.workload == "ttt":
+        run_ttt(args, world, rank, local)
         return
     run_mars(args, world, rank, local)
 

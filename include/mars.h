@@ -261,12 +261,16 @@ int mars_solve_batch(mars_ctx* ctx, int32_t count, const int32_t* insts, const m
  *   sell_smem_table  couplings staged in shared memory when they fit, 0|1
  *   tc_rpw           dense BF16 tensor-core descent: replicas per chain warp, 1|2|4
  *   tc_overlap       panel p+1's GEMM overlapped with panel p's chain, 0|1
- * Only tc_overlap changes results: with it, the previous panel's part of a
- * panel's fields is summed in FP32 instead of through the BF16 GEMM.
+ *   tc_pair          panels 2q and 2q+1 share one GEMM (one pass over the
+ *                    magnetisations per pair of panels), 0|1; with tc_pair
+ *                    the overlap is off
+ * tc_overlap and tc_pair change results only by rounding: the previous
+ * panel's part of a panel's fields is then summed in FP32 instead of through
+ * the low-precision GEMM.
  */
 typedef struct mars_shape {
     int32_t sell_rt, sell_threads, sell_smem_table;
-    int32_t tc_rpw, tc_overlap;
+    int32_t tc_rpw, tc_overlap, tc_pair;
 } mars_shape;
 
 /* Set (shape non-NULL) or clear (NULL) an instance's launch shape.

@@ -168,6 +168,132 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) tc::tmem_dealloc(tmem, BN);
 }
 
+template <int BN>
+struct PairSmem {
+    static constexpr uint32_t kA = kBM * kBK * 2;     // one 128-row A tile
+    static constexpr uint32_t kB = BN * kBK * 2;
+    static constexpr uint32_t kStage = 2 * kA + kB;   // both panels' rows and one B tile
+    static constexpr size_t kBytes = 1024 + kStages * kStage + (2 * kStages + 1) * 8 + 16;
+};
+
+// Two panels' fields from one pass over K. Accumulator 0 (TMEM columns
+// [0, BN)) takes panel q's rows (first row g.p0) over every K block;
+// accumulator 1 (columns [BN, 2 BN)) takes panel q+1's rows over every K
+// block but panel q's own (g.skip_kb and on), since panel q's new spins reach
+// panel q+1 through its chain in FP32. Both read the same B tile, so the
+// magnetisations are streamed once per pair of panels instead of once per
+// panel. Partials go to g.G (panel q) and g.G1 (panel q+1).
+template <int BN, bool FP8>
+__global__ void __launch_bounds__(128, 1)
+    pair_gemm_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmS,
+                     TcPanel g)
+{
+    using L = PairSmem<BN>;
+    constexpr int kKE = FP8 ? 2 * kBK : kBK;
+    constexpr int kSkipN = kBM / kKE;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + kStages * L::kStage);
+    uint64_t* empty = full + kStages;
+    uint64_t* done = empty + kStages;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+
+    const int n0 = blockIdx.x * BN;
+    if (n0 >= *g.active_prefix) return;  // whole CTA, before any barrier
+    const int split = blockIdx.y;
+    const int kb0 = split * g.kblocks;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    auto own = [&](int kb) { return kb0 + kb >= g.skip_kb && kb0 + kb < g.skip_kb + kSkipN; };
+    int issued1 = 0;  // K blocks accumulator 1 takes (every thread counts them)
+    for (int kb = 0; kb < g.kblocks; ++kb) issued1 += own(kb) ? 0 : 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_barrier_init();
+        tc::tma_prefetch_desc(&tmJ);
+        tc::tma_prefetch_desc(&tmS);
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, 2 * BN);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer: panel q+1's A tile is not loaded for panel q's K blocks.
+        for (int kb = 0; kb < g.kblocks; ++kb) {
+            const int s = kb % kStages;
+            if (kb >= kStages && !tc::mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, g.err)) break;
+            unsigned char* st = smem + s * L::kStage;
+            const bool both = !own(kb);
+            tc::mbar_arrive_expect_tx(&full[s], L::kA + L::kB + (both ? L::kA : 0u));
+            tc::tma_load_2d(st, &tmJ, &full[s], (kb0 + kb) * kKE, g.p0);
+            if (both) tc::tma_load_2d(st + L::kA, &tmJ, &full[s], (kb0 + kb) * kKE, g.p0 + kBM);
+            tc::tma_load_2d(st + 2 * L::kA, &tmS, &full[s], (kb0 + kb) * kKE, n0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = FP8 ? tc::idesc_e4m3_f32(kBM, BN) : tc::idesc_bf16_f32(kBM, BN);
+        int it1 = 0;
+        for (int kb = 0; kb < g.kblocks; ++kb) {
+            const int s = kb % kStages;
+            if (!tc::mbar_wait(&full[s], (kb / kStages) & 1, g.err)) break;
+            tc::tc_fence_after();
+            const uint32_t a0 = tc::smem_addr(smem + s * L::kStage);
+            const uint32_t a1 = a0 + L::kA, b0 = a0 + 2 * L::kA;
+            const bool both = !own(kb);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t bd = tc::smem_desc_sw128(b0 + k * 32);
+                if (FP8) {
+                    tc::mma_e4m3(tmem, tc::smem_desc_sw128(a0 + k * 32), bd, idesc, (kb | k) != 0);
+                    if (both)
+                        tc::mma_e4m3(tmem + BN, tc::smem_desc_sw128(a1 + k * 32), bd, idesc, (it1 | k) != 0);
+                } else {
+                    tc::mma_bf16(tmem, tc::smem_desc_sw128(a0 + k * 32), bd, idesc, (kb | k) != 0);
+                    if (both)
+                        tc::mma_bf16(tmem + BN, tc::smem_desc_sw128(a1 + k * 32), bd, idesc, (it1 | k) != 0);
+                }
+            }
+            it1 += both ? 1 : 0;
+            tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(done);
+    }
+    __syncwarp();
+
+    const bool ok = tc::mbar_wait(done, 0, g.err);
+    tc::tc_fence_after();
+    const int row = warp * 32 + lane;
+    float* dst0 = g.G + ((size_t)split * g.R_pad + n0) * kBM + row;
+    float* dst1 = g.G1 + ((size_t)split * g.R_pad + n0) * kBM + row;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tc::tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dst0[(size_t)(c0 + j) * kBM] = v[j];
+        }
+        if (issued1 > 0) {
+            tc::tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(BN + c0), v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        }
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dst1[(size_t)(c0 + j) * kBM] = v[j];
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * BN);
+}
+
 // Per spin of the panel and replica: its field (the split-K partials in
 // split order, the previous panel's FP32 part and h, summed in FP32: beside
 // the BF16 products their rounding is immaterial, and BF16-exact operands
@@ -560,6 +686,20 @@ cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS,
     const size_t smem = tc_gemm_smem(bn);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    CUtensorMap a = tmJ, b = tmS;
+    TcPanel c = g;
+    void* args[] = {&a, &b, &c};
+    return cudaLaunchKernel(k, dim3(n_tiles, splitk), dim3(128), args, smem, st);
+}
+
+cudaError_t launch_tc_pair_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g, int n_tiles,
+                                int splitk, cudaStream_t st)
+{
+    const void* k = g.fp8 ? (const void*)pair_gemm_kernel<128, true> : (const void*)pair_gemm_kernel<128, false>;
+    const size_t smem = PairSmem<128>::kBytes;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (!g.G1 || g.skip_kb < 0) return cudaErrorInvalidValue;
     CUtensorMap a = tmJ, b = tmS;
     TcPanel c = g;
     void* args[] = {&a, &b, &c};

@@ -384,6 +384,8 @@ struct TcRun {
     // two buffers by panel parity.
     int rpw = 1;
     bool overlap = false;
+    bool pair = false;                 // panels 2q, 2q+1 share one GEMM
+    std::vector<int> timed_rows;       // rows of each GEMM the profiled sweep timed
     cudaStream_t side = nullptr;
     std::vector<cudaEvent_t> ev;
     float* Gbuf[2] = {nullptr, nullptr};
@@ -420,9 +422,9 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     // Replicas per chain warp: several per warp cut the chain's issued
     // instructions per replica and leave SMs to the overlapped GEMM. The
     // defaults are the fastest shapes measured on a GB300 at N = 8192 (ms per
-    // sweep): R = 1024, overlap with 2 per warp 1.04 (plain sweep, 1 per warp,
-    // 1.26); R = 4096, plain sweep with 4 per warp 2.06 (overlap 2.51: the
-    // chain and the GEMM then compete for SMs). mars_autotune picks per
+    // sweep): R = 1024, overlap with 2 per warp 1.04 (pairs 1.13, plain 1.26);
+    // R = 4096, panel pairs with 4 per warp 1.94 (plain 2.04, overlap 2.51:
+    // the chain and the GEMM then compete for SMs). mars_autotune picks per
     // instance.
     const LaunchShape& sh = d.shape;
     int rpw = sh.tc_rpw >= 0 ? sh.tc_rpw : env_flag("MARS_TC_RPW", R >= 2048 ? 4 : R >= 512 ? 2 : 1);
@@ -430,7 +432,8 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     run->rpw = rpw;
     const int ov = sh.tc_overlap >= 0 ? sh.tc_overlap
                                       : env_flag("MARS_TC_OVERLAP", R >= 512 && R < 2048 ? 1 : 0);
-    run->overlap = run->P >= 2 && ov != 0;
+    run->pair = run->P >= 2 && (sh.tc_pair >= 0 ? sh.tc_pair : env_flag("MARS_TC_PAIR", R >= 2048 ? 1 : 0)) != 0;
+    run->overlap = run->P >= 2 && ov != 0 && !run->pair;
     // Split K until the panel GEMM fills the SMs in one wave (one CTA per SM):
     // a short GEMM is bound by each CTA's pipeline fill and TMA bytes in
     // flight, so more, shorter CTAs finish sooner.
@@ -469,11 +472,13 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     if ((rc = get(2 * g_floats * sizeof(float), (void**)&t.G))) return rc;
     run->Gbuf[0] = t.G;
     run->Gbuf[1] = t.G + g_floats;
-    if (run->overlap) {
+    if (run->overlap || run->pair) {
         float* gx = nullptr;
         if ((rc = get(2 * (size_t)R_pad * 128 * sizeof(float), (void**)&gx))) return rc;
         run->Gx[0] = gx;
         run->Gx[1] = gx + (size_t)R_pad * 128;
+    }
+    if (run->overlap) {
         MARS_CUDA(c, cudaStreamCreateWithFlags(&run->side, cudaStreamNonBlocking));
         run->ev.resize(1 + 2 * (size_t)run->P, nullptr);
         for (cudaEvent_t& e : run->ev) MARS_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -523,6 +528,37 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
 {
     const bool ov = run->overlap;
     const int P = run->P;
+    if (timed) run->timed_rows.clear();
+    if (run->pair) {
+        // panels in pairs: one GEMM for panels pp and pp+1, chain pp (which
+        // adds its new spins to panel pp+1's fields), chain pp+1
+        const int kb_per_panel = run->g.fp8 ? 1 : 2;
+        for (int pp = 0; pp < P; pp += 2) {
+            const int e = (int)run->timed_rows.size();
+            TcPanel g = run->g;
+            g.p0 = pp * 128;
+            g.G = run->Gbuf[0];
+            const bool two = pp + 1 < P;
+            if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * e], st));
+            if (two) {
+                g.G1 = run->Gbuf[1];
+                g.skip_kb = kb_per_panel * pp;
+                MARS_CUDA(c, launch_tc_pair_gemm(run->tmJ, run->tmS, g, run->ntiles, run->splitk, st));
+            } else {
+                g.skip_kb = -1;
+                MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->ntiles, run->splitk, st));
+            }
+            if (timed) {
+                MARS_CUDA(c, cudaEventRecord(c->prof[2 * e + 1], st));
+                run->timed_rows.push_back(two ? 256 : 128);
+            }
+            MARS_CUDA(c, launch_tc_chain(run->t, pp, run->rpw, run->Gbuf[0], nullptr, two ? run->Gx[0] : nullptr,
+                                         st));
+            if (two) MARS_CUDA(c, launch_tc_chain(run->t, pp + 1, run->rpw, run->Gbuf[1], run->Gx[0], nullptr, st));
+        }
+        MARS_CUDA(c, launch_tc_advance(run->t, st));
+        return MARS_OK;
+    }
     cudaStream_t gs = ov ? run->side : st;
     if (ov) {
         MARS_CUDA(c, cudaEventRecord(run->ev[0], st));
@@ -536,7 +572,10 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
         if (ov && pp >= 2) MARS_CUDA(c, cudaStreamWaitEvent(gs, run->ev[2 + 2 * (pp - 2)], 0));
         if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp], gs));
         MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->ntiles, run->splitk, gs));
-        if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp + 1], gs));
+        if (timed) {
+            MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp + 1], gs));
+            run->timed_rows.push_back(128);
+        }
         if (ov) {
             MARS_CUDA(c, cudaEventRecord(run->ev[1 + 2 * pp], gs));
             MARS_CUDA(c, cudaStreamWaitEvent(st, run->ev[1 + 2 * pp], 0));
@@ -632,16 +671,19 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     while (state == 1) {
         const int32_t active_now = run.active_at_batch;
         if ((rc = tc_enqueue_batch(c, &run, st))) { cudaFreeHost(pinned); return rc; }
-        prof->launches += (int64_t)run.batch * (2 * run.P + 2);  // per sweep: P GEMMs, P chains, level step
+        // per sweep: the GEMMs (one per panel, or per pair), P chains, the level step and prefix
+        const int gemms = run.pair ? (run.P + 1) / 2 : run.P;
+        prof->launches += (int64_t)run.batch * (gemms + run.P + 2);
         se = cudaStreamSynchronize(st);
         if (se != cudaSuccess) break;
-        for (int pp = 0; pp < run.P; ++pp) {
+        for (size_t e = 0; e < run.timed_rows.size(); ++e) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, c->prof[2 * pp], c->prof[2 * pp + 1]);
+            cudaEventElapsedTime(&ms, c->prof[2 * e], c->prof[2 * e + 1]);
             prof->gemm_seconds += ms * 1e-3;
             prof->gemm_launches += 1;
-            prof->gemm_flops += 2.0 * 128.0 * (double)in->dev.n * (double)active_now;
+            prof->gemm_flops += 2.0 * run.timed_rows[e] * (double)in->dev.n * (double)active_now;
         }
+        run.timed_rows.clear();
         state = tc_after_batch(c, &run);
     }
     cudaFreeHost(pinned);
@@ -2009,13 +2051,14 @@ int mars_set_shape(mars_ctx* c, int32_t id, const mars_shape* shape)
         };
         if (!in_set(shape->sell_rt, {1, 2, 4}) || !in_set(shape->sell_threads, {512, 1024}) ||
             !in_set(shape->sell_smem_table, {0, 1}) || !in_set(shape->tc_rpw, {1, 2, 4}) ||
-            !in_set(shape->tc_overlap, {0, 1}))
+            !in_set(shape->tc_overlap, {0, 1}) || !in_set(shape->tc_pair, {0, 1}))
             return fail(c, MARS_EINVAL, "launch shape value outside its allowed set");
         sh.sell_rt = shape->sell_rt;
         sh.sell_threads = shape->sell_threads;
         sh.sell_smem_table = shape->sell_smem_table;
         sh.tc_rpw = shape->tc_rpw;
         sh.tc_overlap = shape->tc_overlap;
+        sh.tc_pair = shape->tc_pair;
     }
     in->dev.shape = sh;
     return MARS_OK;
@@ -2027,7 +2070,7 @@ int mars_get_shape(mars_ctx* c, int32_t id, mars_shape* out)
     Instance* in = find(c, id);
     if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
     const LaunchShape& sh = in->dev.shape;
-    *out = mars_shape{sh.sell_rt, sh.sell_threads, sh.sell_smem_table, sh.tc_rpw, sh.tc_overlap};
+    *out = mars_shape{sh.sell_rt, sh.sell_threads, sh.sell_smem_table, sh.tc_rpw, sh.tc_overlap, sh.tc_pair};
     return MARS_OK;
 }
 
@@ -2041,11 +2084,12 @@ int mars_autotune(mars_ctx* c, int32_t id, const mars_params* p, int32_t repeats
     const DevInstance& d = in->dev;
     std::vector<LaunchShape> cands;
     if (d.dense && (p->precision == MARS_BF16 || p->precision == MARS_FP8)) {
-        for (int ov = 1; ov >= 0; --ov)
+        for (int sched = 0; sched < 3; ++sched)  // plain, overlap, pairs
             for (int rpw : {1, 2, 4}) {
                 LaunchShape sh;
                 sh.tc_rpw = rpw;
-                sh.tc_overlap = ov;
+                sh.tc_overlap = sched == 1 ? 1 : 0;
+                sh.tc_pair = sched == 2 ? 1 : 0;
                 cands.push_back(sh);
             }
     } else if (!d.dense && p->update == MARS_UPDATE_GS && d.slices && (d.sell_pm1 || d.sell_gen)) {
@@ -2081,7 +2125,8 @@ int mars_autotune(mars_ctx* c, int32_t id, const mars_params* p, int32_t repeats
         }
     }
     in->dev.shape = win;
-    if (best) *best = mars_shape{win.sell_rt, win.sell_threads, win.sell_smem_table, win.tc_rpw, win.tc_overlap};
+    if (best)
+        *best = mars_shape{win.sell_rt, win.sell_threads, win.sell_smem_table, win.tc_rpw, win.tc_overlap, win.tc_pair};
     if (seconds) *seconds = best_t;
     return MARS_OK;
 }

@@ -20,6 +20,7 @@ enum DeviceStatus : int32_t { kDevOk = 0, kDevBadIndex = 1 };
 struct LaunchShape {
     int32_t sell_rt = -1, sell_threads = -1, sell_smem_table = -1;
     int32_t tc_rpw = -1, tc_overlap = -1;
+    int32_t tc_pair = -1;  // panel pairs share one GEMM (exclusive with the overlap)
 };
 
 struct DevInstance {
@@ -193,6 +194,7 @@ struct TcPanel {
     int32_t kblocks = 0;     // 64-wide K blocks per split
     int32_t R_pad = 0;
     float* G = nullptr;      // [split][R_pad][128]
+    float* G1 = nullptr;     // the second panel's partials of a paired GEMM
     int32_t skip_kb = -1;    // first K block of the panel left out (-1: none)
     int32_t fp8 = 0;         // E4M3 operands (K blocks of 128) instead of BF16 (64)
     const int32_t* active_prefix = nullptr;
@@ -236,6 +238,10 @@ constexpr int kChainMaxSplit = 16;
 // split-K fields G; gx_in (nullable) holds the previous panel's FP32 part
 // of the fields, and with gx_out (nullable) the chain writes this panel's
 // part of the next panel's fields there.
+// Panels q and q+1 (first row g.p0) in one pass over K, the second leaving
+// panel q's K blocks (from g.skip_kb) out; partials to g.G and g.G1.
+cudaError_t launch_tc_pair_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g, int n_tiles,
+                                int splitk, cudaStream_t st);
 cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, const float* gx_in,
                             float* gx_out, cudaStream_t st);
 cudaError_t launch_tc_init(const TcState& t, cudaStream_t st);

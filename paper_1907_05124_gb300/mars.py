@@ -77,7 +77,7 @@ class Shape(ctypes.Structure):
     """mars_shape: an instance's launch shape (-1 = library default)."""
     _fields_ = [("sell_rt", ctypes.c_int32), ("sell_threads", ctypes.c_int32),
                 ("sell_smem_table", ctypes.c_int32), ("tc_rpw", ctypes.c_int32),
-                ("tc_overlap", ctypes.c_int32)]
+                ("tc_overlap", ctypes.c_int32), ("tc_pair", ctypes.c_int32)]
 
 
 SIGNATURES = {
@@ -352,7 +352,7 @@ class Context:
     # -- launch shape and autotuner -------------------------------------------
     def set_shape(self, inst: int, **shape):
         """mars_set_shape: sell_rt, sell_threads, sell_smem_table, tc_rpw,
-        tc_overlap (omitted = -1, the default); no keywords clears the shape."""
+        tc_overlap, tc_pair (omitted = -1, the default); no keywords clears the shape."""
         unknown = set(shape) - {k for k, _ in Shape._fields_}
         if unknown:
             raise ValueError(f"unknown launch-shape keys {sorted(unknown)}")

@@ -322,3 +322,48 @@ def test_fp8_sk_pm1_quality(ctx):
         assert g.best_energy == O.energy(oi, g.best_spins)
         assert abs(g.best_energy - o["energy"].min()) <= 0.01 * abs(o["energy"].min())
     ctx.free(inst)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("n,R", [(512, 200), (640, 96)])
+def test_paired_panel_gemm(ctx, monkeypatch, precision, n, R):
+    """Panels 2q and 2q+1 share one GEMM: panel 2q over every K block, panel
+    2q+1 over all but panel 2q's, whose new spins reach it in FP32 through
+    chain 2q. With +-1 couplings only inside 256-spin blocks (pairs of panels)
+    and start states exact in the operand format, one contracting sweep then
+    equals the FP64 sweep to 1e-5 (n = 640 ends on an unpaired panel), for
+    every replicas-per-warp choice alike."""
+    J = block_diagonal_pm1(n, n + 1, block=256)
+    inst = ctx.add_dense(J)
+    m0 = (fp8_exact_m0 if precision == "fp8" else bf16_exact_m0)(R, n, 8)
+    t0 = np.random.default_rng(9).uniform(110.0, 114.0, size=R).astype(np.float32)
+    oi = O.Instance.dense(J)
+    o = O.mars_solve(oi, m0, t0, c_step=60.0, fixed_sweeps=1)
+    kw = dict(c_step=60.0, fixed_sweeps=1, m0=m0, t0=t0, precision=precision,
+              outputs=("m_final", "energies", "spins"))
+    monkeypatch.setenv("MARS_TC_PAIR", "1")
+    runs = []
+    for rpw in (1, 2, 4):
+        monkeypatch.setenv("MARS_TC_RPW", str(rpw))
+        runs.append(ctx.solve(inst, R, float(t0.min()), float(t0.max()), **kw))
+    err = np.abs(runs[0].m_final - o["m"]).max()
+    assert err <= 1e-5, err
+    for r in runs[1:]:
+        assert np.array_equal(r.m_final, runs[0].m_final)
+    assert np.array_equal(runs[0].energies, O.energies(oi, runs[0].spins))
+    ctx.free(inst)
+
+
+def test_paired_panels_sk_quality(ctx, monkeypatch):
+    n, R = 512, 256
+    J = I.sk_pm1(n, 7)
+    inst = ctx.add_dense(J)
+    m0, t0 = I.replica_inputs(R, n, 0.0, 48.0, 8)
+    oi = O.Instance.dense(J)
+    o = O.mars_solve(oi, m0, t0, nthreads=8, want_m=False)
+    monkeypatch.setenv("MARS_TC_PAIR", "1")
+    for prec in ("bf16", "fp8"):
+        g = ctx.solve(inst, R, 0.0, 48.0, m0=m0, t0=t0, precision=prec, outputs=("energies", "spins"))
+        assert np.array_equal(g.energies, O.energies(oi, g.spins))
+        assert abs(g.best_energy - o["energy"].min()) <= 0.01 * abs(o["energy"].min()), prec
+    ctx.free(inst)
