@@ -423,13 +423,16 @@ def run_mars(args, world, rank, local):
     else:
         achieved = gemm_flops / gemm_s / 1e12 if gemm_s > 0 else 0.0
         fp8 = wl.precision == "fp8"
+        sh = shape or {}
+        paired = sh.get("tc_pair", -1) == 1 or (sh.get("tc_pair", -1) == -1 and wl.R >= 2048)
         # an E4M3 contraction's peak: the measured BF16 peak times the nominal
         # FP8 / BF16 ratio (4.5 / 2.25 PFLOP/s dense)
         peak = peaks["bf16_tflops_sustained"] * (2.0 if fp8 else 1.0)
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": "panel_gemm_kernel<128, {}> (tcgen05 {}, split-K)".format(
-                        "FP8" if fp8 else "BF16", "kind::f8f6f4 E4M3" if fp8 else "kind::f16 BF16"),
+                    "kernel": "{}<128, {}> (tcgen05 {}, split-K)".format(
+                        "pair_gemm_kernel" if paired else "panel_gemm_kernel", "FP8" if fp8 else "BF16",
+                        "kind::f8f6f4 E4M3" if fp8 else "kind::f16 BF16"),
                     "peak_source": ("2 x bf16 sustained" if fp8 else "bf16 sustained") + f" ({peaks['source']})",
                     "gemm_launches_sampled": gemm_launches,
                     "descent_ms_mean": 1e3 * d_mean}

@@ -1,17 +1,24 @@
-// Dense MARS descent with tcgen05 tensor cores (BF16 operands, FP32 fields).
+// Dense MARS descent with tcgen05 tensor cores (BF16 or E4M3 operands, FP32
+// fields).
 //
 // A sweep visits the spins sequentially (Section 3, Algorithm 1 with the
 // per-spin update of the GPU text). For dense J every spin couples to every
 // other, so the sweep is cut into panels of 128 consecutive spins and each
-// panel p does two things, exactly reproducing the sequential sweep:
+// panel p does two things, reproducing the sequential sweep:
 //
 //   1. G = J[p, :] S^T over all active replicas, one tensor-core GEMM
 //      (panel_gemm_kernel): S holds the newest values of panels < p and the
-//      old values of panels >= p, in BF16; split-K partials in FP32.
-//   2. The panel's spins in order (panel_chain_kernel, one warp per replica):
-//      Phi_a = G_a + sum_{b in p, b < a} J_ab (s_b_new - s_b_used_in_G) + h_a,
-//      s_a = -tanh(Phi_a / T); each new s_a is folded into the remaining
-//      fields of the panel from the FP32 diagonal block of J.
+//      old values of panels >= p, in BF16 (or E4M3); split-K partials in FP32.
+//   2. The panel's spins in order (panel_chain_kernel, 1, 2 or 4 replicas per
+//      warp): Phi_a = G_a + sum_{b in p, b < a} J_ab (s_b_new - s_b_used_in_G)
+//      + h_a, s_a = -tanh(Phi_a / T); each new s_a is folded into the
+//      remaining fields of the panel from the FP32 diagonal block of J.
+//
+// Two schedules reorganise the GEMMs. With the overlap, panel p+1's GEMM
+// leaves panel p's K blocks out and runs beside chain p on a second stream;
+// with panel pairs (pair_gemm_kernel), one GEMM computes panels 2q and 2q+1.
+// Either way the left-out block reaches the next panel through the chain, in
+// FP32 from J[p][p+1].
 //
 // The GEMM is the O(n^2 R) part of the sweep; the chain adds O(n * 128 * R).
 // Replicas live in slots ordered by start temperature (longest first), so the
