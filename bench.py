@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip mars_autotune before the warm-up (library default launch shape)")
     ap.add_argument("--workload", default="ea2d",
-                    choices=["ea2d", "sk8192", "sk8192pm1", "serve", "ttt"],
+                    choices=["ea2d", "sk8192", "sk8192pm1", "serve", "ttt", "batch", "sensitivity"],
                     help="ea2d: the 2-D lattice (default); sk8192: dense SK on tensor cores; "
                          "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
@@ -534,6 +534,166 @@ def run_serve(args, world, rank, local):
     ctx.close()
 
 
+def batch_jobs(instances):
+    """The batched configuration: 8 Erdos-Renyi graphs (N in {800, 2000, 5000,
+    10000} x mean degree {6, 40}; weights {+1} for the first four, {-1,+1} for
+    the rest; seeds 0-7) and a periodic 3-D +-J lattice L=32 (N=32768, seed 8),
+    with uneven replica counts between 512 and 4096. T_max is each instance's
+    paramagnetic instability scale: about d+1 for {+1} weights (the adjacency's
+    top eigenvalue), 2 sqrt(d)+1 for +-1 weights, 6 for the 3-D lattice."""
+    graphs, k = [], 0
+    for nn in (800, 2000, 5000, 10000):
+        for d in (6, 40):
+            w = "one" if k < 4 else "pm1"
+            tmax = d + 1.0 if w == "one" else 2.0 * d ** 0.5 + 1.0
+            graphs.append((f"er_{nn}_{d}_{w}", instances.er_graph(nn, d, k, w), tmax))
+            k += 1
+    graphs.append(("ea3d_32", instances.ea_lattice(32, 3, 8), 6.0))
+    reps = [512, 4096, 1024, 2048, 512, 4096, 1024, 2048, 2048]
+    return graphs, reps
+
+
+def run_batch(args, world, rank, local):
+    """One mars_solve_batch over the batched configuration per step: uneven
+    instances and replica counts in one persistent launch."""
+    import numpy as np
+    import torch
+
+    from paper_1907_05124_gb300 import build, instances, mars
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    build.build()
+    graphs, reps = batch_jobs(instances)
+    base = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+        cores = os.cpu_count() or 1
+        t_used, upd = 0.0, 0
+        for (name, g, tmax), R in zip(graphs, reps):
+            m0, t0 = O.draw_replicas(0, cores, g.n, T_MIN, tmax)
+            t = time.perf_counter()
+            out = O.mars_solve(O.Instance.csr(g), m0, t0, c_step=1.0, d_min=D_MIN, k_max=K_MAX,
+                               order=instances.greedy_colour_order(g), nthreads=cores, want_m=False)
+            t_used += time.perf_counter() - t
+            upd += int(out["sweeps"].sum()) * g.n
+        base = {"value": upd / t_used, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+                "sample": f"{cores} replicas of each of the 9 instances, FP64 oracle, OpenMP over "
+                          f"replicas, {t_used:.1f} s"}
+    ctx = mars.Context(local)
+    insts = [ctx.add_csr(*g) for _, g, _ in graphs]
+
+    def jobs(seed):
+        return [(i, R, T_MIN, tmax, {"c_step": 1.0, "d_min": D_MIN, "k_max": K_MAX, "seed": seed + j})
+                for j, (i, R, (_, _, tmax)) in enumerate(zip(insts, reps, graphs))]
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = ctx.torch_stream
+    for w in range(max(args.warmup, 0)):
+        ctx.solve_batch(jobs(10_000 + 100 * w))
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    step_ms, updates, descent_s, launches = [], 0, [], 0
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = ctx.solve_batch(jobs(100 * k))
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        updates += sum(r.spin_updates for r in out)
+        descent_s.append(out[0].descent_seconds)
+        launches += out[0].kernel_launches
+    clocks = sampler.stop()
+    tot_ms = sum(step_ms)
+    # end to end: ingest every instance from host memory, batch-solve, read back
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    e2e_ins = [ctx.add_csr(*g) for _, g, _ in graphs]
+    saved, insts[:] = list(insts), e2e_ins
+    out = ctx.solve_batch(jobs(7))
+    for i in e2e_ins:
+        ctx.free(i)
+    e2e_t = time.perf_counter() - t
+    insts[:] = saved
+    e2e_u = sum(r.spin_updates for r in out)
+    h2d = sum(int(g.row_ptr.nbytes + g.col.nbytes + g.val.nbytes) for _, g, _ in graphs)
+    d2h = sum(g.n + 64 for _, g, _ in graphs)
+    sfu_updates_per_clk = 1.0 / (1.0 / 32.0 + 1.0 / 16.0)
+    sm_clock_ghz = (clocks.get("sm_max_mhz") or 2070.0) / 1e3
+    achieved = updates / sum(descent_s)
+    peak = 152 * sfu_updates_per_clk * sm_clock_ghz * 1e9
+    line = {
+        "metric": "spin-updates/s", "value": updates / (tot_ms * 1e-3), "unit": "spin-updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded instances, Philox start states on device)",
+        "config": {"workload": "batched: 8 Erdos-Renyi graphs (N 800-10000, mean degree 6/40, weights "
+                               "+1 or +-1) and a periodic 3-D +-J lattice L=32, R 512-4096 per instance, "
+                               "one persistent launch", "instances": [g[0] for g in graphs],
+                   "replicas": reps, "c_step": 1.0, "d_min": D_MIN, "k_max": K_MAX,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "1 GPU"},
+        "e2e": {"value": e2e_u / e2e_t, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "spin-updates/s (SFU-bound)", "frac": achieved / peak, "traffic": None,
+                     "kernel": "sparse_sell_batch_kernel (persistent, jobs in order)",
+                     "peak_source": "152 SMs x (1/32 + 1/16 SFU clocks per tanh)^-1 x SM clock",
+                     "descent_ms_mean": 1e3 * sum(descent_s) / len(descent_s)},
+        "cpu_baseline": base,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_sensitivity(args, world, rank, local):
+    """The sensitivity study of the paper's Section 4 on synthetic SK: best and
+    mean energy and the fraction P of replicas reaching the best, against the
+    number of replicas (1e2, 1e3, 1e4; T0 ~ U(0, lambda) with lambda = 2
+    sqrt(N/3), the semicircle edge of U(-1,1) couplings) and against the start
+    window ([0,10], [10,20], [20,30]; 1e3 replicas). Couplings uniform in
+    (-1, 1), N = 500, 1000, 2000, the FP32 path, C_step 1, d_min 1e-4."""
+    import numpy as np
+    import torch
+
+    from paper_1907_05124_gb300 import build, instances, mars
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    build.build()
+    ctx = mars.Context(local)
+    cells = []
+    t_all = time.perf_counter()
+    for n in (500, 1000, 2000):
+        inst = ctx.add_dense(instances.sk_uniform(n, n))
+        lam = 2.0 * (n / 3.0) ** 0.5
+        runs = [("replicas", R, 0.0, lam) for R in (100, 1000, 10000)]
+        runs += [("window", 1000, lo, hi) for lo, hi in ((0.0, 10.0), (10.0, 20.0), (20.0, 30.0))]
+        for kind, R, lo, hi in runs:
+            t = time.perf_counter()
+            r = ctx.solve(inst, R, lo, hi, c_step=1.0, d_min=D_MIN, k_max=K_MAX, seed=n + R,
+                          outputs=("energies",))
+            cells.append({"n": n, "study": kind, "replicas": R, "t_window": [lo, hi],
+                          "best": r.best_energy, "mean": r.mean_energy, "P": r.hits / R,
+                          "levels_mean": r.levels / R, "solve_s": time.perf_counter() - t})
+        ctx.free(inst)
+    line = {"metric": "sensitivity table (best, mean, P)", "value": None, "unit": None, "n_gpus": 1,
+            "higher_is_better": None, "dtype": "f32", "data": "synthetic (seeded SK instances)",
+            "config": {"workload": "SK J_ij ~ U(-1,1), N 500/1000/2000; replicas 1e2/1e3/1e4 at "
+                                   "T0 ~ U(0, 2 sqrt(N/3)); windows [0,10]/[10,20]/[20,30] at 1e3 "
+                                   "replicas; FP32 sequential sweeps, C_step 1"},
+            "cells": cells, "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_ttt(args, world, rank, local):
     """Time to target energy of the tensor-core paths against the plain FP32 path.
 
@@ -600,6 +760,12 @@ def main():
         return
     if args.workload == "ttt":
         run_ttt(args, world, rank, local)
+        return
+    if args.workload == "batch":
+        run_batch(args, world, rank, local)
+        return
+    if args.workload == "sensitivity":
+        run_sensitivity(args, world, rank, local)
         return
     run_mars(args, world, rank, local)
 

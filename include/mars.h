@@ -223,8 +223,9 @@ typedef struct {
     double gemm_seconds;
     int64_t gemm_launches;
     double gemm_flops;
-    /* Kernels mars_solve launched for this result (a captured sweep's graph
-     * nodes counted one by one); 0 from the batch and serving calls. */
+    /* Kernels launched for this result (a captured sweep's graph nodes
+     * counted one by one); mars_solve_batch reports the whole batch's count
+     * in every job's result; 0 from the serving calls. */
     int64_t kernel_launches;
 } mars_result;
 

@@ -86,7 +86,7 @@ def _load():
         _lib.or_mars_solve.restype = ctypes.c_int
         _lib.or_mars_solve.argtypes = [P, P, ctypes.c_int32, P, P, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_int32, ctypes.c_int32, P, P, P, P]
+                                       ctypes.c_int32, P, ctypes.c_int32, P, P, P, P]
         _lib.or_philox4x32_10.restype = None
         _lib.or_philox4x32_10.argtypes = [P, P, P]
         _lib.or_draw_replicas.restype = None
@@ -187,9 +187,20 @@ def bruteforce(inst: Instance, tol: float = 0.0):
     return e.value, s, cnt.value
 
 
+class Schedule(ctypes.Structure):
+    """or_schedule: the paper's linear cooling when geometric and quench are 0."""
+    _fields_ = [("geometric", ctypes.c_int32), ("ratio", ctypes.c_double),
+                ("t_floor", ctypes.c_double), ("quench", ctypes.c_int32)]
+
+
 def mars_solve(inst: Instance, m0, t0, *, c_step=1.0, d_min=1e-4, k_max=1000, fixed_sweeps=0,
-               update=UPDATE_GS, order=None, nthreads=1, want_m=True):
-    """Run Algorithm 1 for every replica; returns a dict of per-replica results."""
+               update=UPDATE_GS, order=None, nthreads=1, want_m=True, geometric=None,
+               t_floor=0.0, quench=False):
+    """Run Algorithm 1 for every replica; returns a dict of per-replica results.
+
+    geometric=r (0 < r < 1) cools T <- r T while T > t_floor instead of the
+    paper's T <- T - c_step; quench=True adds the final T -> 0+ level
+    (s_i <- -sgn(Phi_i)). Both are labelled variants, off by default."""
     m0 = np.ascontiguousarray(m0, dtype=np.float32)
     t0 = np.ascontiguousarray(t0, dtype=np.float32)
     R = t0.shape[0]
@@ -203,10 +214,11 @@ def mars_solve(inst: Instance, m0, t0, *, c_step=1.0, d_min=1e-4, k_max=1000, fi
     en = np.zeros(R, dtype=np.float64)
     st = (ReplicaStats * max(R, 1))()
     c = inst._c()
+    sch = Schedule(1 if geometric else 0, float(geometric or 0.0), float(t_floor), 1 if quench else 0)
     rc = _load().or_mars_solve(ctypes.byref(c), _ptr(order_a), R, _ptr(m0), _ptr(t0),
                                float(c_step), float(d_min), int(k_max), int(fixed_sweeps),
-                               int(update), int(nthreads), _ptr(m_out), _ptr(sig), _ptr(en),
-                               ctypes.addressof(st))
+                               int(update), ctypes.byref(sch), int(nthreads), _ptr(m_out), _ptr(sig),
+                               _ptr(en), ctypes.addressof(st))
     if rc != 0:
         raise ValueError("oracle rejected the inputs")
     stats = {k: np.array([getattr(st[r], k) for r in range(R)])

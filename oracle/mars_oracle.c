@@ -207,46 +207,72 @@ double or_local_field(const or_instance* in, const double* s, int32_t i)
  *    a Jacobi sweep computes every new value from the old vector first;
  *  - Phi_i includes the field h_i (Eq. 2 has it; Algorithm 1 drops it for h=0).
  */
+/* -sgn(phi), the update's T -> 0+ limit (0 for phi = 0) */
+static double quench_value(double phi) { return phi > 0.0 ? -1.0 : (phi < 0.0 ? 1.0 : 0.0); }
+
+/* One sweep at temperature T (T = 0 selects the quench update); returns d. */
+static double sweep(const or_instance* in, const int32_t* order, double* m, double T, int32_t update,
+                    double* scratch)
+{
+    const int32_t n = in->n;
+    double d = 0.0;
+    if (update == OR_UPDATE_GS) {
+        for (int32_t q = 0; q < n; ++q) {
+            int32_t i = order ? order[q] : q;
+            double phi = or_local_field(in, m, i);
+            double shat = T > 0.0 ? -tanh(phi / T) : quench_value(phi);
+            double diff = fabs(shat - m[i]);
+            if (diff > d) d = diff;
+            m[i] = shat;
+        }
+    } else {
+        for (int32_t i = 0; i < n; ++i) {
+            double phi = or_local_field(in, m, i);
+            scratch[i] = T > 0.0 ? -tanh(phi / T) : quench_value(phi);
+            double diff = fabs(scratch[i] - m[i]);
+            if (diff > d) d = diff;
+        }
+        memcpy(m, scratch, sizeof(double) * (size_t)n);
+    }
+    return d;
+}
+
 int or_mars_replica(const or_instance* in, const int32_t* order, double* m, double t0,
                     double c_step, double d_min, int32_t k_max, int32_t fixed_sweeps,
-                    int32_t update, double* scratch, or_replica_stats* st)
+                    int32_t update, double* scratch, const or_schedule* sch, or_replica_stats* st)
 {
     if (!in || !m || in->n < 0 || !(c_step > 0) || k_max < 1 || fixed_sweeps < 0) return -1;
     if (update == OR_UPDATE_JACOBI && !scratch) return -1;
-    const int32_t n = in->n;
+    const int geometric = sch && sch->geometric;
+    if (geometric && !(sch->ratio > 0.0 && sch->ratio < 1.0 && sch->t_floor > 0.0)) return -1;
     or_replica_stats s = {0, 0, 0, 0.0, 0.0};
     double T = t0;
     for (;;) {
-        T = T - c_step;
-        if (!(T > 0.0)) break;
+        T = geometric ? T * sch->ratio : T - c_step;
+        if (!(T > (geometric ? sch->t_floor : 0.0))) break;
         s.levels += 1;
         s.final_T = T;
         int32_t k = 0;
         double d;
         do {
-            d = 0.0;
-            if (update == OR_UPDATE_GS) {
-                for (int32_t q = 0; q < n; ++q) {
-                    int32_t i = order ? order[q] : q;
-                    double phi = or_local_field(in, m, i);
-                    double shat = -tanh(phi / T);
-                    double diff = fabs(shat - m[i]);
-                    if (diff > d) d = diff;
-                    m[i] = shat;
-                }
-            } else {
-                for (int32_t i = 0; i < n; ++i) {
-                    double phi = or_local_field(in, m, i);
-                    scratch[i] = -tanh(phi / T);
-                    double diff = fabs(scratch[i] - m[i]);
-                    if (diff > d) d = diff;
-                }
-                memcpy(m, scratch, sizeof(double) * (size_t)n);
-            }
+            d = sweep(in, order, m, T, update, scratch);
             k += 1;
             s.sweeps += 1;
         } while (fixed_sweeps > 0 ? (k < fixed_sweeps) : (d > d_min && k < k_max));
         if (fixed_sweeps == 0 && d > d_min) s.capped_levels += 1;
+        s.last_d = d;
+    }
+    if (sch && sch->quench) {
+        s.levels += 1;
+        s.final_T = 0.0;
+        int32_t k = 0;
+        double d;
+        do {
+            d = sweep(in, order, m, 0.0, update, scratch);
+            k += 1;
+            s.sweeps += 1;
+        } while (d > d_min && k < k_max);
+        if (d > d_min) s.capped_levels += 1;
         s.last_d = d;
     }
     if (st) *st = s;
@@ -255,8 +281,8 @@ int or_mars_replica(const or_instance* in, const int32_t* order, double* m, doub
 
 int or_mars_solve(const or_instance* in, const int32_t* order, int32_t R, const float* m0,
                   const float* t0, double c_step, double d_min, int32_t k_max,
-                  int32_t fixed_sweeps, int32_t update, int32_t nthreads, double* m_out,
-                  int8_t* sigma_out, double* energy_out, or_replica_stats* stats_out)
+                  int32_t fixed_sweeps, int32_t update, const or_schedule* sch, int32_t nthreads,
+                  double* m_out, int8_t* sigma_out, double* energy_out, or_replica_stats* stats_out)
 {
     if (!in || R < 0 || !m0 || !t0) return -1;
     const int32_t n = in->n;
@@ -272,7 +298,7 @@ int or_mars_solve(const or_instance* in, const int32_t* order, int32_t R, const 
         for (int32_t i = 0; i < n; ++i) m[i] = (double)m0[(int64_t)r * n + i];
         or_replica_stats st;
         if (or_mars_replica(in, order, m, (double)t0[r], c_step, d_min, k_max, fixed_sweeps,
-                            update, m + n, &st) != 0)
+                            update, m + n, sch, &st) != 0)
             bad |= 1;
         for (int32_t i = 0; i < n; ++i) sg[i] = m[i] >= 0.0 ? 1 : -1;
         if (m_out) memcpy(m_out + (int64_t)r * n, m, sizeof(double) * (size_t)n);

@@ -47,6 +47,24 @@ typedef struct {
 
 enum { OR_UPDATE_GS = 0, OR_UPDATE_JACOBI = 1 };
 
+/*
+ * Cooling schedule. NULL (or all zero) is the paper's Algorithm 1: T <- T -
+ * C_step before each level, levels while T > 0. The rest are labelled
+ * variants, not the paper's schedule:
+ *   geometric: T <- ratio * T before each level (0 < ratio < 1), levels
+ *              while T > t_floor (> 0);
+ *   quench:    after the last level, one more level at the T -> 0+ limit of
+ *              the update, s_i <- -sgn(Phi_i) with 0 for Phi_i = 0 (Algorithm
+ *              1's last decrement taken to T = 0), sweeps until no spin
+ *              changes (d = 0 <= d_min) or k_max; it counts as a level.
+ */
+typedef struct {
+    int32_t geometric;
+    double ratio;
+    double t_floor;
+    int32_t quench;
+} or_schedule;
+
 /* Phi_i = sum_{j != i} J_ij s_j + h_i, summed in column order, then h added. */
 double or_local_field(const or_instance* in, const double* s, int32_t i);
 
@@ -54,12 +72,14 @@ double or_local_field(const or_instance* in, const double* s, int32_t i);
  * One replica of Algorithm 1. m holds s on entry (the start state) and the
  * final s on return. order is the sweep's spin order (NULL = 0..n-1).
  * fixed_sweeps > 0 replaces the stopping rule by exactly that many sweeps per
- * level. update selects sequential (GS) or synchronous (Jacobi) sweeps.
- * scratch: n doubles, needed for Jacobi only. Returns 0, or -1 on bad input.
+ * level (the quench level keeps its own rule). update selects sequential (GS)
+ * or synchronous (Jacobi) sweeps. scratch: n doubles, needed for Jacobi only.
+ * sch: the cooling schedule (NULL = the paper's). Returns 0, or -1 on bad
+ * input.
  */
 int or_mars_replica(const or_instance* in, const int32_t* order, double* m, double t0,
                     double c_step, double d_min, int32_t k_max, int32_t fixed_sweeps,
-                    int32_t update, double* scratch, or_replica_stats* st);
+                    int32_t update, double* scratch, const or_schedule* sch, or_replica_stats* st);
 
 /*
  * R replicas with start states m0 (R*n floats, replica-major) and start
@@ -70,8 +90,8 @@ int or_mars_replica(const or_instance* in, const int32_t* order, double* m, doub
  */
 int or_mars_solve(const or_instance* in, const int32_t* order, int32_t R, const float* m0,
                   const float* t0, double c_step, double d_min, int32_t k_max,
-                  int32_t fixed_sweeps, int32_t update, int32_t nthreads, double* m_out,
-                  int8_t* sigma_out, double* energy_out, or_replica_stats* stats_out);
+                  int32_t fixed_sweeps, int32_t update, const or_schedule* sch, int32_t nthreads,
+                  double* m_out, int8_t* sigma_out, double* energy_out, or_replica_stats* stats_out);
 
 /* Exact energy of spins (entries +-1), rounded once to the nearest double. */
 double or_energy(const or_instance* in, const int8_t* sigma);

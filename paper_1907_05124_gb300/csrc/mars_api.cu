@@ -1904,6 +1904,8 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
     std::vector<BatchJob> jobs(count);
     std::vector<DevResult*> dres(count);
     std::vector<int8_t*> dbest(count);
+    std::vector<std::vector<float>> t0h_all(count);
+    int64_t launches = 0;
     for (int32_t j = 0; j < count; ++j) {
         const mars_params* p = &params[j];
         Instance* in = find(c, insts[j]);
@@ -1930,12 +1932,14 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
         const bool pdev = p->flags & MARS_DEVICE_PTR;
         float* t0 = nullptr;
         if ((rc = S.get(R, &t0))) return rc;
-        std::vector<float> t0h(R);
+        std::vector<float>& t0h = t0h_all[j];
+        t0h.resize(R);
         if (p->t0) {
             MARS_CUDA(c, cudaMemcpyAsync(t0, p->t0, R * sizeof(float),
                                          pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
         } else {
             MARS_CUDA(c, launch_draw(p->seed, p->stream, 0, R, 0, p->t_min, p->t_max, nullptr, t0, st));
+            ++launches;
         }
         MARS_CUDA(c, cudaMemcpyAsync(t0h.data(), t0, R * sizeof(float), cudaMemcpyDeviceToHost, st));
         s.t0 = t0;
@@ -1961,7 +1965,15 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
         MARS_CUDA(c, cudaMemsetAsync(s.work_counter, 0, 2 * sizeof(int32_t), st));
         if ((rc = S.get(1, &dres[j]))) return rc;
         if ((rc = S.get(n, &dbest[j]))) return rc;
-        MARS_CUDA(c, cudaStreamSynchronize(st));
+        jobs[j].in = in->dev;
+    }
+    // every job's start temperatures, read back once
+    MARS_CUDA(c, cudaStreamSynchronize(st));
+    for (int32_t j = 0; j < count; ++j) {
+        const mars_params* p = &params[j];
+        const std::vector<float>& t0h = t0h_all[j];
+        DevSolve& s = jobs[j].s;
+        const int32_t R = p->replicas;
         for (float v : t0h)
             if (!std::isfinite(v) || v / p->c_step > kMaxLevels)
                 return fail(c, MARS_EINVAL, "job %d: start temperatures out of range", j);
@@ -1974,7 +1986,6 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
         s.tile_rep = dq;
         s.ntiles = R;
         s.rt = 1;
-        jobs[j].in = in->dev;
     }
     BatchPlan bp;
     std::vector<int> fmts(count);
@@ -1990,11 +2001,15 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
     MARS_CUDA(c, cudaEventRecord(c->ev0, st));
     MARS_CUDA(c, launch_sparse_batch(djobs, count, cursor, bp, st));
     MARS_CUDA(c, cudaEventRecord(c->ev2, st));
+    ++launches;
     for (int32_t j = 0; j < count; ++j) {
         const DevSolve& s = jobs[j].s;
-        if (!dins[j].integer && dins[j].exact_ok)
+        if (!dins[j].integer && dins[j].exact_ok) {
             MARS_CUDA(c, launch_energy(dins[j], s.sigma, s.R, s.energy, nullptr, s.status, st));
+            ++launches;
+        }
         MARS_CUDA(c, launch_best(s, dins[j].n, dins[j].integer, dbest[j], dres[j], st));
+        ++launches;
     }
     MARS_CUDA(c, cudaEventRecord(c->ev1, st));
     std::vector<DevResult> hres(count);
@@ -2032,6 +2047,7 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
                                   ? 0.0
                                   : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + dins[j].n);
         r->status = MARS_OK;
+        r->kernel_launches = launches;  // the whole batch's
     }
     return MARS_OK;
 }

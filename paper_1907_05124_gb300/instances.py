@@ -86,6 +86,15 @@ def sk_gauss(n: int, seed: int, sigma: float | None = None) -> np.ndarray:
     return _symmetric_from_upper(upper)
 
 
+def sk_uniform(n: int, seed: int) -> np.ndarray:
+    """Dense SK instance with J_ij uniform in (-1, 1) (i<j), mirrored, zero
+    diagonal: the coupling scale (standard deviation 1/sqrt(3)) that the
+    paper's printed SK energies and temperature windows correspond to."""
+    rng = np.random.default_rng(seed)
+    upper = rng.uniform(-1.0, 1.0, size=(n, n))
+    return _symmetric_from_upper(upper)
+
+
 def _csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray) -> Csr:
     """Symmetric CSR from an undirected edge list (each edge listed once)."""
     rows = np.concatenate([src, dst]).astype(np.int64)

@@ -425,7 +425,7 @@ class Context:
                 mean_energy=r.mean_energy, sweeps=r.sweeps, spin_updates=r.spin_updates,
                 levels=r.levels, capped_levels=r.capped_levels, gpu_seconds=r.gpu_seconds,
                 descent_seconds=r.descent_seconds, energy_err_bound=r.energy_err_bound,
-                integer=bool(r.integer), best_spins=bests[j]))
+                integer=bool(r.integer), best_spins=bests[j], kernel_launches=r.kernel_launches))
         return out
 
     # -- serving ------------------------------------------------------------------

@@ -363,3 +363,71 @@ def test_antiferromagnet_lattice_reaches_checkerboard():
     m0, t0 = I.replica_inputs(32, csr.n, 0.0, 4.0, 2)
     r = O.mars_solve(O.Instance.csr(csr), m0, t0, order=I.greedy_colour_order(csr))
     assert r["energy"].min() == -csr.nnz // 2
+
+
+# --------------------------------------------------------------------------
+# cooling-schedule variants (labelled, not the paper's): geometric, quench
+# --------------------------------------------------------------------------
+
+def test_geometric_levels_closed_form():
+    """Fields only, geometric cooling T <- r T while T > t_floor: the levels
+    are t0 r, t0 r^2, ... down to the last one above t_floor, each landing on
+    -tanh(h / T) in exactly two sweeps."""
+    n = 40
+    h = np.linspace(-1.5, 1.9, n)
+    inst = O.Instance.dense(np.zeros((n, n)), h)
+    r, floor_ = 0.75, 0.2
+    t0 = np.array([3.0, 0.9, 0.25, 0.2], dtype=np.float32)
+    m0 = np.zeros((t0.size, n), dtype=np.float32)
+    out = O.mars_solve(inst, m0, t0, geometric=r, t_floor=floor_)
+    for k, t in enumerate(t0.astype(np.float64)):
+        levels, T = 0, t
+        while T * r > floor_:
+            T *= r
+            levels += 1
+        assert out["levels"][k] == levels
+        assert out["sweeps"][k] == 2 * levels
+        if levels:
+            assert out["final_T"][k] == T
+            np.testing.assert_allclose(out["m"][k], -np.tanh(h / T), rtol=4e-16, atol=1e-300)
+        else:
+            assert np.all(out["m"][k] == 0.0)
+
+
+def test_quench_fields_only_closed_form():
+    """The quench level takes the update's T -> 0+ limit, s_i = -sgn(Phi_i):
+    with fields only it lands on -sgn(h) in one sweep and stops after the
+    second (no change); a zero field gives 0."""
+    h = np.array([-2.0, -1e-9, 0.0, 3e-12, 0.5, 7.0])
+    n = h.size
+    inst = O.Instance.dense(np.zeros((n, n)), h)
+    m0 = np.random.default_rng(1).uniform(-1, 1, size=(2, n)).astype(np.float32)
+    t0 = np.array([0.5, 2.5], dtype=np.float32)  # no level, then two linear levels
+    out = O.mars_solve(inst, m0, t0, quench=True)
+    assert np.array_equal(out["m"][0], -np.sign(h))
+    assert np.array_equal(out["m"][1], -np.sign(h))
+    assert list(out["levels"]) == [1, 3]
+    assert list(out["sweeps"]) == [2, 2 * 2 + 2]
+    assert list(out["final_T"]) == [0.0, 0.0]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_quench_ends_in_single_flip_local_minimum(seed):
+    """After the quench level converges every spin sits against its field, so
+    no single flip lowers the exact energy (E changes by -2 sigma_i Phi_i >= 0
+    under a flip of i). With N = 40 (+-1 couplings) every field of a +-1
+    state is an odd integer, never 0."""
+    n = 40
+    J = I.sk_pm1(n, seed)
+    inst = O.Instance.dense(J)
+    m0, t0 = I.replica_inputs(16, n, 0.0, 12.0, seed + 10)
+    out = O.mars_solve(inst, m0, t0, quench=True)
+    for r in range(16):
+        m = out["m"][r]
+        assert np.all(np.abs(m) == 1.0), m  # converged onto +-1 spins
+        sig = out["sigma"][r]
+        e = O.energy(inst, sig)
+        for i in range(n):
+            flip = sig.copy()
+            flip[i] = -flip[i]
+            assert O.energy(inst, flip) >= e
