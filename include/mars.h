@@ -161,7 +161,17 @@ int mars_instance_order(mars_ctx* ctx, int32_t inst, int32_t* order_out);
  *                original spin labels, values in [-1, 1]) and t0 R floats;
  *                NULL draws them as above
  *  flags         MARS_DEVICE_PTR if m0/t0 are device pointers; MARS_POLISH_FP32
+ *  schedule      MARS_SCHEDULE_LINEAR (default, the paper's: T <- T - c_step
+ *                while T > 0) or MARS_SCHEDULE_GEOMETRIC (a labelled variant:
+ *                T <- cool_ratio T while T > t_floor, 0 < cool_ratio < 1,
+ *                t_floor > 0, at most 1e6 levels)
+ *  quench        nonzero: after the last level, one more level at the T -> 0+
+ *                limit of the update, s_i <- -sgn(Phi_i) (0 for a zero
+ *                field), until no spin changes or k_max sweeps (a labelled
+ *                variant: Algorithm 1's last decrement taken to T = 0); it
+ *                counts as a level and ignores fixed_sweeps
  */
+typedef enum { MARS_SCHEDULE_LINEAR = 0, MARS_SCHEDULE_GEOMETRIC = 1 } mars_schedule;
 typedef struct {
     int32_t replicas;
     double t_min, t_max, c_step, d_min;
@@ -174,6 +184,9 @@ typedef struct {
     const float* m0;
     const float* t0;
     uint32_t flags;
+    int32_t schedule;
+    double cool_ratio, t_floor;
+    int32_t quench;
 } mars_params;
 
 /* Fill p with the paper's defaults: c_step 1, d_min 1e-4, k_max 1000, GS, FP32. */

@@ -9,6 +9,7 @@
 // warp on the SM. This is the plain FP32 path the tensor-core path is checked
 // against; it is exact in its arithmetic order, not fast for large n.
 #include "device_common.cuh"
+#include "schedule.cuh"
 #include "mars_internal.h"
 
 #include <algorithm>
@@ -71,9 +72,16 @@ __global__ void __launch_bounds__(kDenseWarps * 32) dense_descent_kernel(DevInst
     }
     __syncwarp();
 
-    double T = s.t_first ? s.t_first[r] : (double)s.t0[r] - s.c_step;
-    bool act = T > 0.0;
-    float invT = act ? (float)(1.0 / T) : 0.f;
+    // the first level (schedule.cuh), or the given one (the FP32 polish)
+    double T = 0.0;
+    bool act;
+    if (s.t_first) {
+        T = s.t_first[r];
+        act = T > 0.0;
+    } else {
+        act = sched_first(s, (double)s.t0[r], &T);
+    }
+    float invT = act ? sched_inv_t(T) : 0.f;
     int levels = act ? 1 : 0, sweeps = 0, capped = 0, lvl_sweeps = 0;
 
     while (act) {
@@ -96,15 +104,14 @@ __global__ void __launch_bounds__(kDenseWarps * 32) dense_descent_kernel(DevInst
         }
         ++sweeps;
         ++lvl_sweeps;
-        const bool level_done = s.fixed_sweeps > 0 ? lvl_sweeps >= s.fixed_sweeps
-                                                   : (d <= s.d_min || lvl_sweeps >= s.k_max);
+        const bool fixed = sched_fixed(s, T);
+        const bool level_done = fixed ? lvl_sweeps >= s.fixed_sweeps : (d <= s.d_min || lvl_sweeps >= s.k_max);
         if (level_done) {
-            if (s.fixed_sweeps == 0 && !(d <= s.d_min)) ++capped;
-            T = T - s.c_step;
+            if (!fixed && !(d <= s.d_min)) ++capped;
             lvl_sweeps = 0;
-            if (T > 0.0 && !s.one_level) {
+            if (!s.one_level && sched_advance(s, &T)) {
                 ++levels;
-                invT = (float)(1.0 / T);
+                invT = sched_inv_t(T);
             } else {
                 act = false;
             }

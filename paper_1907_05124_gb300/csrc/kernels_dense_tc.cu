@@ -25,6 +25,7 @@
 // active ones form a prefix and the GEMM skips tiles past it.
 #include "device_common.cuh"
 #include "mars_internal.h"
+#include "schedule.cuh"
 #include "tc_primitives.cuh"
 
 #include <cuda_bf16.h>
@@ -557,10 +558,10 @@ __global__ void tc_init_kernel(TcState t)
             t.Sb[idx] = __float2bfloat16_rn(v);
     }
     for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < t.R; slot += gridDim.x * blockDim.x) {
-        const double T = (double)t.t0[t.rep[slot]] - t.c_step;
-        const bool act = T > 0.0;
+        double T;
+        const bool act = sched_first(t, (double)t.t0[t.rep[slot]], &T);
         t.T[slot] = T;
-        t.invT[slot] = act ? (float)(1.0 / T) : 0.f;
+        t.invT[slot] = act ? sched_inv_t(T) : 0.f;
         t.active[slot] = act;
         t.levels[slot] = act ? 1 : 0;
         t.lvl_sweeps[slot] = 0;
@@ -579,16 +580,16 @@ __global__ void tc_advance_kernel(TcState t)
         t.d[slot] = 0.f;
         const int ls = t.lvl_sweeps[slot] + 1;
         t.sweeps[slot] += 1;
-        const bool level_done = t.fixed_sweeps > 0 ? ls >= t.fixed_sweeps
-                                                   : (dd <= t.d_min || ls >= t.k_max);
+        double T = t.T[slot];
+        const bool fixed = sched_fixed(t, T);
+        const bool level_done = fixed ? ls >= t.fixed_sweeps : (dd <= t.d_min || ls >= t.k_max);
         if (level_done) {
-            if (t.fixed_sweeps == 0 && !(dd <= t.d_min)) t.capped[slot] += 1;
-            const double T = t.T[slot] - t.c_step;
-            t.T[slot] = T;
+            if (!fixed && !(dd <= t.d_min)) t.capped[slot] += 1;
             t.lvl_sweeps[slot] = 0;
-            if (T > 0.0) {
+            if (sched_advance(t, &T)) {
+                t.T[slot] = T;
                 t.levels[slot] += 1;
-                t.invT[slot] = (float)(1.0 / T);
+                t.invT[slot] = sched_inv_t(T);
             } else {
                 t.active[slot] = 0;
             }
@@ -669,7 +670,7 @@ __global__ void tc_export_kernel(TcState t, DevInstance in, float* m_out, double
         m_out[(size_t)r * t.n + __ldg(in.new2old + a)] = t.S[(size_t)slot * t.n_pad + a];
     }
     for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < t.R; slot += gridDim.x * blockDim.x)
-        t_last[t.rep[slot]] = t.levels[slot] > 0 ? t.T[slot] + t.c_step : 0.0;
+        t_last[t.rep[slot]] = t.levels[slot] > 0 ? t.T[slot] : 0.0;  // the last level's T (0: a quench)
 }
 
 }  // namespace

@@ -18,6 +18,7 @@
 // per-replica running max d and the per-replica state live in registers and a
 // handful of shared words.
 #include "device_common.cuh"
+#include "schedule.cuh"
 #include "mars_internal.h"
 
 #include <algorithm>
@@ -62,11 +63,11 @@ __global__ void __launch_bounds__(kThreads) sparse_descent_kernel(DevInstance in
             m[idx] = v;
         }
         if (tid < RT) {
-            // first level: T = t0 - c_step, visited only while T > 0
-            const double T = (r >= 0 ? (double)s.t0[r] : 0.0) - s.c_step;
-            const bool act = r >= 0 && T > 0.0;
+            // the first level (schedule.cuh)
+            double T = 0.0;
+            const bool act = r >= 0 && sched_first(s, (double)s.t0[r], &T);
             s_T[tid] = T;
-            s_invT[tid] = act ? (float)(1.0 / T) : 0.f;
+            s_invT[tid] = act ? sched_inv_t(T) : 0.f;
             s_active[tid] = act;
             s_levels[tid] = act ? 1 : 0;
             s_lvl_sweeps[tid] = 0;
@@ -120,16 +121,16 @@ __global__ void __launch_bounds__(kThreads) sparse_descent_kernel(DevInstance in
                 for (int w = 0; w < kWarps; ++w) d = fmaxf(d, s_dred[w][tid]);
                 int ls = s_lvl_sweeps[tid] + 1;
                 s_sweeps[tid] += 1;
-                const bool level_done = s.fixed_sweeps > 0 ? ls >= s.fixed_sweeps
-                                                           : (d <= s.d_min || ls >= s.k_max);
+                double T = s_T[tid];
+                const bool fixed = sched_fixed(s, T);
+                const bool level_done = fixed ? ls >= s.fixed_sweeps : (d <= s.d_min || ls >= s.k_max);
                 if (level_done) {
-                    if (s.fixed_sweeps == 0 && !(d <= s.d_min)) s_capped[tid] += 1;
-                    const double T = s_T[tid] - s.c_step;
-                    s_T[tid] = T;
+                    if (!fixed && !(d <= s.d_min)) s_capped[tid] += 1;
                     ls = 0;
-                    if (T > 0.0) {
+                    if (sched_advance(s, &T)) {
+                        s_T[tid] = T;
                         s_levels[tid] += 1;
-                        s_invT[tid] = (float)(1.0 / T);
+                        s_invT[tid] = sched_inv_t(T);
                     } else {
                         s_active[tid] = 0;
                     }

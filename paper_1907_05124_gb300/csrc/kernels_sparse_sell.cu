@@ -21,6 +21,7 @@
 // block barrier.
 #include "best_reduce.cuh"
 #include "device_common.cuh"
+#include "schedule.cuh"
 #include "mars_internal.h"
 
 #include <algorithm>
@@ -220,10 +221,10 @@ __device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, Slot
             }
             __syncthreads();
             if (tid < RT && fresh[tid]) {
-                const double T = (double)s.t0[s_rep[tid]] - s.c_step;
-                const bool act = T > 0.0;
+                double T;
+                const bool act = sched_first(s, (double)s.t0[s_rep[tid]], &T);
                 s_T[tid] = T;
-                s_invT[tid] = act ? (float)(1.0 / T) : 0.f;
+                s_invT[tid] = act ? sched_inv_t(T) : 0.f;
                 s_active[tid] = act;
                 s_done[tid] = !act;  // no level with T > 0: the result is sign(m0)
                 s_levels[tid] = act ? 1 : 0;
@@ -440,16 +441,16 @@ __device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, Slot
                     if (q == k) dd = dk[q];
                 int ls = s_lvl_sweeps[k] + 1;
                 s_sweeps[k] += 1;
-                const bool level_done = s.fixed_sweeps > 0 ? ls >= s.fixed_sweeps
-                                                           : (dd <= s.d_min || ls >= s.k_max);
+                double T = s_T[k];
+                const bool fixed = sched_fixed(s, T);
+                const bool level_done = fixed ? ls >= s.fixed_sweeps : (dd <= s.d_min || ls >= s.k_max);
                 if (level_done) {
-                    if (s.fixed_sweeps == 0 && !(dd <= s.d_min)) s_capped[k] += 1;
-                    const double T = s_T[k] - s.c_step;
-                    s_T[k] = T;
+                    if (!fixed && !(dd <= s.d_min)) s_capped[k] += 1;
                     ls = 0;
-                    if (T > 0.0) {
+                    if (sched_advance(s, &T)) {
+                        s_T[k] = T;
                         s_levels[k] += 1;
-                        s_invT[k] = (float)(1.0 / T);
+                        s_invT[k] = sched_inv_t(T);
                     } else {
                         s_active[k] = 0;
                         s_done[k] = 1;

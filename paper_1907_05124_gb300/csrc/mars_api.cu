@@ -28,6 +28,36 @@ using namespace mars;
 // descent ends and T - c_step always lowers T in double precision.
 static constexpr double kMaxLevels = 1e6;
 
+// Levels a replica with start temperature t0 visits under p's schedule (an
+// upper bound, counting a quench level).
+double levels_bound(const mars_params* p, double t0)
+{
+    double L;
+    if (p->schedule == MARS_SCHEDULE_GEOMETRIC)
+        L = t0 > p->t_floor ? std::log(p->t_floor / t0) / std::log(p->cool_ratio) + 1.0 : 0.0;
+    else
+        L = t0 / p->c_step;
+    return L + (p->quench ? 1.0 : 0.0);
+}
+
+// The labelled schedule variants' parameters; the paper's linear schedule
+// needs none.
+bool schedule_ok(const mars_params* p)
+{
+    if (p->schedule == MARS_SCHEDULE_LINEAR) return true;
+    return p->schedule == MARS_SCHEDULE_GEOMETRIC && p->cool_ratio > 0.0 && p->cool_ratio < 1.0 &&
+           p->t_floor > 0.0 && std::isfinite(p->t_floor);
+}
+
+template <class S>
+void set_schedule(S& s, const mars_params* p)
+{
+    s.geometric = p->schedule == MARS_SCHEDULE_GEOMETRIC ? 1 : 0;
+    s.cool_ratio = p->cool_ratio;
+    s.t_floor = p->t_floor;
+    s.quench = p->quench ? 1 : 0;
+}
+
 namespace {
 
 struct DevMem {
@@ -460,6 +490,10 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     t.d_min = s.d_min;
     t.k_max = s.k_max;
     t.fixed_sweeps = s.fixed_sweeps;
+    t.geometric = s.geometric;
+    t.quench = s.quench;
+    t.cool_ratio = s.cool_ratio;
+    t.t_floor = s.t_floor;
     t.rep = rep_dev;
     if ((rc = get((size_t)R * n_pad * sizeof(float), (void**)&t.S))) return rc;
     if (fp8 && !d.J8) return fail(c, MARS_EINVAL, "FP8 needs couplings exact in E4M3");
@@ -512,7 +546,11 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     run->g.active_prefix = t.counters;
     run->g.err = t.counters + 2;
     // Every replica ends within (levels + 1) x (sweeps per level) sweeps.
-    const double levels_max = std::ceil((double)t0_max / s.c_step) + 1.0;
+    double levels_max = std::ceil((double)t0_max / s.c_step) + 1.0;
+    if (s.geometric)
+        levels_max = t0_max > s.t_floor ? std::ceil(std::log(s.t_floor / t0_max) / std::log(s.cool_ratio)) + 1.0
+                                        : 1.0;
+    levels_max += s.quench ? 1.0 : 0.0;
     run->sweep_cap = (int64_t)(levels_max * (double)(s.fixed_sweeps > 0 ? s.fixed_sweeps : s.k_max)) + 1;
     run->batch = 1;
     run->done_sweeps = 0;
@@ -973,6 +1011,7 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
     s.d_min = (float)p.d_min;
     s.k_max = p.k_max;
     s.fixed_sweeps = p.fixed_sweeps;
+    set_schedule(s, &p);
     s.jacobi = p.update == MARS_UPDATE_JACOBI;
     s.m0 = p.m0;
     float* t0 = nullptr;
@@ -1697,8 +1736,9 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     if (!std::isfinite(p->t_min) || !std::isfinite(p->t_max) || p->t_min > p->t_max)
         return fail(c, MARS_EINVAL, "need finite t_min <= t_max");
     if (!(p->c_step > 0.0) || !std::isfinite(p->c_step)) return fail(c, MARS_EINVAL, "c_step must be > 0");
-    if (p->t_max / p->c_step > kMaxLevels)
-        return fail(c, MARS_EINVAL, "t_max / c_step exceeds %.0f temperature levels", kMaxLevels);
+    if (!schedule_ok(p)) return fail(c, MARS_EINVAL, "bad schedule (geometric: 0 < cool_ratio < 1, t_floor > 0)");
+    if (levels_bound(p, p->t_max) > kMaxLevels)
+        return fail(c, MARS_EINVAL, "t_max needs more than %.0f temperature levels", kMaxLevels);
     if (!(p->d_min >= 0.0)) return fail(c, MARS_EINVAL, "d_min must be >= 0");
     if (p->k_max < 1 || p->fixed_sweeps < 0) return fail(c, MARS_EINVAL, "k_max >= 1, fixed_sweeps >= 0");
     if (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI)
@@ -1725,6 +1765,7 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     s.d_min = (float)p->d_min;
     s.k_max = p->k_max;
     s.fixed_sweeps = p->fixed_sweeps;
+    set_schedule(s, p);
     s.jacobi = p->update == MARS_UPDATE_JACOBI;
     // start temperatures
     float* t0 = nullptr;
@@ -1744,7 +1785,7 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
         ++launches;
     }
     for (float v : t0h)
-        if (!std::isfinite(v) || v / p->c_step > kMaxLevels)
+        if (!std::isfinite(v) || levels_bound(p, v) > kMaxLevels)
             return fail(c, MARS_EINVAL, "start temperatures must be finite with t0 / c_step <= %.0f",
                         kMaxLevels);
     s.t0 = t0;
@@ -1913,7 +1954,8 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
         const int32_t R = p->replicas, n = in->dev.n;
         if (in->dev.dense) return fail(c, MARS_EINVAL, "job %d: batched launches take CSR instances", j);
         if (R < 1 || !std::isfinite(p->t_min) || !std::isfinite(p->t_max) || p->t_min > p->t_max ||
-            !(p->c_step > 0.0) || p->t_max / p->c_step > kMaxLevels || !(p->d_min >= 0.0) ||
+            !(p->c_step > 0.0) || !schedule_ok(p) || levels_bound(p, p->t_max) > kMaxLevels ||
+            !(p->d_min >= 0.0) ||
             p->k_max < 1 || p->fixed_sweeps < 0)
             return fail(c, MARS_EINVAL, "job %d: bad parameters", j);
         if (p->update != MARS_UPDATE_GS || p->precision != MARS_FP32)
@@ -1929,6 +1971,7 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
         s.d_min = (float)p->d_min;
         s.k_max = p->k_max;
         s.fixed_sweeps = p->fixed_sweeps;
+        set_schedule(s, p);
         const bool pdev = p->flags & MARS_DEVICE_PTR;
         float* t0 = nullptr;
         if ((rc = S.get(R, &t0))) return rc;
@@ -1975,7 +2018,7 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
         DevSolve& s = jobs[j].s;
         const int32_t R = p->replicas;
         for (float v : t0h)
-            if (!std::isfinite(v) || v / p->c_step > kMaxLevels)
+            if (!std::isfinite(v) || levels_bound(p, v) > kMaxLevels)
                 return fail(c, MARS_EINVAL, "job %d: start temperatures out of range", j);
         std::vector<int32_t> reps(R);
         std::iota(reps.begin(), reps.end(), 0);
@@ -2163,7 +2206,8 @@ int mars_submit(mars_ctx* c, int32_t id, const mars_params* p, int64_t* req)
     Instance* in = find(c, id);
     if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
     if (p->replicas < 1 || !std::isfinite(p->t_min) || !std::isfinite(p->t_max) || p->t_min > p->t_max ||
-        !(p->c_step > 0.0) || p->t_max / p->c_step > kMaxLevels || !(p->d_min >= 0.0) ||
+        !(p->c_step > 0.0) || !schedule_ok(p) || levels_bound(p, p->t_max) > kMaxLevels ||
+        !(p->d_min >= 0.0) ||
         p->k_max < 1 || p->fixed_sweeps < 0 ||
         (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI))
         return fail(c, MARS_EINVAL, "bad parameters");

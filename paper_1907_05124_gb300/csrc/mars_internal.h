@@ -90,6 +90,11 @@ struct DevSolve {
     float d_min = 1e-4f;
     int32_t k_max = 1000;
     int32_t fixed_sweeps = 0;
+    // labelled schedule variants (schedule.cuh); all zero is the paper's
+    int32_t geometric = 0;
+    int32_t quench = 0;
+    double cool_ratio = 0.5;
+    double t_floor = 0.0;
     int32_t jacobi = 0;
     const double* t_first = nullptr;   // optional per-replica temperature of the first level
     int32_t one_level = 0;             // stop after the first level (the FP32 polish)
@@ -218,6 +223,8 @@ struct TcState {
     double c_step = 1.0;
     float d_min = 1e-4f;
     int32_t k_max = 1000, fixed_sweeps = 0;
+    int32_t geometric = 0, quench = 0;
+    double cool_ratio = 0.5, t_floor = 0.0;
     double* T = nullptr;
     float* invT = nullptr;
     float* d = nullptr;

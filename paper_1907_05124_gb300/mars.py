@@ -42,7 +42,17 @@ class Params(ctypes.Structure):
                 ("fixed_sweeps", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_uint32), ("update", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("m0", ctypes.c_void_p),
-                ("t0", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+                ("t0", ctypes.c_void_p), ("flags", ctypes.c_uint32),
+                ("schedule", ctypes.c_int32), ("cool_ratio", ctypes.c_double),
+                ("t_floor", ctypes.c_double), ("quench", ctypes.c_int32)]
+
+
+def _schedule(p, geometric=None, t_floor=0.0, quench=False):
+    """Set the labelled schedule variants on Params p (defaults: the paper's)."""
+    p.schedule = 1 if geometric else 0
+    p.cool_ratio = float(geometric) if geometric else 0.5
+    p.t_floor = float(t_floor)
+    p.quench = 1 if quench else 0
 
 
 class Outputs(ctypes.Structure):
@@ -294,11 +304,14 @@ class Context:
     def solve(self, inst: int, replicas: int, t_min: float, t_max: float, *, c_step=1.0,
               d_min=1e-4, k_max=1000, fixed_sweeps=0, seed=0, stream=0, update="gs",
               precision="fp32", m0=None, t0=None, outputs=("energies",), device_outputs=False,
-              polish=False):
-        """Run mars_solve; `outputs` names the per-replica arrays to return."""
+              polish=False, geometric=None, t_floor=0.0, quench=False):
+        """Run mars_solve; `outputs` names the per-replica arrays to return.
+        geometric=r (with t_floor) and quench=True select the labelled
+        schedule variants (the paper's linear schedule by default)."""
         n = self._n[inst]
         p = Params()
         self._lib.mars_params_default(ctypes.byref(p))
+        _schedule(p, geometric, t_floor, quench)
         p.replicas, p.t_min, p.t_max, p.c_step, p.d_min = int(replicas), t_min, t_max, c_step, d_min
         p.k_max, p.fixed_sweeps, p.seed, p.stream = int(k_max), int(fixed_sweeps), int(seed), int(stream)
         p.update, p.precision = UPDATE[update], PRECISION[precision]
@@ -407,6 +420,7 @@ class Context:
             p.fixed_sweeps = int(kw.get("fixed_sweeps", 0))
             p.seed = int(kw.get("seed", 0))
             p.stream = int(kw.get("stream", 0))
+            _schedule(p, kw.get("geometric"), kw.get("t_floor", 0.0), kw.get("quench", False))
             pm, km, _ = _arr(kw.get("m0"), np.float32)
             pt, kt, _ = _arr(kw.get("t0"), np.float32)
             p.m0, p.t0 = pm, pt
@@ -434,10 +448,11 @@ class Context:
 
     def submit(self, inst: int, replicas: int, t_min: float, t_max: float, *, c_step=1.0,
                d_min=1e-4, k_max=1000, fixed_sweeps=0, seed=0, stream=0, update="gs",
-               precision="fp32") -> int:
+               precision="fp32", geometric=None, t_floor=0.0, quench=False) -> int:
         """mars_submit: queue a solve and return its request id."""
         p = Params()
         self._lib.mars_params_default(ctypes.byref(p))
+        _schedule(p, geometric, t_floor, quench)
         p.replicas, p.t_min, p.t_max, p.c_step, p.d_min = int(replicas), t_min, t_max, c_step, d_min
         p.k_max, p.fixed_sweeps, p.seed, p.stream = int(k_max), int(fixed_sweeps), int(seed), int(stream)
         p.update, p.precision = UPDATE[update], PRECISION[precision]

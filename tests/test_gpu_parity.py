@@ -520,3 +520,95 @@ def test_sell_launch_shapes_agree(ctx, monkeypatch, rt, threads):
     g2 = ctx.solve(inst, 40, 0.0, 6.0, seed=5, outputs=("energies", "spins"))
     assert np.array_equal(g2.energies, O.energies(O.Instance.csr(csr), g2.spins))
     ctx.free(inst)
+
+
+# --------------------------------------------------------------------------
+# labelled schedule variants: geometric cooling, the final quench level
+# --------------------------------------------------------------------------
+
+def test_geometric_schedule_trajectories(ctx):
+    """Geometric cooling T <- 0.7 T while T > 1 (every level at T >= 1, the
+    strict tier): one sweep per level, per-replica m within 1e-5 of the
+    oracle's, level and sweep counts exact."""
+    csr = I.er_graph(300, 6, 31, "pm1")
+    order = I.greedy_colour_order(csr)
+    inst = ctx.add_csr(*csr, order=order)
+    m0, t0 = I.replica_inputs(48, csr.n, 3.0, 4.0, 32)
+    g = ctx.solve(inst, 48, 3.0, 4.0, m0=m0, t0=t0, fixed_sweeps=1, geometric=0.7, t_floor=1.0,
+                  outputs=("m_final", "sweeps", "levels"))
+    o = O.mars_solve(O.Instance.csr(csr), m0, t0, fixed_sweeps=1, geometric=0.7, t_floor=1.0, order=order)
+    assert np.array_equal(g.replica_levels, o["levels"])
+    assert np.array_equal(g.replica_sweeps, o["sweeps"])
+    assert np.abs(g.m_final - o["m"]).max() <= 1e-5
+    ctx.free(inst)
+
+
+@pytest.mark.parametrize("kind", ["sparse", "dense"])
+def test_quench_fields_only_exact(ctx, kind):
+    """The quench level is the update's T -> 0+ limit: with fields only every
+    spin lands on -sgn(h) exactly (0 for a zero field) in one sweep, and the
+    level stops after the second."""
+    n = 512
+    h = np.concatenate([np.linspace(-3, 3, n - 6), [0.0, 1e-7, -1e-7, 1e-3, -2.5, 2.5]])
+    if kind == "sparse":
+        i = np.arange(n)
+        row_ptr = np.arange(0, 2 * n + 1, 2, dtype=np.int32)
+        col = np.sort(np.stack([(i - 1) % n, (i + 1) % n], axis=1), axis=1).astype(np.int32)
+        inst = ctx.add_csr(row_ptr, col.ravel(), np.zeros(2 * n), h=h)
+        J = None
+    else:
+        J = np.zeros((n, n))
+        inst = ctx.add_dense(J, h=h)
+    R = 6
+    m0 = np.random.default_rng(5).uniform(-1, 1, size=(R, n)).astype(np.float32)
+    t0 = np.array([0.5, 1.5, 2.5, 3.5, 0.9, 2.0], dtype=np.float32)
+    g = ctx.solve(inst, R, 0.5, 3.5, m0=m0, t0=t0, quench=True, outputs=("m_final", "sweeps", "levels"))
+    ref = -np.sign(h.astype(np.float32))
+    for r in range(R):
+        assert np.array_equal(g.m_final[r], ref), r
+    oi = O.Instance.dense(np.zeros((n, n)), h)
+    o = O.mars_solve(oi, m0, t0, quench=True)
+    assert np.array_equal(g.replica_levels, o["levels"])
+    assert np.array_equal(g.replica_sweeps, o["sweeps"])
+    ctx.free(inst)
+
+
+def _single_flip_minimum(inst, sig):
+    e = O.energy(inst, sig)
+    for i in range(sig.size):
+        f = sig.copy()
+        f[i] = -f[i]
+        if O.energy(inst, f) < e:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_quench_ends_in_local_minima(ctx, precision):
+    """After the quench level every returned state is a single-flip local
+    minimum of the exact energy (N = 96, +-1 couplings: a field of a +-1 state
+    sums 95 terms of +-1, an odd integer, never 0), on the FP32 path and on
+    the tensor-core path; energies exact, and the FP32 path agrees with the
+    oracle on nearly every replica."""
+    n, R = 96, 64
+    J = I.sk_pm1(n, 41)
+    inst = ctx.add_dense(J)
+    oi = O.Instance.dense(J)
+    m0, t0 = I.replica_inputs(R, n, 0.0, 16.0, 42)
+    g = ctx.solve(inst, R, 0.0, 16.0, m0=m0, t0=t0, quench=True, precision=precision,
+                  outputs=("energies", "spins"))
+    assert np.array_equal(g.energies, O.energies(oi, g.spins))
+    assert all(_single_flip_minimum(oi, g.spins[r]) for r in range(R))
+    if precision == "fp32":
+        o = O.mars_solve(oi, m0, t0, quench=True, nthreads=8, want_m=False)
+        assert np.mean(g.energies == o["energy"]) >= 0.8
+    ctx.free(inst)
+
+
+def test_schedule_variants_validated(ctx):
+    from paper_1907_05124_gb300.mars import MarsError
+    inst = ctx.add_csr(*I.ea_lattice(6, 2, 0))
+    for kw in ({"geometric": 1.5, "t_floor": 0.5}, {"geometric": 0.5, "t_floor": 0.0}):
+        with pytest.raises(MarsError):
+            ctx.solve(inst, 4, 0.0, 4.0, **kw)
+    ctx.free(inst)
