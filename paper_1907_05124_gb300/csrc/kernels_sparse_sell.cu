@@ -144,10 +144,12 @@ struct SlotState {
 };
 
 // Run one instance's replica queue on this CTA until the queue is empty and
-// every slot has drained. Called by the whole CTA (it contains barriers).
-template <int RT, int NT, int FMT, int DEG = 0>
-__device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, SlotState<RT, NT / 32>& S)
+// every slot has drained. Called by the whole CTA (it contains barriers). The
+// slot bookkeeping S may be sized for more slots (RTS) than the job uses.
+template <int RT, int NT, int FMT, int DEG = 0, int RTS = RT>
+__device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, SlotState<RTS, NT / 32>& S)
 {
+    static_assert(RT <= RTS, "the slot bookkeeping holds the job's slots");
     constexpr int kThreads = NT;
     constexpr int kWarps = NT / 32;
     using V = Vec<RT>;
@@ -475,12 +477,34 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_kernel(DevInstance 
 // in order, each draining one instance's replica queue before it moves on, so
 // instances of uneven size and replica count share the SMs without a launch
 // per instance. The coupling format is chosen per job.
-template <int RT, int NT>
+// One job of a batched launch with its own slot width (1 or 2, job.rt) and
+// coupling format under the CTA's two-slot bookkeeping.
+template <int NT>
+__device__ void run_batch_job(const BatchJob& job, float* m, SlotState<2, NT / 32>& S)
+{
+    switch (job.rt * 4 + job.fmt) {
+    case 4 + 3: run_job<1, NT, 3, 0, 2>(job.in, job.s, m, S); break;
+    case 4 + 2: run_job<1, NT, 2, 0, 2>(job.in, job.s, m, S); break;
+    case 4 + 1: run_job<1, NT, 1, 0, 2>(job.in, job.s, m, S); break;
+    case 4 + 0: run_job<1, NT, 0, 0, 2>(job.in, job.s, m, S); break;
+    case 8 + 3: run_job<2, NT, 3, 0, 2>(job.in, job.s, m, S); break;
+    case 8 + 2: run_job<2, NT, 2, 0, 2>(job.in, job.s, m, S); break;
+    case 8 + 1: run_job<2, NT, 1, 0, 2>(job.in, job.s, m, S); break;
+    default: run_job<2, NT, 0, 0, 2>(job.in, job.s, m, S); break;
+    }
+}
+
+// Several instances in one persistent launch: CTAs work through the job list
+// in order, each job's replica queue drained by every CTA before it moves on
+// (a job is a CTA's current work until its queue is empty). Shared memory is
+// sized for the most demanding job; slot width and coupling format are chosen
+// per job.
+template <int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_batch_kernel(const BatchJob* jobs, int njobs,
                                                                        int* cursor)
 {
     extern __shared__ __align__(16) float m[];
-    __shared__ SlotState<RT, NT / 32> S;
+    __shared__ SlotState<2, NT / 32> S;
     __shared__ BatchJob s_jobcopy;  // the current job's descriptors, read from shared memory
     __shared__ int s_job;
     for (;;) {
@@ -502,13 +526,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_batch_kernel(const 
                 dst[w] = src[w];
         }
         __syncthreads();
-        const BatchJob& job = s_jobcopy;
-        switch (job.fmt) {
-        case 3: run_job<RT, NT, 3>(job.in, job.s, m, S); break;
-        case 2: run_job<RT, NT, 2>(job.in, job.s, m, S); break;
-        case 1: run_job<RT, NT, 1>(job.in, job.s, m, S); break;
-        default: run_job<RT, NT, 0>(job.in, job.s, m, S); break;
-        }
+        run_batch_job<NT>(s_jobcopy, m, S);
         __syncthreads();
     }
 }
@@ -518,11 +536,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) sparse_sell_batch_kernel(const 
 // (about 2 us apart, at most idle_polls times) and the CTA exits when nothing
 // new arrives. Descriptors written by the host's copies are read through
 // volatile loads (past L1), after the tail that published them.
-template <int RT, int NT>
+template <int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) serve_ring_kernel(ServeRing* ring, int idle_polls)
 {
     extern __shared__ __align__(16) float m[];
-    __shared__ SlotState<RT, NT / 32> S;
+    __shared__ SlotState<2, NT / 32> S;
     __shared__ BatchJob s_jobcopy;
     __shared__ int s_job;
     for (;;) {
@@ -559,13 +577,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) serve_ring_kernel(ServeRing* ri
                 dst[w] = src[w];
         }
         __syncthreads();
-        const BatchJob& job = s_jobcopy;
-        switch (job.fmt) {
-        case 3: run_job<RT, NT, 3>(job.in, job.s, m, S); break;
-        case 2: run_job<RT, NT, 2>(job.in, job.s, m, S); break;
-        case 1: run_job<RT, NT, 1>(job.in, job.s, m, S); break;
-        default: run_job<RT, NT, 0>(job.in, job.s, m, S); break;
-        }
+        run_batch_job<NT>(s_jobcopy, m, S);
         __syncthreads();
     }
 }
@@ -685,50 +697,44 @@ cudaError_t launch_sparse_sell(const DevInstance& in, const DevSolve& s, const S
 }
 
 namespace {
-template <int RT>
 const void* pick_batch(int nt)
 {
-    return nt == 1024 ? (const void*)sparse_sell_batch_kernel<RT, 1024>
-                      : (const void*)sparse_sell_batch_kernel<RT, 512>;
+    return nt == 1024 ? (const void*)sparse_sell_batch_kernel<1024> : (const void*)sparse_sell_batch_kernel<512>;
 }
 }  // namespace
 
-// Shared launch shape of a batch: one slot width for every job (the widest
-// that fits the largest instance), per-job coupling format, and the shared
-// memory of the most demanding job.
-bool plan_sparse_batch(const DevInstance* ins, int count, int device, BatchPlan* p, int* fmts)
+// Launch shape of a batch: per job the widest slot width (2, else 1) whose
+// magnetisations fit on chip and its coupling format; shared memory of the
+// most demanding job.
+bool plan_sparse_batch(const DevInstance* ins, int count, int device, BatchPlan* p, int* fmts, int* rts)
 {
     int sms = 1, optin = 48 * 1024;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     const size_t budget = (size_t)optin - 16 * 1024;
-    int nmax = 0;
-    for (int j = 0; j < count; ++j) {
-        if (ins[j].dense || !ins[j].slices || (!ins[j].sell_pm1 && !ins[j].sell_gen)) return false;
-        nmax = std::max(nmax, ins[j].n);
-    }
-    int rt = env_int("MARS_SELL_RT", 2);
+    const int rt_max = env_int("MARS_SELL_RT", 2) >= 2 ? 2 : 1;
     int nt = env_int("MARS_SELL_THREADS", 1024);
-    if (rt != 1 && rt != 2) rt = 1;
     if (nt != 512 && nt != 1024) nt = 1024;
     auto m_bytes = [&](int n, int c) { return align16((size_t)(n + 1) * c * sizeof(float)); };
-    while (rt > 1 && m_bytes(nmax, rt) > budget) rt /= 2;
-    if (m_bytes(nmax, rt) > budget) return false;
     size_t smem = 0;
     for (int j = 0; j < count; ++j) {
         const DevInstance& in = ins[j];
+        if (in.dense || !in.slices || (!in.sell_pm1 && !in.sell_gen)) return false;
+        int rt = rt_max;
+        while (rt > 1 && m_bytes(in.n, rt) > budget) rt /= 2;
+        if (m_bytes(in.n, rt) > budget) return false;
         const size_t table = (size_t)in.nslices * 16 + (size_t)in.sell_len * 2;
         int fmt = in.sell_pm1 ? 1 : 0;
         if (in.sell16) fmt = 3;
         if (in.sell16 && env_int("MARS_SELL_SMEM_TABLE", 1) && m_bytes(in.n, rt) + table <= budget) fmt = 2;
         fmts[j] = fmt;
+        rts[j] = rt;
         smem = std::max(smem, m_bytes(in.n, rt) + (fmt == 2 ? table : 0));
     }
-    p->rt = rt;
+    p->rt = 2;
     p->threads = nt;
     p->smem = smem;
-    const void* k = pick_batch<1>(nt);
-    if (rt == 2) k = pick_batch<2>(nt);
+    const void* k = pick_batch(nt);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem);
@@ -739,7 +745,7 @@ bool plan_sparse_batch(const DevInstance* ins, int count, int device, BatchPlan*
 cudaError_t launch_sparse_batch(const BatchJob* jobs, int count, int* cursor, const BatchPlan& p,
                                 cudaStream_t st)
 {
-    const void* k = p.rt == 2 ? pick_batch<2>(p.threads) : pick_batch<1>(p.threads);
+    const void* k = pick_batch(p.threads);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&jobs, (void*)&count, (void*)&cursor};
@@ -754,7 +760,7 @@ bool plan_serve_ring(int device, RingPlan* p)
     p->rt = 2;
     p->threads = 1024;
     p->smem = (size_t)optin - 16 * 1024;  // static shared memory and slack
-    const void* k = (const void*)serve_ring_kernel<2, 1024>;
+    const void* k = (const void*)serve_ring_kernel<1024>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess)
         return false;
     int per_sm = 1;
@@ -763,10 +769,12 @@ bool plan_serve_ring(int device, RingPlan* p)
     return true;
 }
 
-int ring_job_format(const DevInstance& in, const RingPlan& p)
+int ring_job_format(const DevInstance& in, const RingPlan& p, int* rt)
 {
     if (in.dense || !in.slices || (!in.sell_pm1 && !in.sell_gen)) return -1;
-    const size_t mb = align16((size_t)(in.n + 1) * p.rt * sizeof(float));
+    auto m_bytes = [&](int c) { return align16((size_t)(in.n + 1) * c * sizeof(float)); };
+    *rt = m_bytes(2) <= p.smem ? 2 : 1;
+    const size_t mb = m_bytes(*rt);
     if (mb > p.smem) return -1;
     const size_t table = (size_t)in.nslices * 16 + (size_t)in.sell_len * 2;
     if (in.sell16 && mb + table <= p.smem) return 2;
@@ -776,8 +784,8 @@ int ring_job_format(const DevInstance& in, const RingPlan& p)
 
 cudaError_t launch_serve_ring(ServeRing* ring, const RingPlan& p, int idle_polls, cudaStream_t st)
 {
-    if (p.rt != 2 || p.threads != 1024) return cudaErrorInvalidValue;
-    const void* k = (const void*)serve_ring_kernel<2, 1024>;
+    if (p.threads != 1024) return cudaErrorInvalidValue;
+    const void* k = (const void*)serve_ring_kernel<1024>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&ring, (void*)&idle_polls};

@@ -1045,11 +1045,13 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
         // the serving ring: one persistent kernel for every sparse request
         // (integer couplings: the kernel's fused int64 energies are final, so
         // the job needs no kernel after the serving kernel)
-        const int fmt =
-            !s.jacobi && q->dev.integer && serve_ring_init(c, sv) ? ring_job_format(q->dev, sv->plan) : -1;
+        int job_rt = 1;
+        const int fmt = !s.jacobi && q->dev.integer && serve_ring_init(c, sv)
+                            ? ring_job_format(q->dev, sv->plan, &job_rt)
+                            : -1;
         const int k = (int)sv->tail;
         if (fmt >= 0 && sv->tail < kRingCap) {
-            const int32_t rr = sv->plan.rt;
+            const int32_t rr = job_rt;
             const int32_t ntiles = (R + rr - 1) / rr;
             int32_t* queue = nullptr;
             if ((rc = get((size_t)ntiles * rr * sizeof(int32_t), (void**)&queue))) return rc;
@@ -1069,6 +1071,7 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
             job.in = q->dev;
             job.s = s;
             job.fmt = fmt;
+            job.rt = job_rt;
             sv->stage_jobs[k] = job;
             sv->stage_slots[k] = RingSlot{};
             sv->stage_tail[k] = (int32_t)(sv->tail + 1);
@@ -2031,10 +2034,13 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
         s.rt = 1;
     }
     BatchPlan bp;
-    std::vector<int> fmts(count);
-    if (!plan_sparse_batch(dins.data(), count, c->device, &bp, fmts.data()))
+    std::vector<int> fmts(count), rts(count);
+    if (!plan_sparse_batch(dins.data(), count, c->device, &bp, fmts.data(), rts.data()))
         return fail(c, MARS_EINVAL, "an instance is too large for the batched on-chip kernel");
-    for (int32_t j = 0; j < count; ++j) jobs[j].fmt = fmts[j];
+    for (int32_t j = 0; j < count; ++j) {
+        jobs[j].fmt = fmts[j];
+        jobs[j].rt = rts[j];
+    }
     BatchJob* djobs = nullptr;
     int32_t* cursor = nullptr;
     if ((rc = S.get(count, &djobs))) return rc;

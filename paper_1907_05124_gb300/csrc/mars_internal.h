@@ -124,7 +124,7 @@ struct BatchJob {
     DevInstance in;
     DevSolve s;
     int32_t fmt = 0;
-    int32_t pad = 0;
+    int32_t rt = 1;  // replica slots per CTA for this job (1 or 2)
 };
 // The serving ring: job descriptors the host publishes while the persistent
 // serving kernel runs. A job's counters live in the ring (never in request
@@ -155,9 +155,10 @@ struct RingPlan {
     int grid = 1;
 };
 bool plan_serve_ring(int device, RingPlan* p);
-// Coupling format a job uses under the ring's shared memory, or -1 when the
+// Coupling format a job uses under the ring's shared memory (and its slot
+// width, 2 when two replicas' magnetisations fit, else 1), or -1 when the
 // job's magnetisations do not fit on chip.
-int ring_job_format(const DevInstance& in, const RingPlan& p);
+int ring_job_format(const DevInstance& in, const RingPlan& p, int* rt);
 // Persistent serving kernel: runs published jobs and exits after about
 // idle_polls x 2 us without new work (or when ring->stop is set).
 cudaError_t launch_serve_ring(ServeRing* ring, const RingPlan& p, int idle_polls, cudaStream_t st);
@@ -168,7 +169,7 @@ struct BatchPlan {
     size_t smem = 0;
     int grid = 0;
 };
-bool plan_sparse_batch(const DevInstance* ins, int count, int device, BatchPlan* p, int* fmts);
+bool plan_sparse_batch(const DevInstance* ins, int count, int device, BatchPlan* p, int* fmts, int* rts);
 cudaError_t launch_sparse_batch(const BatchJob* jobs, int count, int* cursor, const BatchPlan& p,
                                 cudaStream_t st);
 

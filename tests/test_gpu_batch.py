@@ -92,3 +92,31 @@ def test_batch_rejects_dense_and_bad_jobs(ctx):
         ctx.solve_batch([(s, 0, 0.0, 4.0, {})])
     ctx.free(d)
     ctx.free(s)
+
+
+def test_batch_mixes_slot_widths(ctx):
+    """A 3-D L=32 lattice (N = 32768: one replica slot per CTA fits on chip)
+    shares the launch with small graphs that run two slots per CTA; every job
+    returns exactly what a separate mars_solve returns."""
+    graphs = [I.ea_lattice(32, 3, 21), I.er_graph(900, 6, 22, "pm1"), I.ea_lattice(24, 2, 23)]
+    insts = [ctx.add_csr(*g) for g in graphs]
+    Rs, tmax = [48, 200, 130], [6.0, 6.0, 4.0]
+    jobs = [(i, R, 0.0, tm, {"seed": 60 + j}) for j, (i, R, tm) in enumerate(zip(insts, Rs, tmax))]
+    out = ctx.solve_batch(jobs)
+    for (inst, R, lo, hi, kw), b in zip(jobs, out):
+        _same(b, ctx.solve(inst, R, lo, hi, seed=kw["seed"], outputs=("energies",)))
+    for inst in insts:
+        ctx.free(inst)
+
+
+def test_batch_with_schedule_variants(ctx):
+    """Geometric cooling and the quench level travel with each job."""
+    g1, g2 = I.er_graph(600, 6, 27, "pm1"), I.ea_lattice(16, 2, 28)
+    i1, i2 = ctx.add_csr(*g1), ctx.add_csr(*g2)
+    kw1 = {"seed": 3, "geometric": 0.8, "t_floor": 0.3, "quench": True}
+    kw2 = {"seed": 4, "quench": True}
+    out = ctx.solve_batch([(i1, 80, 0.0, 6.0, kw1), (i2, 60, 0.0, 4.0, kw2)])
+    _same(out[0], ctx.solve(i1, 80, 0.0, 6.0, seed=3, geometric=0.8, t_floor=0.3, quench=True))
+    _same(out[1], ctx.solve(i2, 60, 0.0, 4.0, seed=4, quench=True))
+    ctx.free(i1)
+    ctx.free(i2)

@@ -139,3 +139,27 @@ def test_ring_kernel_relaunches_after_idle_exit(ctx):
             _same(out[r], ctx.solve(inst, 64, 0.0, 4.0, seed=wave * 10 + k))
         time.sleep(0.05)
     ctx.free(inst)
+
+
+def test_ring_takes_large_instances_with_one_slot(ctx):
+    """An instance whose two replicas' magnetisations do not fit on chip runs
+    in the serving ring with one slot per CTA, beside two-slot jobs."""
+    big = ctx.add_csr(*I.ea_lattice(32, 3, 25))
+    small = ctx.add_csr(*I.ea_lattice(20, 2, 26))
+    ring0, _ = ctx.serve_counters()
+    reqs = {ctx.submit(big, 40, 0.0, 6.0, seed=1): (big, 40, 6.0, 1),
+            ctx.submit(small, 100, 0.0, 4.0, seed=2): (small, 100, 4.0, 2)}
+    out = _wait(ctx, list(reqs))
+    assert ctx.serve_counters()[0] - ring0 == 2
+    for r, (inst, R, tmax, sd) in reqs.items():
+        _same(out[r], ctx.solve(inst, R, 0.0, tmax, seed=sd))
+    ctx.free(big)
+    ctx.free(small)
+
+
+def test_served_quench_matches_blocking(ctx):
+    inst = ctx.add_csr(*I.er_graph(800, 8, 29, "pm1"))
+    r = ctx.submit(inst, 64, 0.0, 5.0, seed=9, quench=True, geometric=0.75, t_floor=0.5)
+    out = _wait(ctx, [r])
+    _same(out[r], ctx.solve(inst, 64, 0.0, 5.0, seed=9, quench=True, geometric=0.75, t_floor=0.5))
+    ctx.free(inst)
