@@ -945,7 +945,7 @@ size_t serve_footprint(const DevInstance& d, const mars_params& p, int sms)
     size_t b = R * n + R * (4 + 8 + 8 + 12 + 4 + 4) + 4096 + n;
     if (d.dense && (p.precision == MARS_BF16 || p.precision == MARS_FP8)) {
         const size_t np = (size_t)d.n_pad, Rp = (R + 127) / 128 * 128;
-        b += R * np * 4 + Rp * np * 2 + 8 * Rp * 128 * 4 + R * 32;
+        b += R * np * 4 + Rp * np * 2 + 2 * kChainMaxSplit * Rp * 128 * 4 + 2 * Rp * 128 * 4 + R * 32;
     } else if (!d.dense) {
         b += (size_t)sms * n * 8 * sizeof(float);  // a possible streaming slab
     }
