@@ -364,6 +364,7 @@ __device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, Slot
             live |= act[k] ? 1 << k : 0;
         }
         const bool all_live = RT == 1 || __popc(live) > 1;
+        const bool lean = live == (1 << RT) - 1 && !in.h;  // uniform over the CTA
         for (int l = 0; l < in.nlev; ++l) {
             const int s0 = __ldg(in.lvl_slice + l), s1 = __ldg(in.lvl_slice + l + 1);
             for (int sl = s0 + warp; sl < s1; sl += kWarps) {
@@ -388,14 +389,24 @@ __device__ void run_job(const DevInstance& in, const DevSolve& s, float* m, Slot
                     }
                     const typename V::T old = V::load(m + i * RT);
                     typename V::T nv;
+                    if (lean) {
+                        // every slot live, no field: no per-slot test, no add
 #pragma unroll
-                    for (int k = 0; k < RT; ++k) {
-                        if ((live >> k) & 1) {
-                            const float sn = -tanh_sfu((V::get(acc, k) + hv) * invT[k]);
+                        for (int k = 0; k < RT; ++k) {
+                            const float sn = -tanh_sfu(V::get(acc, k) * invT[k]);
                             dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(old, k)));
                             V::set(nv, k, sn);
-                        } else {
-                            V::set(nv, k, V::get(old, k));
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < RT; ++k) {
+                            if ((live >> k) & 1) {
+                                const float sn = -tanh_sfu((V::get(acc, k) + hv) * invT[k]);
+                                dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(old, k)));
+                                V::set(nv, k, sn);
+                            } else {
+                                V::set(nv, k, V::get(old, k));
+                            }
                         }
                     }
                     V::store(m + i * RT, nv);
