@@ -717,7 +717,7 @@ def run_ttt(args, world, rank, local):
     runs = {}
     for prec in ("fp32", "bf16", "fp8"):
         kw = dict(c_step=1.0, d_min=D_MIN, k_max=K_MAX, seed=1, precision=prec, outputs=("energies",))
-        ctx.solve(inst, R, 0.0, tmax, **dict(kw, seed=2))  # warm-up
+        ctx.solve(inst, R, 0.0, tmax, **dict(kw, seed=2, fixed_sweeps=1))  # warm-up (short)
         torch.cuda.synchronize()
         t = time.perf_counter()
         res = ctx.solve(inst, R, 0.0, tmax, **kw)

@@ -264,6 +264,7 @@ cudaError_t launch_tc_export(const TcState& t, const DevInstance& in, float* m_o
 
 struct DensePlan {
     int warps_per_block = 4;
+    int stages = 0;  // > 0: the staged kernel with this many row buffers
     int onchip = 1;
     size_t smem = 0;
     int grid = 0;
