@@ -413,7 +413,7 @@ def run_mars(args, world, rank, local):
         # default shape (2 slots, 1024 threads, table in shared memory); null
         # for another shape, whose counters were not taken.
         default_shape = rt_used == 2 and nt_used == 1024 and tab_used
-        traffic = 1.200128e6 + 4.864e3 if default_shape else None
+        traffic = 1.0368e6 + 8.448e3 if default_shape else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
                     "unit": "spin-updates/s (SFU-bound)", "frac": achieved / peak, "traffic": traffic,
                     "kernel": "sparse_sell_kernel<RT={}, {} threads, halfword couplings{}, degree 4>".format(
