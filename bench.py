@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=3.0,
                     help="serve: mean arrivals per second (about 80 %% of the mix's capacity)")
+    ap.add_argument("--inflight", type=int, default=8,
+                    help="serve: requests admitted at once (mars_serve_limits)")
     ap.add_argument("--replicas", type=int, default=0, help="override R (profiling runs)")
     ap.add_argument("--fixed-sweeps", type=int, default=0,
                     help="profiling runs only: exactly this many sweeps per level")
@@ -496,8 +498,9 @@ def run_serve(args, world, rank, local):
     kinds = rng.integers(0, len(pool), size=n_req)
     reps = rng.choice(np.array([64, 128, 256, 512, 1024]), size=n_req)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n_req))
-    ctx.serve_limits(8)
+    ctx.serve_limits(args.inflight)
     pending, lat, upd = {}, [], 0
+    by_kind = {}  # request kind -> latencies (s)
     t_start = time.perf_counter()
     nxt = 0
     while nxt < n_req or pending:
@@ -506,12 +509,14 @@ def run_serve(args, world, rank, local):
             name, inst, nn, tmax, cstep, prec = pool[kinds[nxt]]
             req = ctx.submit(inst, int(reps[nxt]), 0.0, tmax, c_step=cstep, seed=nxt,
                              precision=prec)
-            pending[req] = arrivals[nxt]
+            pending[req] = (arrivals[nxt], name)
             nxt += 1
         for req in list(pending):
             r = ctx.poll(req)
             if r is not None:
-                lat.append(time.perf_counter() - t_start - pending.pop(req))
+                t_arr, name = pending.pop(req)
+                lat.append(time.perf_counter() - t_start - t_arr)
+                by_kind.setdefault(name, []).append(lat[-1])
                 upd += r.spin_updates
         time.sleep(0.0002)
     wall = time.perf_counter() - t_start
@@ -523,12 +528,15 @@ def run_serve(args, world, rank, local):
         "data": "synthetic (seeded instances, Poisson arrivals)",
         "config": {"workload": f"serving: {n_req} Poisson arrivals at {args.rate}/s, mixed dense SK "
                                "(N 256-1024, +-1 / Gaussian) and sparse lattices / ER graphs "
-                               "(N 1k-100k), R 64-1024, 8 in flight, 120 GB budget",
-                   "requests": n_req, "rate_per_s": args.rate},
+                               f"(N 1k-100k), R 64-1024, {args.inflight} in flight, 120 GB budget",
+                   "requests": n_req, "rate_per_s": args.rate, "inflight": args.inflight},
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                        "p99": float(np.percentile(lat_ms, 99)),
                        "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
         "served_by": dict(zip(("persistent_ring_kernel", "own_stream"), ctx.serve_counters())),
+        "latency_ms_by_kind": {k: {"count": len(v), "p50": float(np.percentile(1e3 * np.array(v), 50)),
+                                   "p99": float(np.percentile(1e3 * np.array(v), 99))}
+                               for k, v in sorted(by_kind.items())},
     }
     print(json.dumps(line), flush=True)
     ctx.close()
