@@ -51,6 +51,21 @@ SK_WORKLOAD = {
     "d_min": D_MIN, "k_max": K_MAX, "precision": "bf16",
 }
 
+# A sparse instance too large for shared memory: the 3-D lattice L=100, whose
+# replicas' magnetisations stream through per-CTA slabs of HBM.
+EA3_L, EA3_R, EA3_TMAX = 100, 608, 6.0
+EA3_WORKLOAD = {
+    "workload": "3-D EA +-J spin glass, periodic 100^3 (N=1,000,000), R=608 replicas, "
+                "T0~U(0,6), C_step=1, d_min=1e-4, k_max=1000, FP32 sequential sweeps in colour "
+                "order, magnetisations in per-CTA slabs of global memory",
+    "n_spins": EA3_L ** 3, "replicas": EA3_R, "t_range": [0.0, EA3_TMAX], "c_step": 1.0,
+    "d_min": D_MIN, "k_max": K_MAX,
+}
+# Algorithmic DRAM bytes per spin-update of a two-colour sweep whose slabs are
+# far larger than L2: every magnetisation is read twice per sweep (as the
+# other colour's neighbour and as its own old value) and written once.
+EA3_BYTES_PER_UPDATE = 12.0
+
 # The FP8 variant: dense SK with +-1 couplings (exact in E4M3) on E4M3 tensor
 # cores; the same schedule in units of the couplings' scale sqrt(N).
 SK8_TMAX = 2.0 * SK_N ** 0.5
@@ -75,8 +90,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip mars_autotune before the warm-up (library default launch shape)")
     ap.add_argument("--workload", default="ea2d",
-                    choices=["ea2d", "sk8192", "sk8192pm1", "serve", "ttt", "batch", "sensitivity"],
-                    help="ea2d: the 2-D lattice (default); sk8192: dense SK on tensor cores; "
+                    choices=["ea2d", "ea3d_big", "sk8192", "sk8192pm1", "serve", "ttt", "batch",
+                             "sensitivity"],
+                    help="ea2d: the 2-D lattice (default); ea3d_big: the 3-D lattice with N=10^6 "
+                         "(magnetisations in HBM); sk8192: dense SK on tensor cores; "
                          "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=3.0,
@@ -174,6 +191,19 @@ def cpu_baseline(target_s: float, wl=None):
         upd = int(out["sweeps"].sum()) * SK_N
         return {"value": upd / dt, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
                 "sample": f"{cores} replicas of the N=8192 workload, one sweep per level, "
+                          f"FP64 oracle, OpenMP over replicas, {dt:.1f} s"}
+    if wl is not None and wl.name == "ea3d_big":
+        # One replica per core of the N=10^6 lattice, one sweep per level.
+        inst = O.Instance.csr(wl.csr)
+        order = I.greedy_colour_order(wl.csr)
+        m0, t0 = O.draw_replicas(0, cores, wl.csr.n, T_MIN, wl.t_max)
+        t = time.perf_counter()
+        out = O.mars_solve(inst, m0, t0, c_step=wl.c_step, d_min=D_MIN, k_max=K_MAX, order=order,
+                           fixed_sweeps=1, nthreads=cores, want_m=False)
+        dt = time.perf_counter() - t
+        upd = int(out["sweeps"].sum()) * wl.csr.n
+        return {"value": upd / dt, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+                "sample": f"{cores} replicas of the N=10^6 lattice workload, one sweep per level, "
                           f"FP64 oracle, OpenMP over replicas, {dt:.1f} s"}
     csr = I.ea_lattice(L, 2, 0)
     inst = O.Instance.csr(csr)
@@ -276,6 +306,13 @@ class Workload:
             self.t_max, self.c_step, self.precision = T_MAX, C_STEP, "fp32"
             self.config = dict(WORKLOAD, replicas=self.R)
             self.dtype = "f32"
+        elif self.name == "ea3d_big":
+            self.csr = instances.ea_lattice(EA3_L, 3, 0)
+            self.J = None
+            self.R = args.replicas or EA3_R
+            self.t_max, self.c_step, self.precision = EA3_TMAX, 1.0, "fp32"
+            self.config = dict(EA3_WORKLOAD, replicas=self.R)
+            self.dtype = "f32"
         elif self.name == "sk8192":
             self.csr = None
             self.J = instances.sk_gauss(SK_N, 0)
@@ -302,9 +339,12 @@ class Workload:
         """mars_autotune on this workload's replicas: the full solve for the
         lattice (milliseconds), a two-level fixed-sweep schedule for the dense
         instance (its full solve takes minutes). Untimed, before the warm-up."""
-        if self.csr is not None:
+        if self.name == "ea2d":
             return ctx.autotune(inst, self.R, T_MIN, self.t_max, repeats=2, c_step=self.c_step,
                                 d_min=D_MIN, k_max=K_MAX, seed=7, stream=self.rank)
+        if self.csr is not None:  # seconds per solve: two levels of two sweeps each
+            return ctx.autotune(inst, self.R, 0.0, 2.0 * self.c_step, repeats=1, c_step=self.c_step,
+                                fixed_sweeps=2, seed=7, stream=self.rank)
         return ctx.autotune(inst, self.R, 0.0, 2.0 * self.c_step, repeats=1, c_step=self.c_step,
                             fixed_sweeps=4, seed=7, stream=self.rank, precision=self.precision)
 
@@ -421,6 +461,16 @@ def run_mars(args, world, rank, local):
                     "kernel": "sparse_sell_kernel<RT={}, {} threads, halfword couplings{}, degree 4>".format(
                         rt_used, nt_used, " in shared memory" if tab_used else " through L1"),
                     "peak_source": "152 SMs x (1/32 + 1/16 SFU clocks per tanh)^-1 x SM clock",
+                    "descent_ms_mean": 1e3 * d_mean}
+    elif wl.name == "ea3d_big":
+        achieved = EA3_BYTES_PER_UPDATE * upd_per_launch / d_mean / 1e9
+        sh = shape or {}
+        rt_used = sh.get("sell_rt", -1) if sh.get("sell_rt", -1) > 0 else 2
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "kernel": f"sparse_slab_kernel<RT={rt_used}, +-1 words, degree 6>",
+                    "bytes_per_update": EA3_BYTES_PER_UPDATE,
+                    "peak_source": f"hbm copy ({peaks['source']})",
                     "descent_ms_mean": 1e3 * d_mean}
     else:
         achieved = gemm_flops / gemm_s / 1e12 if gemm_s > 0 else 0.0

@@ -178,7 +178,7 @@ cudaError_t launch_sparse_batch(const BatchJob* jobs, int count, int* cursor, co
 // Launchers (return cudaError_t of the launch).
 struct SparsePlan {
     int rt = 1;         // replicas per tile
-    int onchip = 1;     // magnetisations in shared memory
+    int onchip = 1;     // magnetisations in shared memory (sliced-ELL: else per-CTA slabs)
     int threads = 512;
     size_t smem = 0;    // dynamic shared memory
     int grid = 0;
@@ -188,6 +188,9 @@ struct SparsePlan {
     int deg = 0;        // compile-time degree of a regular instance (4 or 6), else 0
 };
 bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p);
+// The sliced-ELL kernel with m in global-memory slabs (format 0 or 1, rt 1, 2
+// or 4); null for another combination.
+const void* pick_sell_slab(int rt, int fmt, int deg);
 cudaError_t launch_sparse_sell(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
                                cudaStream_t st);
 SparsePlan plan_sparse(const DevInstance& in, int R, int jacobi, int device);
