@@ -946,7 +946,9 @@ size_t serve_footprint(const DevInstance& d, const mars_params& p, int sms)
     if (d.dense && (p.precision == MARS_BF16 || p.precision == MARS_FP8)) {
         const size_t np = (size_t)d.n_pad, Rp = (R + 127) / 128 * 128;
         b += R * np * 4 + Rp * np * 2 + 2 * kChainMaxSplit * Rp * 128 * 4 + 2 * Rp * 128 * 4 + R * 32;
-    } else if (!d.dense) {
+    } else if (d.dense) {
+        b += R * n * sizeof(float);  // the FP32 path's rows of m, when they do not fit on chip
+    } else {
         b += (size_t)sms * n * 8 * sizeof(float);  // a possible streaming slab
     }
     return b;
