@@ -217,6 +217,70 @@ def test_fields_only_closed_form():
         assert r["capped_levels"][k] == 0
 
 
+@pytest.mark.parametrize("k_max", [1, 2, 3, 7])
+def test_k_max_cap_counts_on_fields_only_levels(k_max):
+    """The cap on sweeps per level, against the fields-only closed form.
+
+    With J = 0 a level's first sweep lands on -tanh(h/T) and its second moves
+    nothing (d = 0). So k_max = 1 ends every level after one sweep with d > d_min
+    (every level capped), while k_max >= 2 ends it on the second sweep with
+    d = 0: a level that converges on exactly its k_max-th sweep is not capped."""
+    n = 8
+    h = np.linspace(0.5, 2.0, n)
+    inst = O.Instance.dense(np.zeros((n, n)), h)
+    t0 = np.array([3.5, 5.25], dtype=np.float32)
+    m0 = np.zeros((2, n), dtype=np.float32)  # the first sweep moves every spin by tanh(h/T)
+    r = O.mars_solve(inst, m0, t0, c_step=1.0, d_min=1e-4, k_max=k_max)
+    for k in range(2):
+        nl = len(_levels_by_hand(float(t0[k]), 1.0))
+        if k_max == 1:
+            assert r["sweeps"][k] == nl and r["capped_levels"][k] == nl
+        else:
+            assert r["sweeps"][k] == 2 * nl and r["capped_levels"][k] == 0
+
+
+def _two_spin_jacobi_amplitudes(a0, J, Ts, k_max):
+    """|s| after each synchronous sweep of the symmetric two-spin state."""
+    a, out = a0, []
+    for T in Ts:
+        for _ in range(k_max):
+            a = -math.tanh(J * a / T)
+            out.append(abs(a))
+    return out
+
+
+@pytest.mark.parametrize("k_max", [1, 2, 5, 1000])
+def test_k_max_cap_on_jacobi_two_cycle(k_max):
+    """Synchronous sweeps of a two-spin antiferromagnet (J_12 = J > 0 in the
+    paper's sign) below the stability bound T < J never converge.
+
+    From s1 = s2 = a both spins stay equal and a <- -tanh(J a / T): the map
+    flips the sign of a, and for J/T > 1 its second iterate has a non-zero
+    attracting fixed point, so |a| never falls to 0 and every sweep moves each
+    spin by |a_new| + |a_old| > d_min. Every level therefore takes exactly
+    k_max sweeps and is counted as capped. Sequential sweeps of the same pair
+    settle on the antiparallel fixed point instead and are never capped."""
+    J = 4.0
+    inst = O.Instance.dense(np.array([[0.0, J], [J, 0.0]]))
+    t0 = np.array([3.5, 2.25], dtype=np.float32)   # levels 2.5, 1.5, 0.5 and 1.25, 0.25
+    m0 = np.full((2, 2), 0.25, dtype=np.float32)
+    r = O.mars_solve(inst, m0, t0, c_step=1.0, d_min=1e-4, k_max=k_max, update=O.UPDATE_JACOBI)
+    for k in range(2):
+        Ts = _levels_by_hand(float(t0[k]), 1.0)
+        amps = _two_spin_jacobi_amplitudes(0.25, J, Ts, k_max)
+        assert min(amps) > 1e-3  # the premise: the two-cycle never dies out
+        assert r["levels"][k] == len(Ts)
+        assert r["sweeps"][k] == k_max * len(Ts)
+        assert r["capped_levels"][k] == len(Ts)
+        # the state after the last sweep: both spins equal, of the amplitude by hand
+        np.testing.assert_allclose(np.abs(r["m"][k]), amps[-1], rtol=1e-14, atol=0)
+        assert r["m"][k][0] == r["m"][k][1]
+    g = O.mars_solve(inst, m0, t0, c_step=1.0, d_min=1e-4, k_max=k_max, update=O.UPDATE_GS)
+    if k_max >= 50:
+        assert (g["capped_levels"] == 0).all()
+        assert (g["m"][:, 0] * g["m"][:, 1] < 0).all()
+
+
 def test_sweep_never_raises_mean_field_free_energy():
     """Sequential sweeps minimise the mean-field free energy one spin at a time.
 
