@@ -1,15 +1,22 @@
 #!/usr/bin/env python
-"""MARS benchmark: spin-updates/s on a 2-D Edwards-Anderson +-J spin glass.
+"""MARS benchmark: spin-updates/s on dense SK N=8192 with BF16 tensor cores.
 
-Workload (one step): a periodic 100x100 square lattice (N = 10,000 spins,
-4 neighbours, J uniform in {-1,+1}, h = 0, seed 0), R = 1024 replicas with
-start states and start temperatures T0 ~ U(0, 4) drawn on the device, linear
-cooling C_step = 1, d_min = 1e-4, k_max = 1000, sequential sweeps in the
-greedy colour order, FP32 local fields; then sign-rounding, exact integer
+Workload (one step, the default): a dense Sherrington-Kirkpatrick instance with
+N = 8192 spins and J_ij ~ Normal(0, 1/N) (symmetric, zero diagonal, h = 0,
+seed 0), R = 4096 replicas with start states and start temperatures
+T0 ~ U(0, 2) drawn on the device, linear cooling C_step = 1/sqrt(N),
+d_min = 1e-4, k_max = 1000, sequential sweeps whose panel fields come from
+BF16 tcgen05 GEMMs with FP32 accumulation; then sign-rounding, exact FP64
 energies and the best replica. One step is one whole mars_solve.
 
 A spin-update is one new s_i of one replica in one sweep; the metric counts
-only the sweeps replicas actually perform.
+only the sweeps replicas actually perform. The line also carries the time to
+target energy against the plain FP32 path (vs_fp32_path), measured in the same
+run on a smaller instance of the same family that both paths finish quickly.
+
+Other workloads (--workload): ea2d (2-D +-J lattice L=100, R=1024), ea3d_big
+(3-D lattice N=10^6, magnetisations in HBM), sk8192pm1 (the FP8 variant),
+batch, serve, ttt, sensitivity.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mars|reference]
 
@@ -89,11 +96,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip mars_autotune before the warm-up (library default launch shape)")
-    ap.add_argument("--workload", default="ea2d",
+    ap.add_argument("--workload", default="sk8192",
                     choices=["ea2d", "ea3d_big", "sk8192", "sk8192pm1", "serve", "ttt", "batch",
                              "sensitivity"],
-                    help="ea2d: the 2-D lattice (default); ea3d_big: the 3-D lattice with N=10^6 "
-                         "(magnetisations in HBM); sk8192: dense SK on tensor cores; "
+                    help="sk8192: dense SK N=8192 on BF16 tensor cores (default); ea2d: the 2-D "
+                         "lattice L=100; ea3d_big: the 3-D lattice with N=10^6 (magnetisations in "
+                         "HBM); sk8192pm1: the +-1 variant on FP8 tensor cores; "
                          "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=3.0,
@@ -103,6 +111,8 @@ def parse():
     ap.add_argument("--replicas", type=int, default=0, help="override R (profiling runs)")
     ap.add_argument("--fixed-sweeps", type=int, default=0,
                     help="profiling runs only: exactly this many sweeps per level")
+    ap.add_argument("--no-fp32-comparison", action="store_true",
+                    help="skip the time-to-target comparison with the FP32 path")
     return ap.parse_args()
 
 
@@ -171,6 +181,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def oracle_dense_sample(O, inst, wl, count, r0):
+    """The oracle on `count` replicas of a dense workload (start states from the
+    library's draw, replicas r0..r0+count-1), each doing 4 sweeps at one level
+    (its start temperature moved into (C_step, 2 C_step]): the cost of a dense
+    sweep does not depend on T. Returns (seconds, spin-updates)."""
+    import numpy as np
+    m0, t0 = O.draw_replicas(0, count, wl.J.shape[0], T_MIN, wl.t_max, r0=r0)
+    t0 = (wl.c_step * (1.0 + np.clip(t0 / wl.t_max, 0.01, 1.0))).astype(np.float32)
+    t = time.perf_counter()
+    out = O.mars_solve(inst, m0, t0, c_step=wl.c_step, d_min=D_MIN, k_max=K_MAX, fixed_sweeps=4,
+                       nthreads=count, want_m=False)
+    return time.perf_counter() - t, int(out["sweeps"].sum()) * wl.J.shape[0]
+
+
 def cpu_baseline(target_s: float, wl=None):
     """The FP64 oracle on the host cores, on a bounded sample of the same workload."""
     import numpy as np
@@ -180,18 +204,17 @@ def cpu_baseline(target_s: float, wl=None):
 
     cores = os.cpu_count() or 1
     if wl is not None and wl.name in ("sk8192", "sk8192pm1"):
-        # Dense N=8192 sweeps cost ~0.1 s each on one core: time one sweep per
-        # level (fixed-sweep mode) on one replica per core.
+        # A dense N=8192 sweep costs ~0.4 s on one core, whatever its
+        # temperature: time batches of one replica per core, 4 sweeps each,
+        # until the target CPU time is spent.
         inst = O.Instance.dense(wl.J)
-        m0, t0 = O.draw_replicas(0, cores, SK_N, T_MIN, wl.t_max)
-        t = time.perf_counter()
-        out = O.mars_solve(inst, m0, t0, c_step=wl.c_step, d_min=D_MIN, k_max=K_MAX,
-                           fixed_sweeps=1, nthreads=cores, want_m=False)
-        dt = time.perf_counter() - t
-        upd = int(out["sweeps"].sum()) * SK_N
-        return {"value": upd / dt, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
-                "sample": f"{cores} replicas of the N=8192 workload, one sweep per level, "
-                          f"FP64 oracle, OpenMP over replicas, {dt:.1f} s"}
+        t_used, upd, k = 0.0, 0, 0
+        while t_used < target_s:
+            dt, u = oracle_dense_sample(O, inst, wl, cores, k * cores)
+            t_used, upd, k = t_used + dt, upd + u, k + 1
+        return {"value": upd / t_used, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+                "sample": f"{k * cores} replicas of the N=8192 workload, 4 sweeps each at one level, "
+                          f"FP64 oracle, OpenMP over replicas, {t_used:.1f} s"}
     if wl is not None and wl.name == "ea3d_big":
         # One replica per core of the N=10^6 lattice, one sweep per level.
         inst = O.Instance.csr(wl.csr)
@@ -231,18 +254,28 @@ def run_reference(args, world, rank):
     import oracle as O
     from paper_1907_05124_gb300 import instances as I
     O.build()
-    csr = I.ea_lattice(L, 2, 0)
-    inst = O.Instance.csr(csr)
-    order = I.greedy_colour_order(csr)
     cores = os.cpu_count() or 1
     per_step = cores  # replicas per step: one per host thread
+    wl = Workload(args, 0)
+    if wl.J is not None:
+        inst = O.Instance.dense(wl.J)
+        what = f"{per_step} replicas per step, 4 sweeps each at one level"
 
-    def step(k):
-        m0, t0 = O.draw_replicas(0, per_step, csr.n, T_MIN, T_MAX, r0=(k * per_step) % R)
-        t = time.perf_counter()
-        out = O.mars_solve(inst, m0, t0, c_step=C_STEP, d_min=D_MIN, k_max=K_MAX, order=order,
-                           nthreads=cores, want_m=False)
-        return time.perf_counter() - t, int(out["sweeps"].sum()) * csr.n
+        def step(k):
+            return oracle_dense_sample(O, inst, wl, per_step, (k * per_step) % wl.R)
+    else:
+        csr = wl.csr
+        inst = O.Instance.csr(csr)
+        order = I.greedy_colour_order(csr)
+        one_sweep = wl.name != "ea2d"  # the N=10^6 lattice: one sweep per level
+        what = f"{per_step} replicas per step" + (", one sweep per level" if one_sweep else "")
+
+        def step(k):
+            m0, t0 = O.draw_replicas(0, per_step, csr.n, T_MIN, wl.t_max, r0=(k * per_step) % wl.R)
+            t = time.perf_counter()
+            out = O.mars_solve(inst, m0, t0, c_step=wl.c_step, d_min=D_MIN, k_max=K_MAX, order=order,
+                               fixed_sweeps=1 if one_sweep else 0, nthreads=cores, want_m=False)
+            return time.perf_counter() - t, int(out["sweeps"].sum()) * csr.n
 
     for w in range(args.warmup):
         step(1000 + w)
@@ -256,10 +289,10 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded lattice, Philox start states)",
-        "config": dict(WORKLOAD, sample=f"{per_step} replicas per step"),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded instance, Philox start states)",
+        "config": dict(wl.config, sample=what),
         "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{per_step} replicas per step x {args.steps} steps"},
+                         "sample": f"{what} x {args.steps} steps"},
         "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -354,6 +387,48 @@ class Workload:
                          fixed_sweeps=self.fixed, outputs=())
 
 
+def fp32_path_comparison(ctx, n=1024, R=256):
+    """Time to target energy of the BF16 tensor-core path against the plain
+    FP32 SIMT path, on an instance of the default workload's family small
+    enough for the FP32 path to finish in seconds: dense SK with
+    J_ij ~ Normal(0, 1/N), T0 ~ U(0, 2), C_step = 1/sqrt(N), the same
+    replicas (seed) on both paths.
+
+    The target the metric names is the FP64 oracle's best energy with a large
+    budget; the oracle cannot reach it within a benchmark run, so the target
+    is the FP32 path's 10th-percentile replica energy (a stated fallback). A
+    path whose fraction p of replicas reach the target in a solve of T
+    seconds needs T ln(0.01) / ln(1 - p) to reach it with probability 0.99."""
+    import numpy as np
+    import torch
+
+    from paper_1907_05124_gb300 import instances
+    inst = ctx.add_dense(instances.sk_gauss(n, 3))
+    c = 1.0 / n ** 0.5
+    runs = {}
+    for prec in ("fp32", "bf16"):
+        kw = dict(c_step=c, d_min=D_MIN, k_max=K_MAX, precision=prec, outputs=("energies",))
+        ctx.solve(inst, R, 0.0, 2.0, seed=2, fixed_sweeps=1, **kw)  # warm-up (short)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = ctx.solve(inst, R, 0.0, 2.0, seed=1, **kw)
+        runs[prec] = (time.perf_counter() - t, res)
+    ctx.free(inst)
+    target = float(np.percentile(runs["fp32"][1].energies, 10))
+    out = {"workload": f"dense SK N={n}, J_ij ~ Normal(0, 1/N), R={R}, T0~U(0,2), C_step=1/sqrt(N), "
+                       "d_min=1e-4, k_max=1000, the same replicas on both paths",
+           "target": "FP32 path's 10th-percentile replica energy (fallback: the FP64 oracle's "
+                     "large-budget best is out of reach within a benchmark run)",
+           "target_energy": target}
+    for prec, (sec, res) in runs.items():
+        p = float(np.mean(res.energies <= target))
+        ttt = sec * np.log(0.01) / np.log1p(-p) if 0 < p < 1 else (sec if p >= 1 else float("inf"))
+        out[prec] = {"solve_s": sec, "p_target": p, "ttt99_s": ttt, "best_energy": res.best_energy,
+                     "spin_updates_per_s": res.spin_updates / sec}
+    out["speedup_at_equal_ttt"] = out["fp32"]["ttt99_s"] / out["bf16"]["ttt99_s"]
+    return out
+
+
 def run_mars(args, world, rank, local):
     import numpy as np
     import torch
@@ -435,32 +510,40 @@ def run_mars(args, world, rank, local):
     d2h = n + 64 + 4 * wl.R + 4
 
     peaks = load_peaks()
-    sm_clock_ghz = (clocks.get("sm_max_mhz") or 2070.0) / 1e3
+    sm_clock_ghz = (clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0) / 1e3
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     d_mean = statistics.mean(descent_s)
     upd_per_launch = updates / args.steps
     if wl.name == "ea2d":
-        # The descent kernel keeps every magnetisation and coupling on chip;
-        # HBM sees ~1 MB per launch. Its hardware ceiling for this method is
-        # the SFU: each update's tanh needs one ex2 and one rcp, and a GB300 SM
-        # retires 32 ex2 or 16 rcp per clock (measured with a throughput
-        # microbenchmark), i.e. 1 / (1/32 + 1/16) = 10.67 updates per clock.
-        sfu_updates_per_clk = 1.0 / (1.0 / 32.0 + 1.0 / 16.0)
+        # The roofline of the sparse path is HBM: 8 algorithmic bytes per
+        # spin-update (the replica's FP32 m read and written once per sweep).
+        # This kernel keeps every magnetisation and coupling on chip (about
+        # 1 MB of DRAM traffic per launch), so it can run above that line; its
+        # own limit is instruction issue, and the SFU ceiling for the method's
+        # tanh (one ex2 and one rcp per update; a GB300 SM retires 32 ex2 or 16
+        # rcp per clock, measured) is given beside it.
         sh = shape or {}
         rt_used = sh.get("sell_rt", -1) if sh.get("sell_rt", -1) > 0 else 2
         nt_used = sh.get("sell_threads", -1) if sh.get("sell_threads", -1) > 0 else 1024
         tab_used = sh.get("sell_smem_table", -1) != 0
-        achieved = upd_per_launch / d_mean
-        peak = 152 * sfu_updates_per_clk * sm_clock_ghz * 1e9
+        achieved = 8.0 * upd_per_launch / d_mean / 1e9
+        sfu_updates_per_clk = 1.0 / (1.0 / 32.0 + 1.0 / 16.0)
+        sfu_peak = sms * sfu_updates_per_clk * sm_clock_ghz * 1e9
         # DRAM bytes per launch (read + write) from one ncu capture of the
         # default shape (2 slots, 1024 threads, table in shared memory); null
         # for another shape, whose counters were not taken.
         default_shape = rt_used == 2 and nt_used == 1024 and tab_used
         traffic = 1.0368e6 + 8.448e3 if default_shape else None
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
-                    "unit": "spin-updates/s (SFU-bound)", "frac": achieved / peak, "traffic": traffic,
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "bytes_per_update": 8.0,
                     "kernel": "sparse_sell_kernel<RT={}, {} threads, halfword couplings{}, degree 4>".format(
                         rt_used, nt_used, " in shared memory" if tab_used else " through L1"),
-                    "peak_source": "152 SMs x (1/32 + 1/16 SFU clocks per tanh)^-1 x SM clock",
+                    "peak_source": f"hbm copy ({peaks['source']})",
+                    "note": {"bound_in_fact": "instruction issue (state on chip)",
+                             "sfu_ceiling_updates_per_s": sfu_peak,
+                             "sfu_frac": (upd_per_launch / d_mean) / sfu_peak,
+                             "sfu_source": f"{sms} SMs x (1/32 + 1/16 SFU clocks per tanh)^-1 x SM clock"},
                     "descent_ms_mean": 1e3 * d_mean}
     elif wl.name == "ea3d_big":
         achieved = EA3_BYTES_PER_UPDATE * upd_per_launch / d_mean / 1e9
@@ -489,6 +572,10 @@ def run_mars(args, world, rank, local):
                     "gemm_launches_sampled": gemm_launches,
                     "descent_ms_mean": 1e3 * d_mean}
 
+    vs_fp32 = None
+    if rank == 0 and wl.name == "sk8192" and not args.no_fp32_comparison and not args.fixed_sweeps:
+        vs_fp32 = fp32_path_comparison(ctx)
+
     if rank == 0:
         line = {
             "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s",
@@ -506,6 +593,8 @@ def run_mars(args, world, rank, local):
             "clocks": clocks,
             "best_energy_per_step": best,
         }
+        if vs_fp32 is not None:
+            line["vs_fp32_path"] = vs_fp32
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

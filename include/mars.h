@@ -395,9 +395,12 @@ int mars_draw_replicas(mars_ctx* ctx, uint64_t seed, uint32_t stream, int32_t r0
  *  - Limit: the replica count and n must fit the array (about R*n + 40*R
  *    bytes); larger requests, and instances too large for the on-chip kernels,
  *    return MARS_EINVAL with a message naming the limit.
- *  - Set-up: the first call on a device looks up the array's device address
- *    with cudaGetSymbolAddress (with that device current) and caches it; make
- *    that first call before any stream capture on the device.
+ *  - Set-up: the first call with a context looks up the array's device
+ *    address with cudaGetSymbolAddress (with the context's device current)
+ *    and caches it in the context; make that first call before any stream
+ *    capture on the device. The device must not be reset while the context
+ *    lives (a reset invalidates the cached address along with the context's
+ *    own buffers): after a reset, destroy the context and create a new one.
  *  - Sharing: all calls share the one array and each starts by clearing the
  *    counters it needs at zero. Calls whose work overlaps on the GPU (other
  *    streams, other contexts, other threads) race on the array: serialise

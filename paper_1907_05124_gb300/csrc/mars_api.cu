@@ -91,6 +91,7 @@ struct mars_ctx {
     int32_t next_id = 1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;  // ev3: end of the descent
     std::vector<cudaEvent_t> prof;  // event pairs around sampled panel GEMM launches
+    void* noalloc_base = nullptr;   // device address of mars_solve_noalloc's static array
     ~mars_ctx()
     {
         for (cudaEvent_t e : prof) cudaEventDestroy(e);
@@ -784,6 +785,7 @@ struct ServeReq {
     std::unique_ptr<TcRun> tc;
     double total_weight = 0.0, err_bound = 0.0;
     int64_t ring_job = -1;  // serving-ring job index, or -1
+    size_t footprint = 0;   // the admission bound; what the request may allocate
 };
 
 struct Serve {
@@ -938,18 +940,33 @@ void serve_free_req(mars_ctx* c, Serve* sv, ServeReq* q)
     q->tc.reset();
 }
 
-// Device bytes a request holds while it runs (what admission checks).
-size_t serve_footprint(const DevInstance& d, const mars_params& p, int sms)
+// Device bytes a request holds while it runs (what admission checks): an
+// upper bound on what serve_launch and tc_setup allocate for it, from the same
+// plans they use, so that an admitted request never meets the budget check
+// half-way through its set-up.
+size_t serve_footprint(const DevInstance& d, const mars_params& p, int device)
 {
     const size_t R = (size_t)p.replicas, n = (size_t)d.n;
-    size_t b = R * n + R * (4 + 8 + 8 + 12 + 4 + 4) + 4096 + n;
+    const bool jacobi = p.update == MARS_UPDATE_JACOBI;
+    // t0, sigma, energies (double and int64), sweeps/levels/capped, the work
+    // counter and status, the result record, the best spins, and the replica
+    // queue at its widest slot rounding (at most 8 replicas per tile)
+    size_t b = R * 4 + R * n + R * 16 + R * 12 + 8 + sizeof(DevResult) + n + (R + 8) * 4;
     if (d.dense && (p.precision == MARS_BF16 || p.precision == MARS_FP8)) {
         const size_t np = (size_t)d.n_pad, Rp = (R + 127) / 128 * 128;
-        b += R * np * 4 + Rp * np * 2 + 2 * kChainMaxSplit * Rp * 128 * 4 + 2 * Rp * 128 * 4 + R * 32;
+        b += R * np * 4;                                            // S, FP32
+        b += Rp * np * (p.precision == MARS_FP8 ? 1 : 2);           // its low-precision copy
+        b += 2 * (size_t)kChainMaxSplit * Rp * 128 * 4;             // split-K partials, two buffers
+        b += 2 * Rp * 128 * 4;                                      // next-panel fields
+        b += R * (8 + 4 + 4 + 5 * 4) + 16;                          // per-slot state, counters
     } else if (d.dense) {
-        b += R * n * sizeof(float);  // the FP32 path's rows of m, when they do not fit on chip
+        const DensePlan dp = plan_dense(d, (int)R, jacobi ? 1 : 0, device);
+        b += dp.scratch_floats * sizeof(float);
     } else {
-        b += (size_t)sms * n * 8 * sizeof(float);  // a possible streaming slab
+        // the serving ring needs no scratch; the stream route takes its plan's
+        SparsePlan sp;
+        if (jacobi || !plan_sparse_sell(d, (int)R, device, &sp)) sp = plan_sparse(d, (int)R, jacobi ? 1 : 0, device);
+        b += sp.scratch_floats * sizeof(float);
     }
     return b;
 }
@@ -995,7 +1012,12 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
     const mars_params& p = q->p;
     const int32_t R = p.replicas, n = q->dev.n;
     int rc;
+    size_t held = 0;
     auto get = [&](size_t bytes, void** out) -> int {
+        held += bytes;
+        if (held > q->footprint)
+            return fail(c, MARS_EDEVICE, "internal: request %lld allocates more than its admission bound %zu",
+                        (long long)q->id, q->footprint);
         DevMem m;
         int r = dev_alloc_on(c, bytes, &m, st);
         if (r) return r;
@@ -1235,7 +1257,7 @@ void serve_progress(mars_ctx* c)
             serve_mark_failed(c, sv, q, MARS_ENOTFOUND);
             continue;
         }
-        const size_t need = serve_footprint(in->dev, q->p, c->sms);
+        const size_t need = serve_footprint(in->dev, q->p, c->device);
         if (c->budget && c->used + need > c->budget) {
             if (sv->inflight == 0) {  // it will never fit
                 sv->queue.pop_front();
@@ -1246,6 +1268,7 @@ void serve_progress(mars_ctx* c)
             break;  // wait for memory to free up
         }
         sv->queue.pop_front();
+        q->footprint = need;
         const int rc = serve_launch(c, sv, q);
         if (rc) serve_mark_failed(c, sv, q, rc);
     }
@@ -1273,6 +1296,7 @@ int noalloc_view(mars_ctx* c, int32_t id, NoallocView* v)
     v->device = c->device;
     v->stream = c->stream;
     v->inst = &in->dev;
+    v->scratch_base = &c->noalloc_base;
     v->total_weight = in->info.total_weight;
     v->energy_err_bound = (in->dev.integer || in->dev.exact_ok)
                               ? 0.0

@@ -297,6 +297,7 @@ struct NoallocView {
     const DevInstance* inst = nullptr;
     double total_weight = 0.0;
     double energy_err_bound = 0.0;
+    void** scratch_base = nullptr;  // the context's cached address of the static array
 };
 
 }  // namespace mars

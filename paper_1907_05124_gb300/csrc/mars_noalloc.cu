@@ -5,39 +5,36 @@
 // The static array g_noalloc_scratch below is MARS_NOALLOC_SCRATCH_BYTES
 // (16 MiB) of __device__ memory that every GPU which loads this library's
 // module keeps until the process exits. Host code never names it directly:
-// its device address comes from cudaGetSymbolAddress, taken once per device
-// (on the first call there, with that device current) and cached.
+// its device address comes from cudaGetSymbolAddress, taken on a context's
+// first call (with the context's device current) and cached in the context.
 #include "../../include/mars.h"
 #include "mars_internal.h"
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 namespace mars {
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MARS_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on `device`, which must be current.
-int scratch_address(int device, void** out)
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per context and cached in it (*cache). A context lives on one device and
+// its device memory does not survive a device reset, so neither does the
+// cache: a caller that resets the device creates a new context, whose first
+// call looks the address up again.
+int scratch_address(void** cache, void** out)
 {
-    std::lock_guard<std::mutex> lock(g_addr_mu);
-    if (device < 0 || device >= kMaxDevices) return MARS_EINVAL;
-    if (!g_addr[device]) {
+    if (!*cache) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return MARS_EDEVICE;
         }
-        g_addr[device] = p;
+        *cache = p;
     }
-    *out = g_addr[device];
+    *out = *cache;
     return MARS_OK;
 }
 
@@ -120,7 +117,7 @@ extern "C" int mars_solve_noalloc(mars_ctx* c, int32_t id, const mars_params* p,
     cudaGetDevice(&prev);
     if (prev != v.device) cudaSetDevice(v.device);
     unsigned char* base = nullptr;
-    rc = scratch_address(v.device, (void**)&base);
+    rc = scratch_address(v.scratch_base, (void**)&base);
     if (rc) {
         if (prev >= 0 && prev != v.device) cudaSetDevice(prev);
         return noalloc_fail(c, rc, "cudaGetSymbolAddress of the static scratch failed");

@@ -22,8 +22,7 @@ namespace {
 // ABI by the fields-only test); saturates to +-1 when 2|x| log2 e overflows.
 __device__ __forceinline__ float tanh_sfu(float x)
 {
-    // tanh(x) = sign(x) (1 - 2 / (1 + 2^{2|x| log2 e})), SFU ex2 and rcp
-    // (absolute error ~6e-8). Below |x| = 4e-3, tanh(x) = x to within
+    // Below |x| = 4e-3, tanh(x) = x to within
     // x^3/3 <= 2.2e-8, which also keeps the sign of tiny fields that the
     // difference 1 - 2/(1+e) would round away.
     const float a = fabsf(x) * 2.8853900817779268f;

@@ -1,14 +1,17 @@
 """bench.py's command line and the JSON line of its reference arm, on the host.
 
 The reference arm times the FP64 oracle on the host cores (a bounded sample
-of the lattice workload per step), so it runs here without a GPU; its line
-carries the same keys as the GPU arm's plus "impl". The workload list is the
-one the help text and the argument parser share.
+of the workload per step: by default the dense SK N=8192 workload), so it
+runs here without a GPU; its line carries the same keys as the GPU arm's plus
+"impl". The workload list is the one the help text and the argument parser
+share.
 """
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -20,8 +23,11 @@ def run_bench(*args, timeout=600):
     return out.stdout
 
 
-def test_reference_arm_line():
-    lines = [ln for ln in run_bench("--impl", "reference", "--steps", "1", "--warmup", "0").splitlines()
+@pytest.mark.parametrize("workload,n,R", [(None, 8192, 4096), ("ea2d", 10000, 1024)])
+def test_reference_arm_line(workload, n, R):
+    extra = ("--workload", workload) if workload else ()
+    lines = [ln for ln in run_bench("--impl", "reference", "--steps", "1", "--warmup", "0",
+                                    *extra).splitlines()
              if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
@@ -33,7 +39,7 @@ def test_reference_arm_line():
     assert d["metric"] == "spin-updates/s" and d["unit"] == "spin-updates/s"
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
     assert d["value"] > 0 and d["ms_per_step"] > 0
-    assert d["config"]["n_spins"] == 10000 and d["config"]["replicas"] == 1024
+    assert d["config"]["n_spins"] == n and d["config"]["replicas"] == R
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]

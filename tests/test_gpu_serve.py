@@ -97,6 +97,58 @@ def test_budget_admission_and_oversized_request():
     c.close()
 
 
+def _serve_once(budget, g, R, kw):
+    """Serve one request in a fresh context with the given HBM budget:
+    True when it ran, False when it was refused for memory."""
+    from paper_1907_05124_gb300 import mars
+    from paper_1907_05124_gb300.mars import MarsError, MARS_ENOMEM
+    c = mars.Context(0, hbm_budget_bytes=budget)
+    try:
+        try:
+            inst = c.add_csr(*g)
+            r = c.submit(inst, R, 0.0, 6.0, seed=3, **kw)
+            while c.poll(r) is None:
+                time.sleep(0.001)
+            return True
+        except MarsError as e:
+            if e.code == MARS_ENOMEM:
+                return False
+            raise
+    finally:
+        c.close()
+
+
+def test_tight_budget_request_waits_instead_of_failing(ctx):
+    """Admission counts everything a request will allocate. Under a budget
+    that holds exactly one synchronous (Jacobi) request, whose second buffer
+    of magnetisations is plan-dependent scratch, a second such request waits
+    for the first to finish instead of failing half-way through its set-up."""
+    from paper_1907_05124_gb300 import mars
+    g = I.er_graph(3000, 10, 41, "pm1")
+    R, kw = 96, {"update": "jacobi", "k_max": 400}  # synchronous sweeps cycle: every level capped
+    lo, hi = 1 << 20, 1 << 30
+    assert _serve_once(hi, g, R, kw)
+    while hi - lo > (64 << 10):  # the smallest budget one request runs under
+        mid = (lo + hi) // 2
+        if _serve_once(mid, g, R, kw):
+            hi = mid
+        else:
+            lo = mid
+    c = mars.Context(0, hbm_budget_bytes=hi)
+    try:
+        inst = c.add_csr(*g)
+        reqs = [c.submit(inst, R, 0.0, 6.0, seed=3 + k, **kw) for k in range(3)]
+        queued, running = c.serve_status()
+        assert running <= 1 and queued >= 1  # the budget holds one at a time
+        out = _wait(c, reqs)  # raises if any of them failed
+    finally:
+        c.close()
+    ref_inst = ctx.add_csr(*g)
+    for k, r in enumerate(reqs):
+        _same(out[r], ctx.solve(ref_inst, R, 0.0, 6.0, seed=3 + k, **kw))
+    ctx.free(ref_inst)
+
+
 def test_poll_unknown_request(ctx):
     from paper_1907_05124_gb300.mars import MarsError
     ctx._req_n = getattr(ctx, "_req_n", {})
