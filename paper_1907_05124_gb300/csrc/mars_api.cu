@@ -2,8 +2,7 @@
 // (validation, sweep order, level schedule, relabelling, device upload),
 // solve orchestration and result readback. All arithmetic of the method runs
 // in the kernels; this file moves data and makes decisions about launches.
-#include "../../include/mars.h"
-#include "mars_internal.h"
+#include "mars_host.h"
 
 #include <cudaTypedefs.h>
 #include <cuda_fp8.h>
@@ -23,10 +22,6 @@
 #include <vector>
 
 using namespace mars;
-
-// Upper bound on temperature levels per replica (t0 / c_step), so that every
-// descent ends and T - c_step always lowers T in double precision.
-static constexpr double kMaxLevels = 1e6;
 
 // Levels a replica with start temperature t0 visits under p's schedule (an
 // upper bound, counting a quench level).
@@ -49,56 +44,12 @@ bool schedule_ok(const mars_params* p)
            p->t_floor > 0.0 && std::isfinite(p->t_floor);
 }
 
-template <class S>
-void set_schedule(S& s, const mars_params* p)
+
+int env_flag(const char* name, int dflt)
 {
-    s.geometric = p->schedule == MARS_SCHEDULE_GEOMETRIC ? 1 : 0;
-    s.cool_ratio = p->cool_ratio;
-    s.t_floor = p->t_floor;
-    s.quench = p->quench ? 1 : 0;
+    const char* v = std::getenv(name);
+    return v && *v ? std::atoi(v) : dflt;
 }
-
-namespace {
-
-struct DevMem {
-    void* p = nullptr;
-    size_t bytes = 0;
-};
-
-struct Instance {
-    DevInstance dev;
-    std::vector<int32_t> order;     // caller's visiting order (new label a visits order[a]... see build)
-    std::vector<DevMem> mem;
-    mars_instance_info info{};
-    double abs_weight = 0.0;        // sum_{i<j} |J_ij| + sum |h_i| (error bound of float energies)
-};
-
-}  // namespace
-
-struct Serve;  // the serving engine's request table (below)
-void serve_release(mars_ctx* c);
-
-struct mars_ctx {
-    std::unique_ptr<Serve, void (*)(Serve*)> serve{nullptr, nullptr};
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    size_t budget = 0;
-    size_t used = 0;
-    int sms = 0;
-    std::string err = "no error";
-    std::map<int32_t, std::unique_ptr<Instance>> insts;
-    int32_t next_id = 1;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;  // ev3: end of the descent
-    std::vector<cudaEvent_t> prof;  // event pairs around sampled panel GEMM launches
-    void* noalloc_base = nullptr;   // device address of mars_solve_noalloc's static array
-    ~mars_ctx()
-    {
-        for (cudaEvent_t e : prof) cudaEventDestroy(e);
-    }
-};
-
-namespace {
 
 int fail(mars_ctx* c, int code, const char* fmt, ...)
 {
@@ -111,27 +62,6 @@ int fail(mars_ctx* c, int code, const char* fmt, ...)
     return code;
 }
 
-#define MARS_CUDA(c, call)                                                                  \
-    do {                                                                                     \
-        cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess)                                                               \
-            return fail((c), MARS_EDEVICE, "%s failed: %s", #call, cudaGetErrorString(e_));  \
-    } while (0)
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 int dev_alloc(mars_ctx* c, size_t bytes, DevMem* out)
 {
@@ -191,26 +121,6 @@ void dev_free(mars_ctx* c, DevMem* m)
     m->bytes = 0;
 }
 
-// RAII set of device buffers freed at scope exit (stream-ordered).
-struct Scratch {
-    mars_ctx* c;
-    std::vector<DevMem> bufs;
-    explicit Scratch(mars_ctx* ctx) : c(ctx) {}
-    ~Scratch()
-    {
-        for (auto& b : bufs) dev_free(c, &b);
-    }
-    template <typename T>
-    int get(size_t count, T** out)
-    {
-        DevMem m;
-        int rc = dev_alloc(c, count * sizeof(T), &m);
-        if (rc) return rc;
-        bufs.push_back(m);
-        *out = (T*)m.p;
-        return MARS_OK;
-    }
-};
 
 template <typename T>
 int upload(mars_ctx* c, Instance* in, const std::vector<T>& v, const T** out)
@@ -337,7 +247,6 @@ Instance* find(mars_ctx* c, int32_t id)
     return it == c->insts.end() ? nullptr : it->second.get();
 }
 
-}  // namespace
 
 // Round-to-nearest-even FP32 -> BF16 bits (host side, for uploads).
 uint16_t float_to_bf16_bits(float f)
@@ -347,944 +256,6 @@ uint16_t float_to_bf16_bits(float f)
     if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;  // NaN
     u += 0x7fffu + ((u >> 16) & 1u);
     return (uint16_t)(u >> 16);
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* ptr = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
-        cudaGetLastError();
-    }
-    return fn;
-}
-
-// Row-major [outer][inner] BF16 matrix, boxes of box_inner x box_outer with the
-// 128-byte swizzle (box_inner = 64 BF16 = 128 bytes).
-// 2-D K-major operand map: inner (K) extent `inner` elements of `elem` bytes,
-// `outer` rows, 128-byte swizzled boxes of box_inner x box_outer.
-bool encode_2d(CUtensorMap* m, CUtensorMapDataType dt, uint32_t elem, const void* base, uint64_t inner,
-               uint64_t outer, uint32_t box_inner, uint32_t box_outer)
-{
-    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
-    if (!fn) return false;
-    const cuuint64_t dims[2] = {inner, outer};
-    const cuuint64_t strides[1] = {inner * elem};
-    const cuuint32_t box[2] = {box_inner, box_outer};
-    const cuuint32_t es[2] = {1, 1};
-    return fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// The dense descent on tensor cores: slots in start-temperature order, a
-// sweep = for each 128-spin panel {BF16 panel GEMM, in-panel sequential
-// chain}, then the level step; the host checks the active count between
-// batches of sweeps. Writes the same per-replica outputs as the other paths.
-struct TcProfile {
-    double gemm_seconds = 0.0, gemm_flops = 0.0;
-    int64_t gemm_launches = 0;
-    int64_t launches = 0;  // every kernel of the descent, graph nodes counted one by one
-};
-
-// One dense tensor-core descent in flight: its device state, tensor maps and
-// the host's view of progress. run_dense_tc drives it to the end; the serving
-// engine steps it one batch of sweeps at a time.
-struct TcRun {
-    TcState t;
-    TcPanel g;
-    CUtensorMap tmJ, tmS;
-    int P = 0, ntiles = 0, splitk = 1, batch = 1;
-    int64_t done_sweeps = 0, sweep_cap = 0;
-    int32_t* h_counters = nullptr;  // pinned: active prefix, active count, error
-    int32_t active_at_batch = 0;
-    bool profile = false;
-    // One sweep (128-spin panels x {GEMM, chain}, then the level step) captured
-    // as a CUDA graph and replayed: 2P+2 launches become one graph launch.
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    // Replicas per warp in the chain, and the overlap of panel p+1's GEMM
-    // with panel p's chain: the GEMMs run on `side`, the chains on the run's
-    // stream, ordered by the events ev (fork, then per panel GEMM done and
-    // chain done). G and the chains' next-panel fields Gx alternate between
-    // two buffers by panel parity.
-    int rpw = 1;
-    bool overlap = false;
-    bool pair = false;                 // panels 2q, 2q+1 share one GEMM
-    std::vector<int> timed_rows;       // rows of each GEMM the profiled sweep timed
-    cudaStream_t side = nullptr;
-    std::vector<cudaEvent_t> ev;
-    float* Gbuf[2] = {nullptr, nullptr};
-    float* Gx[2] = {nullptr, nullptr};
-    ~TcRun()
-    {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        if (side) cudaStreamDestroy(side);
-    }
-};
-
-int env_flag(const char* name, int dflt)
-{
-    const char* v = std::getenv(name);
-    return v && *v ? std::atoi(v) : dflt;
-}
-
-constexpr int kTcBN = 128;
-
-// Device state of a tensor-core descent; buffers come from `get` so that the
-// blocking path (Scratch) and the serving engine (per-request lists) can own them.
-template <typename Get>
-int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t* rep_dev,
-             float t0_max, bool fp8, cudaStream_t st, Get&& get, TcRun* run)
-{
-    int rc;
-    TcState& t = run->t;
-    const int32_t R = s.R, n = d.n, n_pad = d.n_pad;
-    const int32_t R_pad = (R + kTcBN - 1) / kTcBN * kTcBN;
-    run->P = n_pad / 128;
-    run->ntiles = R_pad / kTcBN;
-    // Replicas per chain warp: several per warp cut the chain's issued
-    // instructions per replica and leave SMs to the overlapped GEMM. The
-    // defaults are the fastest shapes measured on a GB300 at N = 8192 (ms per
-    // sweep): R = 1024, overlap with 2 per warp 1.04 (pairs 1.13, plain 1.26);
-    // R = 4096, panel pairs with 4 per warp 1.94 (plain 2.04, overlap 2.51:
-    // the chain and the GEMM then compete for SMs). mars_autotune picks per
-    // instance.
-    const LaunchShape& sh = d.shape;
-    int rpw = sh.tc_rpw >= 0 ? sh.tc_rpw : env_flag("MARS_TC_RPW", R >= 2048 ? 4 : R >= 512 ? 2 : 1);
-    if (rpw != 1 && rpw != 2 && rpw != 4) rpw = 1;
-    run->rpw = rpw;
-    const int ov = sh.tc_overlap >= 0 ? sh.tc_overlap
-                                      : env_flag("MARS_TC_OVERLAP", R >= 512 && R < 2048 ? 1 : 0);
-    run->pair = run->P >= 2 && (sh.tc_pair >= 0 ? sh.tc_pair : env_flag("MARS_TC_PAIR", R >= 2048 ? 1 : 0)) != 0;
-    run->overlap = run->P >= 2 && ov != 0 && !run->pair;
-    // Split K until the panel GEMM fills the SMs in one wave (one CTA per SM):
-    // a short GEMM is bound by each CTA's pipeline fill and TMA bytes in
-    // flight, so more, shorter CTAs finish sooner.
-    int splitk = 1;
-    const int split_max = env_flag("MARS_TC_SPLITK_MAX", 16);
-    while (splitk < split_max && splitk * 2 <= kChainMaxSplit / rpw && run->ntiles * splitk * 2 <= c->sms &&
-           (n_pad / (fp8 ? 128 : 64)) % (splitk * 2) == 0)
-        splitk *= 2;
-    run->splitk = splitk;
-    t.R = R;
-    t.R_pad = R_pad;
-    t.n = n;
-    t.n_pad = n_pad;
-    t.splitk = splitk;
-    t.Jdiag = d.Jdiag;
-    t.Jsup = d.Jsup;
-    t.h = d.h;
-    t.new2old = d.new2old;
-    t.m0 = s.m0;
-    t.t0 = s.t0;
-    t.seed = s.seed;
-    t.stream = s.stream;
-    t.c_step = s.c_step;
-    t.d_min = s.d_min;
-    t.k_max = s.k_max;
-    t.fixed_sweeps = s.fixed_sweeps;
-    t.geometric = s.geometric;
-    t.quench = s.quench;
-    t.cool_ratio = s.cool_ratio;
-    t.t_floor = s.t_floor;
-    t.rep = rep_dev;
-    if ((rc = get((size_t)R * n_pad * sizeof(float), (void**)&t.S))) return rc;
-    if (fp8 && !d.J8) return fail(c, MARS_EINVAL, "FP8 needs couplings exact in E4M3");
-    if (fp8) {
-        if ((rc = get((size_t)R_pad * n_pad, (void**)&t.S8))) return rc;
-    } else if ((rc = get((size_t)R_pad * n_pad * sizeof(__nv_bfloat16), (void**)&t.Sb))) {
-        return rc;
-    }
-    const size_t g_floats = (size_t)splitk * R_pad * 128;
-    if ((rc = get(2 * g_floats * sizeof(float), (void**)&t.G))) return rc;
-    run->Gbuf[0] = t.G;
-    run->Gbuf[1] = t.G + g_floats;
-    if (run->overlap || run->pair) {
-        float* gx = nullptr;
-        if ((rc = get(2 * (size_t)R_pad * 128 * sizeof(float), (void**)&gx))) return rc;
-        run->Gx[0] = gx;
-        run->Gx[1] = gx + (size_t)R_pad * 128;
-    }
-    if (run->overlap) {
-        MARS_CUDA(c, cudaStreamCreateWithFlags(&run->side, cudaStreamNonBlocking));
-        run->ev.resize(1 + 2 * (size_t)run->P, nullptr);
-        for (cudaEvent_t& e : run->ev) MARS_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
-    if ((rc = get((size_t)R * sizeof(double), (void**)&t.T))) return rc;
-    if ((rc = get((size_t)R * sizeof(float), (void**)&t.invT))) return rc;
-    if ((rc = get((size_t)R * sizeof(float), (void**)&t.d))) return rc;
-    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.active))) return rc;
-    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.levels))) return rc;
-    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.lvl_sweeps))) return rc;
-    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.sweeps))) return rc;
-    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&t.capped))) return rc;
-    if ((rc = get(4 * sizeof(int32_t), (void**)&t.counters))) return rc;
-    if (fp8)
-        MARS_CUDA(c, cudaMemsetAsync(t.S8, 0, (size_t)R_pad * n_pad, st));
-    else
-        MARS_CUDA(c, cudaMemsetAsync(t.Sb, 0, (size_t)R_pad * n_pad * sizeof(__nv_bfloat16), st));
-    MARS_CUDA(c, cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), st));
-    const bool maps_ok =
-        fp8 ? encode_2d(&run->tmJ, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.J8, n_pad, n_pad, 128, 128) &&
-                  encode_2d(&run->tmS, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, t.S8, n_pad, R_pad, 128, kTcBN)
-            : encode_2d(&run->tmJ, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, d.Jbf, n_pad, n_pad, 64, 128) &&
-                  encode_2d(&run->tmS, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t.Sb, n_pad, R_pad, 64, kTcBN);
-    if (!maps_ok) return fail(c, MARS_EDEVICE, "tensor map encoding failed");
-    MARS_CUDA(c, launch_tc_init(t, st));
-    MARS_CUDA(c, launch_tc_prefix(t, st));
-    run->g.kblocks = n_pad / (fp8 ? 128 : 64) / splitk;
-    run->g.fp8 = fp8 ? 1 : 0;
-    run->g.R_pad = R_pad;
-    run->g.G = t.G;
-    run->g.active_prefix = t.counters;
-    run->g.err = t.counters + 2;
-    // Every replica ends within (levels + 1) x (sweeps per level) sweeps.
-    double levels_max = std::ceil((double)t0_max / s.c_step) + 1.0;
-    if (s.geometric)
-        levels_max = t0_max > s.t_floor ? std::ceil(std::log(s.t_floor / t0_max) / std::log(s.cool_ratio)) + 1.0
-                                        : 1.0;
-    levels_max += s.quench ? 1.0 : 0.0;
-    run->sweep_cap = (int64_t)(levels_max * (double)(s.fixed_sweeps > 0 ? s.fixed_sweeps : s.k_max)) + 1;
-    run->batch = 1;
-    run->done_sweeps = 0;
-    return MARS_OK;
-}
-
-// One sweep as direct launches; with `timed`, event pairs bracket each GEMM.
-// With the overlap, panel p's GEMM (on the side stream) leaves panel p-1's
-// K range out and waits only for chain p-2, whose G buffer it overwrites;
-// chain p waits for GEMM p and takes panel p-1's part of its fields from
-// chain p-1 (Gx).
-int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
-{
-    const bool ov = run->overlap;
-    const int P = run->P;
-    if (timed) run->timed_rows.clear();
-    if (run->pair) {
-        // panels in pairs: one GEMM for panels pp and pp+1, chain pp (which
-        // adds its new spins to panel pp+1's fields), chain pp+1
-        const int kb_per_panel = run->g.fp8 ? 1 : 2;
-        for (int pp = 0; pp < P; pp += 2) {
-            const int e = (int)run->timed_rows.size();
-            TcPanel g = run->g;
-            g.p0 = pp * 128;
-            g.G = run->Gbuf[0];
-            const bool two = pp + 1 < P;
-            if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * e], st));
-            if (two) {
-                g.G1 = run->Gbuf[1];
-                g.skip_kb = kb_per_panel * pp;
-                MARS_CUDA(c, launch_tc_pair_gemm(run->tmJ, run->tmS, g, run->ntiles, run->splitk, st));
-            } else {
-                g.skip_kb = -1;
-                MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->ntiles, run->splitk, st));
-            }
-            if (timed) {
-                MARS_CUDA(c, cudaEventRecord(c->prof[2 * e + 1], st));
-                run->timed_rows.push_back(two ? 256 : 128);
-            }
-            MARS_CUDA(c, launch_tc_chain(run->t, pp, run->rpw, run->Gbuf[0], nullptr, two ? run->Gx[0] : nullptr,
-                                         st));
-            if (two) MARS_CUDA(c, launch_tc_chain(run->t, pp + 1, run->rpw, run->Gbuf[1], run->Gx[0], nullptr, st));
-        }
-        MARS_CUDA(c, launch_tc_advance(run->t, st));
-        return MARS_OK;
-    }
-    cudaStream_t gs = ov ? run->side : st;
-    if (ov) {
-        MARS_CUDA(c, cudaEventRecord(run->ev[0], st));
-        MARS_CUDA(c, cudaStreamWaitEvent(gs, run->ev[0], 0));
-    }
-    for (int pp = 0; pp < P; ++pp) {
-        TcPanel g = run->g;
-        g.p0 = pp * 128;
-        g.G = run->Gbuf[pp & 1];
-        g.skip_kb = ov && pp > 0 ? (g.fp8 ? 1 : 2) * (pp - 1) : -1;  // panel pp-1's K blocks
-        if (ov && pp >= 2) MARS_CUDA(c, cudaStreamWaitEvent(gs, run->ev[2 + 2 * (pp - 2)], 0));
-        if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp], gs));
-        MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->ntiles, run->splitk, gs));
-        if (timed) {
-            MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp + 1], gs));
-            run->timed_rows.push_back(128);
-        }
-        if (ov) {
-            MARS_CUDA(c, cudaEventRecord(run->ev[1 + 2 * pp], gs));
-            MARS_CUDA(c, cudaStreamWaitEvent(st, run->ev[1 + 2 * pp], 0));
-        }
-        const float* gx_in = ov && pp > 0 ? run->Gx[pp & 1] : nullptr;
-        float* gx_out = ov && pp + 1 < P ? run->Gx[(pp + 1) & 1] : nullptr;
-        MARS_CUDA(c, launch_tc_chain(run->t, pp, run->rpw, run->Gbuf[pp & 1], gx_in, gx_out, st));
-        if (ov) MARS_CUDA(c, cudaEventRecord(run->ev[2 + 2 * pp], st));
-    }
-    MARS_CUDA(c, launch_tc_advance(run->t, st));
-    return MARS_OK;
-}
-
-// Enqueue run->batch sweeps (the first one with timed GEMMs when profiling,
-// the rest as replays of the captured sweep), then the copy of the counters
-// to pinned memory.
-int tc_enqueue_batch(mars_ctx* c, TcRun* run, cudaStream_t st)
-{
-    int rc;
-    if (run->profile) {
-        while ((int)c->prof.size() < 2 * run->P) {
-            cudaEvent_t e;
-            MARS_CUDA(c, cudaEventCreate(&e));
-            c->prof.push_back(e);
-        }
-    }
-    for (int b = 0; b < run->batch; ++b) {
-        if (b == 0 && run->profile) {
-            if ((rc = tc_enqueue_sweep(c, run, st, true))) return rc;
-            continue;
-        }
-        if (!run->exec) {
-            MARS_CUDA(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-            rc = tc_enqueue_sweep(c, run, st, false);
-            cudaGraph_t graph = nullptr;
-            const cudaError_t e = cudaStreamEndCapture(st, &graph);
-            if (rc) return rc;
-            if (e != cudaSuccess) return fail(c, MARS_EDEVICE, "sweep capture failed: %s", cudaGetErrorString(e));
-            run->graph = graph;
-            MARS_CUDA(c, cudaGraphInstantiate(&run->exec, run->graph, 0));
-        }
-        MARS_CUDA(c, cudaGraphLaunch(run->exec, st));
-    }
-    run->done_sweeps += run->batch;
-    MARS_CUDA(c, cudaMemcpyAsync(run->h_counters, run->t.counters, 4 * sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, st));
-    return MARS_OK;
-}
-
-// After a batch's counters arrived: 1 = more sweeps needed, 0 = done, < 0 = error.
-int tc_after_batch(mars_ctx* c, TcRun* run)
-{
-    if (run->h_counters[2] != 0) return fail(c, MARS_ETIMEOUT, "a tensor-core pipeline wait gave up");
-    if (run->h_counters[1] == 0) return 0;
-    if (run->done_sweeps > run->sweep_cap) return fail(c, MARS_EDEVICE, "descent exceeded its sweep bound");
-    run->active_at_batch = run->h_counters[1];
-    run->batch = std::min(run->batch * 2, 32);
-    return 1;
-}
-
-// The dense descent on tensor cores, blocking: slots in start-temperature
-// order, a sweep = for each 128-spin panel {BF16 panel GEMM, in-panel
-// sequential chain}, then the level step; the host checks the active count
-// between batches of sweeps.
-int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve& s,
-                 const std::vector<int32_t>& reps, float t0_max, Scratch& S, TcProfile* prof,
-                 bool polish)
-{
-    (void)p;
-    cudaStream_t st = c->stream;
-    int rc;
-    int32_t* rep = nullptr;
-    if ((rc = S.get(s.R, &rep))) return rc;
-    MARS_CUDA(c, cudaMemcpyAsync(rep, reps.data(), s.R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    TcRun run;
-    auto get = [&](size_t bytes, void** out) -> int {
-        unsigned char* q = nullptr;
-        int r = S.get(bytes, &q);
-        *out = q;
-        return r;
-    };
-    if ((rc = tc_setup(c, in->dev, s, rep, t0_max, p->precision == MARS_FP8, st, get, &run))) return rc;
-    prof->launches += 2;  // start states, active prefix
-    int32_t* pinned = nullptr;
-    MARS_CUDA(c, cudaMallocHost((void**)&pinned, 4 * sizeof(int32_t)));
-    run.h_counters = pinned;
-    run.profile = true;
-    MARS_CUDA(c, cudaMemcpyAsync(run.h_counters, run.t.counters, 4 * sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, st));
-    cudaError_t se = cudaStreamSynchronize(st);
-    run.active_at_batch = run.h_counters[1];
-    int state = se == cudaSuccess ? (run.h_counters[1] > 0 ? 1 : 0) : -1;
-    while (state == 1) {
-        const int32_t active_now = run.active_at_batch;
-        if ((rc = tc_enqueue_batch(c, &run, st))) { cudaFreeHost(pinned); return rc; }
-        // per sweep: the GEMMs (one per panel, or per pair), P chains, the level step and prefix
-        const int gemms = run.pair ? (run.P + 1) / 2 : run.P;
-        prof->launches += (int64_t)run.batch * (gemms + run.P + 2);
-        se = cudaStreamSynchronize(st);
-        if (se != cudaSuccess) break;
-        for (size_t e = 0; e < run.timed_rows.size(); ++e) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, c->prof[2 * e], c->prof[2 * e + 1]);
-            prof->gemm_seconds += ms * 1e-3;
-            prof->gemm_launches += 1;
-            prof->gemm_flops += 2.0 * run.timed_rows[e] * (double)in->dev.n * (double)active_now;
-        }
-        run.timed_rows.clear();
-        state = tc_after_batch(c, &run);
-    }
-    cudaFreeHost(pinned);
-    if (se != cudaSuccess) return fail(c, MARS_EDEVICE, "CUDA error: %s", cudaGetErrorString(se));
-    if (state < 0) return state;
-    if (!polish) MARS_CUDA(c, cudaEventRecord(c->ev3, st));
-    MARS_CUDA(c, launch_tc_finalize(run.t, in->dev, s, st));
-    prof->launches += 1;
-    if (polish) {
-        // FP32 polish: the SIMT dense path re-converges each replica's last
-        // level from its BF16 final state; it writes the spins and energies.
-        float* m_out = nullptr;
-        double* t_last = nullptr;
-        if ((rc = S.get((size_t)s.R * in->dev.n, &m_out))) return rc;
-        if ((rc = S.get(s.R, &t_last))) return rc;
-        MARS_CUDA(c, launch_tc_export(run.t, in->dev, m_out, t_last, st));
-        DevSolve ps = s;
-        ps.m0 = m_out;
-        ps.t_first = t_last;
-        ps.one_level = 1;
-        ps.add_counts = 1;
-        ps.jacobi = 0;
-        DensePlan dp = plan_dense(in->dev, s.R, 0, c->device);
-        if (dp.scratch_floats && (rc = S.get(dp.scratch_floats, &ps.m_scratch))) return rc;
-        MARS_CUDA(c, launch_dense(in->dev, ps, dp, st));
-        MARS_CUDA(c, cudaEventRecord(c->ev3, st));
-        prof->launches += 2;
-    }
-    return MARS_OK;
-}
-
-// ---------------------------------------------------------------------------
-// Serving: requests admitted while others run (continuous batching).
-//
-// mars_submit queues a request; every mars_submit / mars_poll call advances
-// the engine: finished requests are collected (their events have fired), and
-// queued requests are admitted in arrival order while an in-flight slot is
-// free and the HBM budget holds their buffers. Each admitted request runs on
-// its own stream, so its kernels overlap with the others' on the device; a
-// dense tensor-core request advances one batch of sweeps per event.
-// ---------------------------------------------------------------------------
-enum class ReqState { Queued, Running, TcRunning, RingRunning, Finishing, Done, Failed };
-
-struct ServeReq {
-    int64_t id = 0;
-    int32_t inst = 0;
-    mars_params p{};
-    ReqState state = ReqState::Queued;
-    int rc = MARS_OK;
-    std::string err;
-    int slot = -1;
-    cudaStream_t st = nullptr;
-    std::vector<DevMem> bufs;
-    DevSolve s;
-    DevInstance dev;
-    DevResult* dres = nullptr;
-    int8_t* dbest = nullptr;
-    unsigned char* pinned = nullptr;  // DevResult | status | counters[4] | best spins
-    cudaEvent_t ev = nullptr;
-    std::unique_ptr<TcRun> tc;
-    double total_weight = 0.0, err_bound = 0.0;
-    int64_t ring_job = -1;  // serving-ring job index, or -1
-    size_t footprint = 0;   // the admission bound; what the request may allocate
-};
-
-struct Serve {
-    std::vector<cudaStream_t> streams;
-    std::vector<int> free_slots;
-    std::deque<int64_t> queue;
-    std::map<int64_t, std::unique_ptr<ServeReq>> reqs;
-    int64_t next_id = 1;
-    int max_inflight = 8;
-    int inflight = 0;
-    // The serving ring: sparse requests run as jobs of one persistent kernel
-    // (continuous batching: a job published while the kernel runs is picked
-    // up by CTAs as they free up). Descriptors are staged in pinned memory
-    // and copied on one publish stream, so the tail the kernel reads never
-    // runs ahead of the descriptors it covers.
-    bool ring_on = false;
-    RingPlan plan;
-    ServeRing* ring = nullptr;      // device
-    BatchJob* stage_jobs = nullptr; // pinned [kRingCap]
-    RingSlot* stage_slots = nullptr;
-    int32_t* stage_tail = nullptr;
-    int32_t* done = nullptr;        // host-mapped flags [kRingCap]
-    int32_t* done_dev = nullptr;
-    int ring_refs = 0;              // requests that still read their ring slot
-    cudaStream_t pub_st = nullptr, ring_st = nullptr;
-    cudaEvent_t ring_ev = nullptr;
-    bool kernel_live = false;
-    int64_t tail = 0;
-    int64_t ring_jobs = 0;          // jobs served through the ring
-    int64_t stream_jobs = 0;        // jobs served on their own streams
-    int idle_polls = 50;            // about 100 us without work before the kernel exits
-};
-
-void serve_delete(Serve* sv) { delete sv; }
-
-// Set the ring up on first use; false when it is unavailable (then every
-// request takes its own stream).
-bool serve_ring_init(mars_ctx* c, Serve* sv)
-{
-    if (sv->ring) return true;
-    if (!env_flag("MARS_SERVE_RING", 1) || !plan_serve_ring(c->device, &sv->plan)) return false;
-    bool ok = cudaMalloc((void**)&sv->ring, sizeof(ServeRing)) == cudaSuccess &&
-              cudaMemset(sv->ring, 0, sizeof(ServeRing)) == cudaSuccess &&
-              cudaMallocHost((void**)&sv->stage_jobs, sizeof(BatchJob) * kRingCap) == cudaSuccess &&
-              cudaMallocHost((void**)&sv->stage_slots, sizeof(RingSlot) * kRingCap) == cudaSuccess &&
-              cudaMallocHost((void**)&sv->stage_tail, sizeof(int32_t) * kRingCap) == cudaSuccess &&
-              cudaHostAlloc((void**)&sv->done, sizeof(int32_t) * kRingCap, cudaHostAllocMapped) == cudaSuccess &&
-              cudaHostGetDevicePointer((void**)&sv->done_dev, sv->done, 0) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&sv->pub_st, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&sv->ring_st, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&sv->ring_ev, cudaEventDisableTiming) == cudaSuccess &&
-              cudaDeviceSynchronize() == cudaSuccess;
-    if (ok) std::memset(sv->done, 0, sizeof(int32_t) * kRingCap);
-    sv->ring_on = ok;
-    return ok;
-}
-
-void serve_ring_free(Serve* sv)
-{
-    if (sv->ring) {
-        int32_t one = 1;
-        cudaMemcpyAsync(&sv->ring->stop, &one, sizeof one, cudaMemcpyHostToDevice, sv->pub_st);
-        cudaStreamSynchronize(sv->pub_st);
-        cudaStreamSynchronize(sv->ring_st);
-        cudaFree(sv->ring);
-        sv->ring = nullptr;
-    }
-    if (sv->stage_jobs) cudaFreeHost(sv->stage_jobs);
-    if (sv->stage_slots) cudaFreeHost(sv->stage_slots);
-    if (sv->stage_tail) cudaFreeHost(sv->stage_tail);
-    if (sv->done) cudaFreeHost(sv->done);
-    if (sv->pub_st) cudaStreamDestroy(sv->pub_st);
-    if (sv->ring_st) cudaStreamDestroy(sv->ring_st);
-    if (sv->ring_ev) cudaEventDestroy(sv->ring_ev);
-    sv->stage_jobs = nullptr;
-    sv->stage_slots = nullptr;
-    sv->stage_tail = nullptr;
-    sv->done = nullptr;
-    sv->pub_st = sv->ring_st = nullptr;
-    sv->ring_ev = nullptr;
-    sv->ring_on = false;
-}
-
-// Launch the serving kernel unless one is still running.
-int serve_ring_ensure_kernel(mars_ctx* c, Serve* sv)
-{
-    if (sv->kernel_live) {
-        const cudaError_t e = cudaEventQuery(sv->ring_ev);
-        if (e == cudaErrorNotReady) return MARS_OK;
-        if (e != cudaSuccess) return fail(c, MARS_EDEVICE, "serving kernel: %s", cudaGetErrorString(e));
-        sv->kernel_live = false;
-    }
-    MARS_CUDA(c, launch_serve_ring(sv->ring, sv->plan, sv->idle_polls, sv->ring_st));
-    MARS_CUDA(c, cudaEventRecord(sv->ring_ev, sv->ring_st));
-    sv->kernel_live = true;
-    return MARS_OK;
-}
-
-Serve* serve_get(mars_ctx* c)
-{
-    if (!c->serve) c->serve = std::unique_ptr<Serve, void (*)(Serve*)>(new Serve(), serve_delete);
-    Serve* sv = c->serve.get();
-    while ((int)sv->streams.size() < sv->max_inflight) {
-        cudaStream_t st;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) break;
-        sv->free_slots.push_back((int)sv->streams.size());
-        sv->streams.push_back(st);
-    }
-    return sv;
-}
-
-struct PinnedView {
-    DevResult* res;
-    int32_t* status;
-    int32_t* counters;
-    int8_t* best;
-};
-
-PinnedView pinned_view(unsigned char* base)
-{
-    PinnedView v;
-    v.res = (DevResult*)base;
-    v.status = (int32_t*)(base + 128);
-    v.counters = (int32_t*)(base + 192);
-    v.best = (int8_t*)(base + 256);
-    return v;
-}
-
-void serve_free_req(mars_ctx* c, Serve* sv, ServeReq* q)
-{
-    if (q->ring_job >= 0) {
-        sv->ring_refs -= 1;
-        q->ring_job = -1;
-    }
-    if (q->st) {
-        for (auto& b : q->bufs) dev_free_on(c, &b, q->st);
-        q->bufs.clear();
-    }
-    if (q->pinned) {
-        cudaFreeHost(q->pinned);
-        q->pinned = nullptr;
-    }
-    if (q->ev) {
-        cudaEventDestroy(q->ev);
-        q->ev = nullptr;
-    }
-    if (q->slot >= 0) {
-        sv->free_slots.push_back(q->slot);
-        sv->inflight -= 1;
-        q->slot = -1;
-    }
-    q->tc.reset();
-}
-
-// Device bytes a request holds while it runs (what admission checks): an
-// upper bound on what serve_launch and tc_setup allocate for it, from the same
-// plans they use, so that an admitted request never meets the budget check
-// half-way through its set-up.
-size_t serve_footprint(const DevInstance& d, const mars_params& p, int device)
-{
-    const size_t R = (size_t)p.replicas, n = (size_t)d.n;
-    const bool jacobi = p.update == MARS_UPDATE_JACOBI;
-    // t0, sigma, energies (double and int64), sweeps/levels/capped, the work
-    // counter and status, the result record, the best spins, and the replica
-    // queue at its widest slot rounding (at most 8 replicas per tile)
-    size_t b = R * 4 + R * n + R * 16 + R * 12 + 8 + sizeof(DevResult) + n + (R + 8) * 4;
-    if (d.dense && (p.precision == MARS_BF16 || p.precision == MARS_FP8)) {
-        const size_t np = (size_t)d.n_pad, Rp = (R + 127) / 128 * 128;
-        b += R * np * 4;                                            // S, FP32
-        b += Rp * np * (p.precision == MARS_FP8 ? 1 : 2);           // its low-precision copy
-        b += 2 * (size_t)kChainMaxSplit * Rp * 128 * 4;             // split-K partials, two buffers
-        b += 2 * Rp * 128 * 4;                                      // next-panel fields
-        b += R * (8 + 4 + 4 + 5 * 4) + 16;                          // per-slot state, counters
-    } else if (d.dense) {
-        const DensePlan dp = plan_dense(d, (int)R, jacobi ? 1 : 0, device);
-        b += dp.scratch_floats * sizeof(float);
-    } else {
-        // the serving ring needs no scratch; the stream route takes its plan's
-        SparsePlan sp;
-        if (jacobi || !plan_sparse_sell(d, (int)R, device, &sp)) sp = plan_sparse(d, (int)R, jacobi ? 1 : 0, device);
-        b += sp.scratch_floats * sizeof(float);
-    }
-    return b;
-}
-
-// The request's results to pinned memory, then its event.
-int serve_copy_results(mars_ctx* c, ServeReq* q)
-{
-    cudaStream_t st = q->st;
-    PinnedView v = pinned_view(q->pinned);
-    MARS_CUDA(c, cudaMemcpyAsync(v.res, q->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, st));
-    MARS_CUDA(c, cudaMemcpyAsync(v.status, q->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    MARS_CUDA(c, cudaMemcpyAsync(v.best, q->dbest, q->dev.n, cudaMemcpyDeviceToHost, st));
-    MARS_CUDA(c, cudaEventRecord(q->ev, st));
-    q->state = ReqState::Finishing;
-    return MARS_OK;
-}
-
-int serve_finish_enqueue(mars_ctx* c, ServeReq* q)
-{
-    cudaStream_t st = q->st;
-    if (!q->dev.integer && q->dev.exact_ok)
-        MARS_CUDA(c, launch_energy(q->dev, q->s.sigma, q->s.R, q->s.energy, nullptr, q->s.status, st));
-    MARS_CUDA(c, launch_best(q->s, q->dev.n, q->dev.integer, q->dbest, q->dres, st));
-    return serve_copy_results(c, q);
-}
-
-// Allocate, enqueue the whole pipeline (or the first batch of a tensor-core
-// descent) on the request's stream, and record its event.
-int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
-{
-    Instance* in = find(c, q->inst);
-    if (!in) return fail(c, MARS_ENOTFOUND, "instance %d was freed before its request ran", q->inst);
-    q->dev = in->dev;
-    q->total_weight = in->info.total_weight;
-    q->err_bound = (in->dev.integer || in->dev.exact_ok)
-                       ? 0.0
-                       : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + in->dev.n);
-    q->slot = sv->free_slots.back();
-    sv->free_slots.pop_back();
-    sv->inflight += 1;
-    q->st = sv->streams[q->slot];
-    cudaStream_t st = q->st;
-    const mars_params& p = q->p;
-    const int32_t R = p.replicas, n = q->dev.n;
-    int rc;
-    size_t held = 0;
-    auto get = [&](size_t bytes, void** out) -> int {
-        held += bytes;
-        if (held > q->footprint)
-            return fail(c, MARS_EDEVICE, "internal: request %lld allocates more than its admission bound %zu",
-                        (long long)q->id, q->footprint);
-        DevMem m;
-        int r = dev_alloc_on(c, bytes, &m, st);
-        if (r) return r;
-        q->bufs.push_back(m);
-        *out = m.p;
-        return MARS_OK;
-    };
-    MARS_CUDA(c, cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming));
-    MARS_CUDA(c, cudaMallocHost((void**)&q->pinned, 256 + (size_t)n));
-    DevSolve& s = q->s;
-    s.R = R;
-    s.seed = p.seed;
-    s.stream = p.stream;
-    s.c_step = p.c_step;
-    s.d_min = (float)p.d_min;
-    s.k_max = p.k_max;
-    s.fixed_sweeps = p.fixed_sweeps;
-    set_schedule(s, &p);
-    s.jacobi = p.update == MARS_UPDATE_JACOBI;
-    s.m0 = p.m0;
-    float* t0 = nullptr;
-    if ((rc = get((size_t)R * sizeof(float), (void**)&t0))) return rc;
-    if (p.t0) {
-        MARS_CUDA(c, cudaMemcpyAsync(t0, p.t0, R * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    } else {
-        MARS_CUDA(c, launch_draw(p.seed, p.stream, 0, R, 0, p.t_min, p.t_max, nullptr, t0, st));
-    }
-    s.t0 = t0;
-    if ((rc = get((size_t)R * n, (void**)&s.sigma))) return rc;
-    if ((rc = get((size_t)R * sizeof(double), (void**)&s.energy))) return rc;
-    if ((rc = get((size_t)R * sizeof(long long), (void**)&s.energy_i64))) return rc;
-    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&s.sweeps))) return rc;
-    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&s.levels))) return rc;
-    if ((rc = get((size_t)R * sizeof(int32_t), (void**)&s.capped))) return rc;
-    if ((rc = get(2 * sizeof(int32_t), (void**)&s.work_counter))) return rc;
-    s.status = s.work_counter + 1;
-    if ((rc = get(sizeof(DevResult), (void**)&q->dres))) return rc;
-    if ((rc = get((size_t)n, (void**)&q->dbest))) return rc;
-    const bool tc = q->dev.dense && (p.precision == MARS_BF16 || p.precision == MARS_FP8);
-    int rt = 1;
-    SparsePlan sp;
-    DensePlan dp;
-    if (tc) {
-        rt = 1;
-    } else if (q->dev.dense) {
-        dp = plan_dense(q->dev, R, s.jacobi, c->device);
-        if (dp.scratch_floats && (rc = get(dp.scratch_floats * sizeof(float), (void**)&s.m_scratch))) return rc;
-    } else {
-        // the serving ring: one persistent kernel for every sparse request
-        // (integer couplings: the kernel's fused int64 energies are final, so
-        // the job needs no kernel after the serving kernel)
-        int job_rt = 1;
-        const int fmt = !s.jacobi && q->dev.integer && serve_ring_init(c, sv)
-                            ? ring_job_format(q->dev, sv->plan, &job_rt)
-                            : -1;
-        const int k = (int)sv->tail;
-        if (fmt >= 0 && sv->tail < kRingCap) {
-            const int32_t rr = job_rt;
-            const int32_t ntiles = (R + rr - 1) / rr;
-            int32_t* queue = nullptr;
-            if ((rc = get((size_t)ntiles * rr * sizeof(int32_t), (void**)&queue))) return rc;
-            MARS_CUDA(c, launch_queue_identity(queue, ntiles * rr, R, s.work_counter, st));
-            s.tile_rep = queue;
-            s.ntiles = ntiles;
-            s.rt = rr;
-            // the job's counters and flag live in the ring
-            s.work_counter = &sv->ring->slots[k].taken;
-            s.status = &sv->ring->slots[k].status;
-            s.finished = &sv->ring->slots[k].finished;
-            s.done_flag = sv->done_dev + k;
-            s.res = q->dres;
-            s.best_out = q->dbest;
-            sv->done[k] = 0;
-            BatchJob job;
-            job.in = q->dev;
-            job.s = s;
-            job.fmt = fmt;
-            job.rt = job_rt;
-            sv->stage_jobs[k] = job;
-            sv->stage_slots[k] = RingSlot{};
-            sv->stage_tail[k] = (int32_t)(sv->tail + 1);
-            // publish after the request's own set-up (start temperatures, queue)
-            MARS_CUDA(c, cudaEventRecord(q->ev, st));
-            MARS_CUDA(c, cudaStreamWaitEvent(sv->pub_st, q->ev, 0));
-            MARS_CUDA(c, cudaMemcpyAsync(&sv->ring->jobs[k], &sv->stage_jobs[k], sizeof(BatchJob),
-                                         cudaMemcpyHostToDevice, sv->pub_st));
-            MARS_CUDA(c, cudaMemcpyAsync(&sv->ring->slots[k], &sv->stage_slots[k], sizeof(RingSlot),
-                                         cudaMemcpyHostToDevice, sv->pub_st));
-            MARS_CUDA(c, cudaMemcpyAsync(&sv->ring->tail, &sv->stage_tail[k], sizeof(int32_t),
-                                         cudaMemcpyHostToDevice, sv->pub_st));
-            q->ring_job = sv->tail;
-            sv->ring_refs += 1;
-            sv->tail += 1;
-            sv->ring_jobs += 1;
-            q->state = ReqState::RingRunning;
-            return serve_ring_ensure_kernel(c, sv);
-        }
-        if (s.jacobi || !plan_sparse_sell(q->dev, R, c->device, &sp))
-            sp = plan_sparse(q->dev, R, s.jacobi, c->device);
-        rt = sp.rt;
-        float* scr = nullptr;
-        if (sp.scratch_floats && (rc = get(sp.scratch_floats * sizeof(float), (void**)&scr))) return rc;
-        const size_t per = (size_t)sp.grid * n * rt;
-        if (!sp.onchip) { s.m_scratch = scr; scr += per; }
-        if (s.jacobi) s.m_next = scr;
-    }
-    const int32_t ntiles = (R + rt - 1) / rt;
-    int32_t* queue = nullptr;
-    if ((rc = get((size_t)ntiles * rt * sizeof(int32_t), (void**)&queue))) return rc;
-    MARS_CUDA(c, launch_queue_identity(queue, ntiles * rt, R, s.work_counter, st));
-    s.tile_rep = queue;
-    s.ntiles = ntiles;
-    s.rt = rt;
-    if (tc) {
-        q->tc.reset(new TcRun());
-        TcRun* run = q->tc.get();
-        const float t0_max = (float)std::max(p.t_max, 0.0);
-        if ((rc = tc_setup(c, q->dev, s, queue, p.t0 ? 1e6f * (float)p.c_step : t0_max,
-                           p.precision == MARS_FP8, st, get, run)))
-            return rc;
-        run->h_counters = pinned_view(q->pinned).counters;
-        sv->stream_jobs += 1;
-        if ((rc = tc_enqueue_batch(c, run, st))) return rc;
-        MARS_CUDA(c, cudaEventRecord(q->ev, st));
-        q->state = ReqState::TcRunning;
-        return MARS_OK;
-    }
-    sv->stream_jobs += 1;
-    if (q->dev.dense) {
-        MARS_CUDA(c, launch_dense(q->dev, s, dp, st));
-    } else if (sp.sell) {
-        MARS_CUDA(c, launch_sparse_sell(q->dev, s, sp, st));
-    } else {
-        MARS_CUDA(c, launch_sparse(q->dev, s, sp, st));
-    }
-    return serve_finish_enqueue(c, q);
-}
-
-void serve_mark_failed(mars_ctx* c, Serve* sv, ServeReq* q, int rc)
-{
-    q->rc = rc;
-    q->err = c->err;
-    q->state = ReqState::Failed;
-    serve_free_req(c, sv, q);
-}
-
-void serve_progress(mars_ctx* c)
-{
-    Serve* sv = serve_get(c);
-    // collect
-    bool ring_pending = false;
-    for (auto& kv : sv->reqs) {
-        ServeReq* q = kv.second.get();
-        if (q->state == ReqState::RingRunning) {
-            const int k = (int)q->ring_job;
-            if (*reinterpret_cast<volatile int32_t*>(sv->done + k)) {
-                const int rc = serve_copy_results(c, q);  // the kernel already selected the best
-                if (rc) serve_mark_failed(c, sv, q, rc);
-            } else {
-                ring_pending = true;
-            }
-            continue;
-        }
-        if (q->state != ReqState::TcRunning && q->state != ReqState::Finishing) continue;
-        const cudaError_t e = cudaEventQuery(q->ev);
-        if (e == cudaErrorNotReady) continue;
-        if (e != cudaSuccess) {
-            fail(c, MARS_EDEVICE, "CUDA error: %s", cudaGetErrorString(e));
-            serve_mark_failed(c, sv, q, MARS_EDEVICE);
-            continue;
-        }
-        if (q->state == ReqState::TcRunning) {
-            const int r = tc_after_batch(c, q->tc.get());
-            int rc = MARS_OK;
-            if (r < 0) {
-                rc = r;
-            } else if (r == 1) {
-                rc = tc_enqueue_batch(c, q->tc.get(), q->st);
-                if (!rc && cudaEventRecord(q->ev, q->st) != cudaSuccess) rc = MARS_EDEVICE;
-            } else {
-                rc = launch_tc_finalize(q->tc->t, q->dev, q->s, q->st) == cudaSuccess ? MARS_OK : MARS_EDEVICE;
-                if (!rc) rc = serve_finish_enqueue(c, q);
-            }
-            if (rc) serve_mark_failed(c, sv, q, rc);
-            continue;
-        }
-        // Finishing: results are in pinned memory
-        PinnedView v = pinned_view(q->pinned);
-        if (*v.status != kDevOk) {
-            fail(c, MARS_EDEVICE, "device status %d", *v.status);
-            serve_mark_failed(c, sv, q, MARS_EDEVICE);
-            continue;
-        }
-        q->state = ReqState::Done;
-        if (q->ring_job >= 0) {
-            sv->ring_refs -= 1;
-            q->ring_job = -1;
-        }
-        for (auto& b : q->bufs) dev_free_on(c, &b, q->st);
-        q->bufs.clear();
-        if (q->slot >= 0) {
-            sv->free_slots.push_back(q->slot);
-            sv->inflight -= 1;
-            q->slot = -1;
-        }
-    }
-    // a published job is always taken up: relaunch the serving kernel if it
-    // went idle and exited before the job's tail reached it
-    if (ring_pending) {
-        const int rc = serve_ring_ensure_kernel(c, sv);
-        if (rc) {
-            for (auto& kv : sv->reqs)
-                if (kv.second->state == ReqState::RingRunning) serve_mark_failed(c, sv, kv.second.get(), rc);
-        }
-    }
-    // reset the ring once its kernel has exited and no request reads a slot
-    if (sv->ring && sv->tail > 0 && sv->ring_refs == 0) {
-        const bool live = sv->kernel_live && cudaEventQuery(sv->ring_ev) == cudaErrorNotReady;
-        if (!live) {
-            sv->kernel_live = false;
-            if (cudaMemsetAsync(sv->ring, 0, sizeof(ServeRing), sv->pub_st) == cudaSuccess) {
-                std::memset(sv->done, 0, sizeof(int32_t) * kRingCap);
-                sv->tail = 0;
-            }
-        }
-    }
-    // admit, in arrival order
-    while (!sv->queue.empty() && !sv->free_slots.empty()) {
-        const int64_t id = sv->queue.front();
-        auto it = sv->reqs.find(id);
-        if (it == sv->reqs.end()) { sv->queue.pop_front(); continue; }
-        ServeReq* q = it->second.get();
-        Instance* in = find(c, q->inst);
-        if (!in) {
-            sv->queue.pop_front();
-            fail(c, MARS_ENOTFOUND, "instance %d was freed before its request ran", q->inst);
-            serve_mark_failed(c, sv, q, MARS_ENOTFOUND);
-            continue;
-        }
-        const size_t need = serve_footprint(in->dev, q->p, c->device);
-        if (c->budget && c->used + need > c->budget) {
-            if (sv->inflight == 0) {  // it will never fit
-                sv->queue.pop_front();
-                fail(c, MARS_ENOMEM, "request needs about %zu bytes; the HBM budget is %zu", need, c->budget);
-                serve_mark_failed(c, sv, q, MARS_ENOMEM);
-                continue;
-            }
-            break;  // wait for memory to free up
-        }
-        sv->queue.pop_front();
-        q->footprint = need;
-        const int rc = serve_launch(c, sv, q);
-        if (rc) serve_mark_failed(c, sv, q, rc);
-    }
-}
-
-void serve_release(mars_ctx* c)
-{
-    if (!c->serve) return;
-    Serve* sv = c->serve.get();
-    serve_ring_free(sv);
-    for (cudaStream_t st : sv->streams) cudaStreamSynchronize(st);
-    for (auto& kv : sv->reqs) serve_free_req(c, sv, kv.second.get());
-    sv->reqs.clear();
-    for (cudaStream_t st : sv->streams) cudaStreamDestroy(st);
-    sv->streams.clear();
-    c->serve.reset();
 }
 
 // Accessors for mars_noalloc.cu.
@@ -2219,108 +1190,6 @@ int mars_autotune(mars_ctx* c, int32_t id, const mars_params* p, int32_t repeats
     if (best)
         *best = mars_shape{win.sell_rt, win.sell_threads, win.sell_smem_table, win.tc_rpw, win.tc_overlap, win.tc_pair};
     if (seconds) *seconds = best_t;
-    return MARS_OK;
-}
-
-int mars_serve_limits(mars_ctx* c, int32_t max_inflight)
-{
-    if (!c || max_inflight < 1 || max_inflight > 64) return MARS_EINVAL;
-    DeviceGuard g(c->device);
-    Serve* sv = serve_get(c);
-    sv->max_inflight = std::max(max_inflight, (int32_t)sv->inflight);
-    serve_get(c);
-    return MARS_OK;
-}
-
-int mars_submit(mars_ctx* c, int32_t id, const mars_params* p, int64_t* req)
-{
-    if (!c || !p || !req) return MARS_EINVAL;
-    Instance* in = find(c, id);
-    if (!in) return fail(c, MARS_ENOTFOUND, "unknown instance %d", id);
-    if (p->replicas < 1 || !std::isfinite(p->t_min) || !std::isfinite(p->t_max) || p->t_min > p->t_max ||
-        !(p->c_step > 0.0) || !schedule_ok(p) || levels_bound(p, p->t_max) > kMaxLevels ||
-        !(p->d_min >= 0.0) ||
-        p->k_max < 1 || p->fixed_sweeps < 0 ||
-        (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI))
-        return fail(c, MARS_EINVAL, "bad parameters");
-    const bool tc = p->precision == MARS_BF16 || p->precision == MARS_FP8;
-    if (p->precision != MARS_FP32 && !(tc && in->dev.dense && p->update == MARS_UPDATE_GS))
-        return fail(c, MARS_EINVAL, "precision %d is not available for this instance", p->precision);
-    if (p->precision == MARS_FP8 && !in->dev.J8)
-        return fail(c, MARS_EINVAL, "FP8 needs integer couplings exactly representable in E4M3");
-    if ((p->m0 || p->t0) && !(p->flags & MARS_DEVICE_PTR))
-        return fail(c, MARS_EINVAL, "served requests take m0/t0 as device pointers");
-    if (tc && p->t0) return fail(c, MARS_EINVAL, "served tensor-core requests draw t0 themselves");
-    DeviceGuard g(c->device);
-    Serve* sv = serve_get(c);
-    auto q = std::make_unique<ServeReq>();
-    q->id = sv->next_id++;
-    q->inst = id;
-    q->p = *p;
-    *req = q->id;
-    sv->queue.push_back(q->id);
-    sv->reqs[q->id] = std::move(q);
-    serve_progress(c);
-    return MARS_OK;
-}
-
-int mars_poll(mars_ctx* c, int64_t req, int8_t* best_spins, mars_result* result)
-{
-    if (!c) return MARS_EINVAL;
-    DeviceGuard g(c->device);
-    serve_progress(c);
-    Serve* sv = c->serve.get();
-    auto it = sv ? sv->reqs.find(req) : std::map<int64_t, std::unique_ptr<ServeReq>>::iterator();
-    if (!sv || it == sv->reqs.end()) return fail(c, MARS_ENOTFOUND, "unknown request %lld", (long long)req);
-    ServeReq* q = it->second.get();
-    if (q->state == ReqState::Failed) {
-        const int rc = q->rc;
-        c->err = q->err;
-        sv->reqs.erase(it);
-        return rc;
-    }
-    if (q->state != ReqState::Done) return MARS_EAGAIN;
-    PinnedView v = pinned_view(q->pinned);
-    if (best_spins) std::memcpy(best_spins, v.best, q->dev.n);
-    if (result) {
-        const DevResult& h = *v.res;
-        std::memset(result, 0, sizeof *result);
-        result->best_energy = h.best_energy;
-        result->best_energy_i64 = h.best_energy_i64;
-        result->best_cut = (q->total_weight - h.best_energy) / 2.0;
-        result->best_replica = h.best_replica;
-        result->hits = h.hits;
-        result->mean_energy = h.sum_energy / q->p.replicas;
-        result->sweeps = h.sweeps;
-        result->spin_updates = h.sweeps * (int64_t)q->dev.n;
-        result->levels = h.levels;
-        result->capped_levels = h.capped;
-        result->integer = q->dev.integer;
-        result->energy_err_bound = q->err_bound;
-        result->status = MARS_OK;
-    }
-    serve_free_req(c, sv, q);
-    sv->reqs.erase(it);
-    return MARS_OK;
-}
-
-int mars_serve_status(mars_ctx* c, int32_t* queued, int32_t* running)
-{
-    if (!c) return MARS_EINVAL;
-    DeviceGuard g(c->device);
-    serve_progress(c);
-    Serve* sv = c->serve.get();
-    if (queued) *queued = sv ? (int32_t)sv->queue.size() : 0;
-    if (running) *running = sv ? sv->inflight : 0;
-    return MARS_OK;
-}
-
-int mars_serve_counters(mars_ctx* c, int64_t* ring_jobs, int64_t* stream_jobs)
-{
-    if (!c) return MARS_EINVAL;
-    const Serve* sv = c->serve.get();
-    if (ring_jobs) *ring_jobs = sv ? sv->ring_jobs : 0;
-    if (stream_jobs) *stream_jobs = sv ? sv->stream_jobs : 0;
     return MARS_OK;
 }
 
