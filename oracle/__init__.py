@@ -87,6 +87,13 @@ def _load():
         _lib.or_mars_solve.argtypes = [P, P, ctypes.c_int32, P, P, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, P, ctypes.c_int32, P, P, P, P]
+        _lib.or_nmfa_normal.restype = ctypes.c_double
+        _lib.or_nmfa_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.c_uint32]
+        _lib.or_nmfa_solve.restype = ctypes.c_int
+        _lib.or_nmfa_solve.argtypes = [P, ctypes.c_int32, P, P, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, P,
+                                       ctypes.c_int32, P, P, P, P]
         _lib.or_philox4x32_10.restype = None
         _lib.or_philox4x32_10.argtypes = [P, P, P]
         _lib.or_draw_replicas.restype = None
@@ -224,6 +231,37 @@ def mars_solve(inst: Instance, m0, t0, *, c_step=1.0, d_min=1e-4, k_max=1000, fi
     stats = {k: np.array([getattr(st[r], k) for r in range(R)])
              for k in ("sweeps", "levels", "capped_levels", "final_T", "last_d")}
     return {"m": m_out, "sigma": sig, "energy": en, **stats}
+
+
+def nmfa_solve(inst: Instance, m0, t0, *, c_step=1.0, alpha=0.5, sigma=0.0, seed=0, stream=0,
+               nthreads=1, want_m=True, geometric=None, t_floor=0.0):
+    """Noisy mean-field annealing (Section 2) for every replica: synchronous
+    normalised-field updates with Gaussian noise and alpha-mixing, one
+    iteration per temperature level (see mars_oracle.h)."""
+    m0 = np.ascontiguousarray(m0, dtype=np.float32)
+    t0 = np.ascontiguousarray(t0, dtype=np.float32)
+    R = t0.shape[0]
+    if m0.shape != (R, inst.n):
+        raise ValueError("m0 must have shape (R, n)")
+    m_out = np.zeros((R, inst.n), dtype=np.float64) if want_m else None
+    sig = np.zeros((R, inst.n), dtype=np.int8)
+    en = np.zeros(R, dtype=np.float64)
+    st = (ReplicaStats * max(R, 1))()
+    c = inst._c()
+    sch = Schedule(1 if geometric else 0, float(geometric or 0.0), float(t_floor), 0)
+    rc = _load().or_nmfa_solve(ctypes.byref(c), R, _ptr(m0), _ptr(t0), float(c_step), float(alpha),
+                               float(sigma), int(seed) & (2**64 - 1), int(stream), ctypes.byref(sch),
+                               int(nthreads), _ptr(m_out), _ptr(sig), _ptr(en), ctypes.addressof(st))
+    if rc != 0:
+        raise ValueError("oracle rejected the inputs")
+    stats = {k: np.array([getattr(st[r], k) for r in range(R)])
+             for k in ("sweeps", "levels", "capped_levels", "final_T", "last_d")}
+    return {"m": m_out, "sigma": sig, "energy": en, **stats}
+
+
+def nmfa_normal(seed: int, stream: int, r: int, k: int, i: int) -> float:
+    """NMFA's standard normal for (replica r, iteration k, spin i) (see mars_oracle.h)."""
+    return _load().or_nmfa_normal(int(seed) & (2**64 - 1), int(stream), int(r), int(k), int(i))
 
 
 def philox4x32_10(ctr, key):

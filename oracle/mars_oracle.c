@@ -423,3 +423,109 @@ void or_draw_replicas(uint64_t seed, uint32_t stream, int32_t r0, int32_t R, int
         if (t0) t0[q] = (float)t;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Noisy mean-field annealing (Section 2)                                    */
+/* ------------------------------------------------------------------------ */
+
+double or_nmfa_normal(uint64_t seed, uint32_t stream, uint32_t r, uint32_t k, uint32_t i)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const uint32_t ctr[4] = {i >> 1, r, 2u + k, stream};
+    uint32_t w[4];
+    or_philox4x32_10(ctr, key, w);
+    const double u1 = (double)((w[0] >> 8) + 1u) * 0x1p-24;
+    const double u2 = (double)(w[1] >> 8) * 0x1p-24;
+    const double rho = sqrt(-2.0 * log(u1));
+    const double two_pi = 6.283185307179586476925286766559;
+    return (i & 1u) ? rho * sin(two_pi * u2) : rho * cos(two_pi * u2);
+}
+
+/* sum_{j != i} J_ij^2 + h_i^2, summed in column order, then h added */
+static double field_norm2(const or_instance* in, int32_t i)
+{
+    double q = 0.0;
+    if (in->J) {
+        const double* row = in->J + (int64_t)i * in->n;
+        for (int32_t j = 0; j < in->n; ++j)
+            if (j != i) q += row[j] * row[j];
+    } else {
+        for (int32_t e = in->row_ptr[i]; e < in->row_ptr[i + 1]; ++e)
+            if (in->col[e] != i) q += in->val[e] * in->val[e];
+    }
+    if (in->h) q += in->h[i] * in->h[i];
+    return q;
+}
+
+int or_nmfa_replica(const or_instance* in, double* m, double t0, double c_step, double alpha,
+                    double sigma, uint64_t seed, uint32_t stream, uint32_t r, double* scratch,
+                    const or_schedule* sch, or_replica_stats* st)
+{
+    if (!in || !m || !scratch || in->n < 0 || !(c_step > 0) || !(alpha >= 0.0 && alpha <= 1.0) ||
+        !(sigma >= 0.0))
+        return -1;
+    const int geometric = sch && sch->geometric;
+    if (geometric && !(sch->ratio > 0.0 && sch->ratio < 1.0 && sch->t_floor > 0.0)) return -1;
+    const int32_t n = in->n;
+    or_replica_stats s = {0, 0, 0, 0.0, 0.0};
+    double T = t0;
+    uint32_t k = 0;
+    for (;;) {
+        T = geometric ? T * sch->ratio : T - c_step;
+        if (!(T > (geometric ? sch->t_floor : 0.0))) break;
+        s.levels += 1;
+        s.final_T = T;
+        /* every spin's new value from the same state s */
+        for (int32_t i = 0; i < n; ++i) {
+            const double norm = sqrt(field_norm2(in, i));
+            const double field = or_local_field(in, m, i);
+            double phi = norm > 0.0 ? field / norm : 0.0;
+            if (sigma > 0.0) phi += sigma * or_nmfa_normal(seed, stream, r, k, (uint32_t)i);
+            scratch[i] = -tanh(phi / T);
+        }
+        double d = 0.0;
+        for (int32_t i = 0; i < n; ++i) {
+            const double v = alpha * scratch[i] + (1.0 - alpha) * m[i];
+            const double diff = fabs(v - m[i]);
+            if (diff > d) d = diff;
+            m[i] = v;
+        }
+        s.sweeps += 1;
+        s.last_d = d;
+        k += 1;
+    }
+    if (st) *st = s;
+    return 0;
+}
+
+int or_nmfa_solve(const or_instance* in, int32_t R, const float* m0, const float* t0, double c_step,
+                  double alpha, double sigma, uint64_t seed, uint32_t stream, const or_schedule* sch,
+                  int32_t nthreads, double* m_out, int8_t* sigma_out, double* energy_out,
+                  or_replica_stats* stats_out)
+{
+    if (!in || R < 0 || !m0 || !t0) return -1;
+    const int32_t n = in->n;
+    int bad = 0;
+    if (nthreads < 1) nthreads = 1;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1) reduction(| : bad)
+#endif
+    for (int32_t r = 0; r < R; ++r) {
+        double* m = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 2);
+        int8_t* sg = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
+        if (!m || !sg) { bad |= 1; free(m); free(sg); continue; }
+        for (int32_t i = 0; i < n; ++i) m[i] = (double)m0[(int64_t)r * n + i];
+        or_replica_stats st;
+        if (or_nmfa_replica(in, m, (double)t0[r], c_step, alpha, sigma, seed, stream, (uint32_t)r,
+                            m + n, sch, &st) != 0)
+            bad |= 1;
+        for (int32_t i = 0; i < n; ++i) sg[i] = m[i] >= 0.0 ? 1 : -1;
+        if (m_out) memcpy(m_out + (int64_t)r * n, m, sizeof(double) * (size_t)n);
+        if (sigma_out) memcpy(sigma_out + (int64_t)r * n, sg, (size_t)n);
+        if (energy_out) energy_out[r] = or_energy(in, sg);
+        if (stats_out) stats_out[r] = st;
+        free(m);
+        free(sg);
+    }
+    return bad ? -1 : 0;
+}

@@ -110,6 +110,42 @@ double or_exact_sum(const double* x, int64_t count);
 int or_bruteforce(const or_instance* in, double tol, double* e_min, int8_t* sigma_min,
                   int64_t* n_min);
 
+/*
+ * Noisy mean-field annealing (NMFA), the alternative method the paper surveys
+ * in Section 2 (its "normalised mean-field terms plus Gaussian noise" and the
+ * convex combination). One iteration computes, for every spin from the same
+ * state s (synchronously),
+ *     Phi_i  = (h_i + sum_{j != i} J_ij s_j) / sqrt(h_i^2 + sum_{j != i} J_ij^2) + sigma xi_i,
+ *     shat_i = -tanh(Phi_i / T),
+ * then sets s_i <- alpha shat_i + (1 - alpha) s_i for every i and lowers T
+ * by the schedule: one iteration per temperature level, levels while T > 0
+ * (or T > t_floor when geometric; the quench flag is not used). A spin with
+ * no coupling and no field has Phi_i = sigma xi_i. xi_i ~ N(0, 1) is drawn by
+ * or_nmfa_normal for (replica r, iteration k counted from 0 over all levels,
+ * spin i). Replica stats count one sweep per level; capped_levels is 0.
+ */
+
+/*
+ * The standard normal of NMFA's noise, restated from its definition: Philox
+ * with key (seed low word, seed high word) at counter (i/2, r, 2 + k, stream)
+ * gives words w0, w1; u1 = ((w0 >> 8) + 1) 2^-24 in (0, 1], u2 = (w1 >> 8)
+ * 2^-24; the Box-Muller transform (Box and Muller, 1958) gives
+ * sqrt(-2 ln u1) cos(2 pi u2) for even i and sqrt(-2 ln u1) sin(2 pi u2) for
+ * odd i, in double.
+ */
+double or_nmfa_normal(uint64_t seed, uint32_t stream, uint32_t r, uint32_t k, uint32_t i);
+
+int or_nmfa_replica(const or_instance* in, double* m, double t0, double c_step, double alpha,
+                    double sigma, uint64_t seed, uint32_t stream, uint32_t r, double* scratch,
+                    const or_schedule* sch, or_replica_stats* st);
+
+/* R replicas of NMFA; replica q uses noise index r = q and the outputs of
+ * or_mars_solve. scratch is internal. Returns 0, or -1 on bad input. */
+int or_nmfa_solve(const or_instance* in, int32_t R, const float* m0, const float* t0, double c_step,
+                  double alpha, double sigma, uint64_t seed, uint32_t stream, const or_schedule* sch,
+                  int32_t nthreads, double* m_out, int8_t* sigma_out, double* energy_out,
+                  or_replica_stats* stats_out);
+
 /* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 

@@ -495,3 +495,122 @@ def test_quench_ends_in_single_flip_local_minimum(seed):
             flip = sig.copy()
             flip[i] = -flip[i]
             assert O.energy(inst, flip) >= e
+
+
+# --------------------------------------------------------------------------
+# Noisy mean-field annealing (Section 2): the alternative epilogue
+# --------------------------------------------------------------------------
+
+def _kat_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for ln in f:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            v = [int(x, 16) for x in ln.split()]
+            rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+def test_nmfa_normal_box_muller_of_published_philox_words():
+    """The noise is the Box-Muller transform of the first two words of
+    Philox at counter (i/2, r, 2 + k, stream) under key (seed): choose the
+    arguments so that counter and key are a published known-answer vector."""
+    for ctr, key, out in _kat_rows():
+        i0 = 2 * ctr[0]
+        if i0 >= 2**32:
+            continue  # the spin index is 32-bit: this counter word is out of reach
+        seed = key[0] | (key[1] << 32)
+        k = (ctr[2] - 2) % 2**32
+        u1 = ((out[0] >> 8) + 1) * 2.0**-24
+        u2 = (out[1] >> 8) * 2.0**-24
+        rho = math.sqrt(-2.0 * math.log(u1))
+        assert O.nmfa_normal(seed, ctr[3], ctr[1], k, i0) == pytest.approx(
+            rho * math.cos(2 * math.pi * u2), rel=1e-15, abs=1e-15)
+        assert O.nmfa_normal(seed, ctr[3], ctr[1], k, i0 + 1) == pytest.approx(
+            rho * math.sin(2 * math.pi * u2), rel=1e-15, abs=1e-15)
+
+
+def test_nmfa_normal_is_standard_normal():
+    from scipy import stats
+    x = np.array([O.nmfa_normal(7, 1, r, k, i) for r in range(5) for k in range(40) for i in range(500)])
+    assert abs(x.mean()) < 4.0 / math.sqrt(len(x))
+    assert abs(x.var() - 1.0) < 0.03
+    assert stats.kstest(x, "norm").pvalue > 1e-3
+    # the two normals of one Box-Muller pair are uncorrelated
+    ev = np.array([O.nmfa_normal(3, 0, 0, 0, 2 * q) for q in range(20000)])
+    od = np.array([O.nmfa_normal(3, 0, 0, 0, 2 * q + 1) for q in range(20000)])
+    assert abs(np.corrcoef(ev, od)[0, 1]) < 0.03
+
+
+def test_nmfa_zero_mixing_moves_nothing():
+    J = I.sk_pm1(24, 3)
+    m0, t0 = I.replica_inputs(4, 24, 2.0, 9.0, 4)
+    r = O.nmfa_solve(O.Instance.dense(J), m0, t0, alpha=0.0, sigma=0.7, seed=5)
+    assert np.array_equal(r["m"], m0.astype(np.float64))
+
+
+def test_nmfa_fields_only_closed_form_with_mixing():
+    """J = 0: the normalised field is h_i / |h_i| = sign(h_i), so each
+    iteration at T_k sets s <- alpha (-tanh(sign(h)/T_k)) + (1 - alpha) s."""
+    n = 6
+    h = np.array([0.3, -2.0, 5.0, -0.01, 1.0, 0.0])
+    inst = O.Instance.dense(np.zeros((n, n)), h)
+    m0 = np.linspace(-0.9, 0.8, n).astype(np.float32)[None, :]
+    t0 = np.array([3.75], dtype=np.float32)
+    a = 0.3
+    r = O.nmfa_solve(inst, m0, t0, c_step=1.0, alpha=a, sigma=0.0)
+    s = m0[0].astype(np.float64)
+    for T in (2.75, 1.75, 0.75):
+        s = a * (-np.tanh(np.sign(h) / T)) + (1 - a) * s
+    np.testing.assert_allclose(r["m"][0], s, rtol=0, atol=1e-15)
+    assert r["levels"][0] == 3 and r["sweeps"][0] == 3 and r["capped_levels"][0] == 0
+
+
+def test_nmfa_field_is_normalised():
+    """Scaling J and h by a > 0 leaves every normalised field, and therefore
+    the whole trajectory, unchanged (noise included)."""
+    J = I.sk_gauss(40, 2)
+    h = np.random.default_rng(3).normal(size=40)
+    m0, t0 = I.replica_inputs(3, 40, 0.5, 3.0, 9)
+    kw = dict(c_step=0.25, alpha=0.6, sigma=0.2, seed=11)
+    a = O.nmfa_solve(O.Instance.dense(J, h), m0, t0, **kw)
+    b = O.nmfa_solve(O.Instance.dense(37.5 * J, 37.5 * h), m0, t0, **kw)
+    np.testing.assert_allclose(a["m"], b["m"], rtol=0, atol=1e-12)
+    assert np.abs(a["m"] - m0).max() > 0.1  # the trajectory did move
+
+
+def test_nmfa_without_noise_is_synchronous_mars_on_regular_rows():
+    """With sigma = 0 and alpha = 1, on an instance whose rows all have the
+    same norm c (h = 0, +-1 couplings, every spin of the same degree), an
+    iteration at T is a synchronous MARS sweep at temperature c T; one
+    iteration per level. So NMFA(t0, C_step) equals the oracle's synchronous
+    MARS with one sweep per level from c t0 in steps of c C_step."""
+    csr = I.ea_lattice(6, 2, 1)  # degree 4: c = 2
+    inst = O.Instance.csr(csr)
+    m0, t0 = I.replica_inputs(4, csr.n, 1.0, 3.0, 2)
+    a = O.nmfa_solve(inst, m0, t0, c_step=0.5, alpha=1.0, sigma=0.0)
+    b = O.mars_solve(inst, m0, (2.0 * t0).astype(np.float32), c_step=1.0, fixed_sweeps=1,
+                     update=O.UPDATE_JACOBI)
+    np.testing.assert_allclose(a["m"], b["m"], rtol=0, atol=1e-12)
+    assert np.array_equal(a["levels"], b["levels"]) and np.array_equal(a["sweeps"], b["levels"])
+
+
+def test_nmfa_noise_enters_with_scale_sigma():
+    """J = 0, h = 0, alpha = 1: one iteration gives s_i = -tanh(sigma xi_i / T),
+    so T atanh(-s_i) / sigma over many spins is standard normal."""
+    from scipy import stats
+    n = 4000
+    inst = O.Instance.csr((np.zeros(n + 1, np.int32), np.zeros(0, np.int32), np.zeros(0)))
+    m0 = np.zeros((2, n), dtype=np.float32)
+    t0 = np.array([1.5, 1.5], dtype=np.float32)  # one level at T = 0.5
+    r = O.nmfa_solve(inst, m0, t0, c_step=1.0, alpha=1.0, sigma=0.3, seed=4)
+    z = (0.5 * np.arctanh(-r["m"]) / 0.3).ravel()
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert not np.array_equal(r["m"][0], r["m"][1])  # each replica draws its own noise
+    # the last iteration's noise alone decides s, and a new iteration draws anew
+    t2 = np.array([2.5, 2.5], dtype=np.float32)  # levels at T = 1.5, then 0.5
+    r2 = O.nmfa_solve(inst, m0, t2, c_step=1.0, alpha=1.0, sigma=0.3, seed=4)
+    z2 = (0.5 * np.arctanh(-r2["m"]) / 0.3).ravel()
+    assert stats.kstest(z2, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(z, z2)[0, 1]) < 0.06
