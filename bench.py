@@ -451,7 +451,12 @@ def run_mars(args, world, rank, local):
     stream = ctx.torch_stream  # the stream every library call is ordered on
 
     shape = None
-    if not args.no_autotune:
+    if wl.J is not None:
+        # dense tensor-core solves: the library re-plans every batch of sweeps
+        # for the replicas still active, which a fixed shape tuned on a short
+        # all-active run would switch off
+        wl.config = dict(wl.config, launch_shape_by="library plan per batch of sweeps (active replicas)")
+    elif not args.no_autotune:
         shape, _ = wl.autotune(ctx, inst)
         wl.config = dict(wl.config, launch_shape=shape, launch_shape_by="mars_autotune")
     for w in range(max(args.warmup, 0)):

@@ -170,8 +170,27 @@ int mars_instance_order(mars_ctx* ctx, int32_t inst, int32_t* order_out);
  *                field), until no spin changes or k_max sweeps (a labelled
  *                variant: Algorithm 1's last decrement taken to T = 0); it
  *                counts as a level and ignores fixed_sweeps
+ *  method        MARS_METHOD_MARS (default: Algorithm 1) or MARS_METHOD_NMFA,
+ *                noisy mean-field annealing as Section 2 surveys it: every
+ *                iteration computes, synchronously for all spins,
+ *                Phi_i = (h_i + sum_j J_ij s_j) / sqrt(h_i^2 + sum_j J_ij^2)
+ *                + nmfa_sigma xi_i and shat_i = -tanh(Phi_i / T), then sets
+ *                s_i <- nmfa_alpha shat_i + (1 - nmfa_alpha) s_i and lowers T
+ *                by the schedule: one iteration per level (update, d_min,
+ *                k_max and fixed_sweeps are not used; quench is refused).
+ *                xi_i ~ N(0, 1) is counter-based: Philox (key = seed words)
+ *                at counter (i/2, r, 2 + k, stream) gives words w0, w1 for
+ *                replica r, iteration k (from 0 over all levels), original
+ *                spin label i; u1 = ((w0 >> 8) + 1) 2^-24, u2 = (w1 >> 8)
+ *                2^-24 and the Box-Muller transform gives sqrt(-2 ln u1)
+ *                cos(2 pi u2) for even i, sqrt(-2 ln u1) sin(2 pi u2) for odd
+ *                i. A spin without coupling or field has Phi_i = sigma xi_i.
+ *                FP32 precision only; dense and CSR instances.
+ *  nmfa_alpha    mixing weight in [0, 1] (NMFA)
+ *  nmfa_sigma    noise standard deviation >= 0 (NMFA)
  */
 typedef enum { MARS_SCHEDULE_LINEAR = 0, MARS_SCHEDULE_GEOMETRIC = 1 } mars_schedule;
+typedef enum { MARS_METHOD_MARS = 0, MARS_METHOD_NMFA = 1 } mars_method;
 typedef struct {
     int32_t replicas;
     double t_min, t_max, c_step, d_min;
@@ -187,9 +206,12 @@ typedef struct {
     int32_t schedule;
     double cool_ratio, t_floor;
     int32_t quench;
+    int32_t method;
+    double nmfa_alpha, nmfa_sigma;
 } mars_params;
 
-/* Fill p with the paper's defaults: c_step 1, d_min 1e-4, k_max 1000, GS, FP32. */
+/* Fill p with the paper's defaults: c_step 1, d_min 1e-4, k_max 1000, GS, FP32,
+ * method MARS (nmfa_alpha 0.5, nmfa_sigma 0). */
 void mars_params_default(mars_params* p);
 
 /*

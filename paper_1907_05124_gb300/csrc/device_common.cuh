@@ -50,6 +50,34 @@ __device__ __forceinline__ float draw_t0(uint64_t seed, uint32_t stream, uint32_
     return __double2float_rn(__dadd_rn(t_min, prod));
 }
 
+// Noisy mean-field annealing's standard normal for replica r, iteration k and
+// spin i (caller label): Philox(i/2, r, 2 + k, stream) gives words w0, w1;
+// u1 = ((w0 >> 8) + 1) 2^-24 in (0, 1], u2 = (w1 >> 8) 2^-24, and the
+// Box-Muller transform (Box and Muller, 1958) gives sqrt(-2 ln u1) times
+// cos(2 pi u2) (even i) or sin(2 pi u2) (odd i), in FP32 with CUDA's
+// accurate logf, sqrtf and sincospif.
+__device__ __forceinline__ float nmfa_normal(uint64_t seed, uint32_t stream, uint32_t r, uint32_t k,
+                                             uint32_t i)
+{
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint4 w = philox4x32_10(make_uint4(i >> 1, r, 2u + k, stream), key);
+    const float u1 = (float)((w.x >> 8) + 1u) * 0x1p-24f;
+    const float u2 = (float)(w.y >> 8) * 0x1p-24f;
+    const float rho = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    return rho * ((i & 1u) ? sn : cs);
+}
+
+// One NMFA update of a spin from its local field phi = h_i + sum_j J_ij s_j:
+// alpha (-tanh((phi inv_norm + sigma xi) invT)) + (1 - alpha) s_old.
+__device__ __forceinline__ float nmfa_update(float phi, float inv_norm, float xi, float sigma,
+                                             float invT, float alpha, float s_old)
+{
+    const float shat = -tanhf(fmaf(sigma, xi, phi * inv_norm) * invT);
+    return fmaf(alpha, shat - s_old, s_old);
+}
+
 template <typename T>
 __device__ __forceinline__ T shfl_xor(T v, int mask)
 {

@@ -149,6 +149,28 @@ struct Level {
     }
 };
 
+// Noisy mean-field annealing after a synchronous sweep that left the raw
+// field Phi_a = sum_b J_ab s_b + h_a of every spin in phi[a]: each lane updates
+// its spins a = lane, lane + 32, ... with the normalised field and its noise
+// (iteration lv.sweeps of replica r), s_a <- alpha shat_a + (1 - alpha) s_a.
+// Returns the sweep's largest change (every lane).
+__device__ float nmfa_finish_sweep(const DevInstance& in, const DevSolve& s, int r, const Level& lv,
+                                   float* m, const float* phi, int lane)
+{
+    float d = 0.f;
+    for (int a = lane; a < in.n; a += 32) {
+        const float xi = s.nmfa_sigma > 0.f
+                             ? nmfa_normal(s.seed, s.stream, (uint32_t)r, (uint32_t)lv.sweeps,
+                                           (uint32_t)__ldg(in.new2old + a))
+                             : 0.f;
+        const float v = nmfa_update(phi[a], __ldg(in.inv_norm + a), xi, s.nmfa_sigma, lv.invT,
+                                    s.nmfa_alpha, m[a]);
+        d = fmaxf(d, fabsf(v - m[a]));
+        m[a] = v;
+    }
+    return warp_reduce_strided<1>(d, MaxOp());
+}
+
 __device__ __forceinline__ void init_m(const DevInstance& in, const DevSolve& s, int r, float* m,
                                        int lane)
 {
@@ -242,14 +264,19 @@ __global__ void __launch_bounds__(kDenseWarps * 32) dense_descent_kernel(DevInst
             prefetch_row_l1(in.Jf + (size_t)(a + 1 < n ? a + 1 : 0) * n, n, lane);
             const float p = row_field<true>(in.Jf + (size_t)a * n, m, n, n4, lane,
                                             in.h && lane == 0 ? __ldg(in.h + a) : 0.f);
-            const float sn = -tanhf(p * lv.invT);
-            d = fmaxf(d, fabsf(sn - m[a]));
+            // NMFA keeps the raw field; its update follows the sweep
+            const float sn = JACOBI && s.nmfa ? p : -tanhf(p * lv.invT);
+            if (!(JACOBI && s.nmfa)) d = fmaxf(d, fabsf(sn - m[a]));
             __syncwarp();
             if (lane == 0) mn[a] = sn;
             __syncwarp();
         }
         if (JACOBI) {
-            for (int a = lane; a < n; a += 32) m[a] = mn[a];
+            if (s.nmfa) {
+                d = nmfa_finish_sweep(in, s, r, lv, m, mn, lane);
+            } else {
+                for (int a = lane; a < n; a += 32) m[a] = mn[a];
+            }
             __syncwarp();
         }
         lv.after_sweep(s, d);
@@ -331,8 +358,9 @@ __global__ void __launch_bounds__(kDenseWarps * 32) dense_staged_kernel(DevInsta
             if (lv.act) {
                 const float p = row_field<false>(rows + (size_t)st * n, m, n, n4, lane,
                                                  in.h && lane == 0 ? __ldg(in.h + a) : 0.f);
-                const float sn = -tanhf(p * lv.invT);
-                d = fmaxf(d, fabsf(sn - m[a]));
+                // NMFA keeps the raw field; its update follows the sweep
+                const float sn = JACOBI && s.nmfa ? p : -tanhf(p * lv.invT);
+                if (!(JACOBI && s.nmfa)) d = fmaxf(d, fabsf(sn - m[a]));
                 __syncwarp();
                 if (lane == 0) mn[a] = sn;
             }
@@ -349,7 +377,11 @@ __global__ void __launch_bounds__(kDenseWarps * 32) dense_staged_kernel(DevInsta
             }
         }
         if (JACOBI && lv.act) {
-            for (int a = lane; a < n; a += 32) m[a] = mn[a];
+            if (s.nmfa) {
+                d = nmfa_finish_sweep(in, s, r, lv, m, mn, lane);
+            } else {
+                for (int a = lane; a < n; a += 32) m[a] = mn[a];
+            }
             __syncwarp();
         }
         if (lv.act) lv.after_sweep(s, d);

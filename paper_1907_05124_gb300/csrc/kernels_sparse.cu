@@ -101,7 +101,20 @@ __global__ void __launch_bounds__(kThreads) sparse_descent_kernel(DevInstance in
                         for (int e = e0; e < e1; ++e)
                             phi = fmaf(__ldg(in.val + e), m[__ldg(in.col + e) * RT + k], phi);
                         if (in.h) phi += __ldg(in.h + i);
-                        const float sn = -tanhf(phi * invT);
+                        float sn;
+                        if (JACOBI && s.nmfa) {
+                            // noisy mean-field annealing: normalised field plus
+                            // noise for iteration s_sweeps[k], then alpha-mixing
+                            const float xi = s.nmfa_sigma > 0.f
+                                                 ? nmfa_normal(s.seed, s.stream, (uint32_t)r,
+                                                               (uint32_t)s_sweeps[k],
+                                                               (uint32_t)__ldg(in.new2old + i))
+                                                 : 0.f;
+                            sn = nmfa_update(phi, __ldg(in.inv_norm + i), xi, s.nmfa_sigma, invT,
+                                             s.nmfa_alpha, m[idx]);
+                        } else {
+                            sn = -tanhf(phi * invT);
+                        }
                         dloc = fmaxf(dloc, fabsf(sn - m[idx]));
                         if (JACOBI) mnext[idx] = sn; else m[idx] = sn;
                     }

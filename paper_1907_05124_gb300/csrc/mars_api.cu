@@ -44,6 +44,27 @@ bool schedule_ok(const mars_params* p)
            p->t_floor > 0.0 && std::isfinite(p->t_floor);
 }
 
+const char* method_error(const mars_params* p)
+{
+    if (p->method == MARS_METHOD_MARS) return nullptr;
+    if (p->method != MARS_METHOD_NMFA) return "unknown method";
+    if (p->precision != MARS_FP32) return "NMFA runs with FP32 local fields only";
+    if (p->quench) return "NMFA has no quench level";
+    if (!(p->nmfa_alpha >= 0.0 && p->nmfa_alpha <= 1.0)) return "NMFA needs 0 <= nmfa_alpha <= 1";
+    if (!(p->nmfa_sigma >= 0.0) || !std::isfinite(p->nmfa_sigma)) return "NMFA needs a finite nmfa_sigma >= 0";
+    return nullptr;
+}
+
+void set_method(DevSolve& s, const mars_params* p)
+{
+    if (p->method != MARS_METHOD_NMFA) return;
+    s.nmfa = 1;
+    s.jacobi = 1;        // every spin's update from the same state
+    s.fixed_sweeps = 1;  // one iteration per temperature level
+    s.nmfa_alpha = (float)p->nmfa_alpha;
+    s.nmfa_sigma = (float)p->nmfa_sigma;
+}
+
 
 int env_flag(const char* name, int dflt)
 {
@@ -350,6 +371,9 @@ void mars_params_default(mars_params* p)
     p->k_max = 1000;
     p->update = MARS_UPDATE_GS;
     p->precision = MARS_FP32;
+    p->method = MARS_METHOD_MARS;
+    p->nmfa_alpha = 0.5;
+    p->nmfa_sigma = 0.0;
 }
 
 int mars_instance_dense(mars_ctx* c, int32_t n, const void* J, int32_t jt, const double* h,
@@ -461,6 +485,20 @@ int mars_instance_dense(mars_ctx* c, int32_t n, const void* J, int32_t jt, const
     if ((rc = upload(c, in.get(), hf, &d.h))) return rc;
     if ((rc = upload(c, in.get(), hd, &d.h_f64))) return rc;
     if ((rc = upload(c, in.get(), o, &d.new2old))) return rc;
+    {
+        // NMFA's field normalisation, 1 / sqrt(h_a^2 + sum_b J_ab^2), in FP64
+        std::vector<float> inv(n);
+        for (int32_t a = 0; a < n; ++a) {
+            double q = 0.0;
+            for (int32_t b = 0; b < n; ++b) {
+                const double v = Jh[(size_t)o[a] * n + o[b]];
+                q += v * v;
+            }
+            if (!hh.empty()) q += hh[o[a]] * hh[o[a]];
+            inv[a] = q > 0.0 ? (float)(1.0 / std::sqrt(q)) : 0.f;
+        }
+        if ((rc = upload(c, in.get(), inv, &d.inv_norm))) return rc;
+    }
     MARS_CUDA(c, cudaStreamSynchronize(c->stream));
     guard.done = true;
     in->info.n = n;
@@ -684,6 +722,17 @@ int mars_instance_csr(mars_ctx* c, int32_t n, int64_t nnz, const int32_t* row_pt
     if ((rc = upload(c, in.get(), hf, &d.h))) return rc;
     if ((rc = upload(c, in.get(), hd, &d.h_f64))) return rc;
     if ((rc = upload(c, in.get(), new2old, &d.new2old))) return rc;
+    {
+        // NMFA's field normalisation, 1 / sqrt(h_i^2 + sum_j J_ij^2), in FP64
+        std::vector<float> inv(n);
+        for (int32_t a = 0; a < n; ++a) {
+            double q = 0.0;
+            for (int32_t e = nrp[a]; e < nrp[a + 1]; ++e) q += nval_f64[e] * nval_f64[e];
+            if (!hh.empty()) q += hh[new2old[a]] * hh[new2old[a]];
+            inv[a] = q > 0.0 ? (float)(1.0 / std::sqrt(q)) : 0.f;
+        }
+        if ((rc = upload(c, in.get(), inv, &d.inv_norm))) return rc;
+    }
     MARS_CUDA(c, cudaStreamSynchronize(c->stream));
     guard.done = true;
     in->info.n = n;
@@ -743,6 +792,7 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     if (p->k_max < 1 || p->fixed_sweeps < 0) return fail(c, MARS_EINVAL, "k_max >= 1, fixed_sweeps >= 0");
     if (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI)
         return fail(c, MARS_EINVAL, "unknown update rule %d", p->update);
+    if (const char* e = method_error(p)) return fail(c, MARS_EINVAL, "%s", e);
     const bool tc = p->precision == MARS_BF16 || p->precision == MARS_FP8;
     if (p->precision != MARS_FP32 && !(tc && in->dev.dense && p->update == MARS_UPDATE_GS))
         return fail(c, MARS_EINVAL, "precision %d is not available for this instance and update rule",
@@ -767,6 +817,7 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     s.fixed_sweeps = p->fixed_sweeps;
     set_schedule(s, p);
     s.jacobi = p->update == MARS_UPDATE_JACOBI;
+    set_method(s, p);
     // start temperatures
     float* t0 = nullptr;
     if ((rc = S.get(R, &t0))) return rc;
@@ -958,8 +1009,8 @@ int mars_solve_batch(mars_ctx* c, int32_t count, const int32_t* insts, const mar
             !(p->d_min >= 0.0) ||
             p->k_max < 1 || p->fixed_sweeps < 0)
             return fail(c, MARS_EINVAL, "job %d: bad parameters", j);
-        if (p->update != MARS_UPDATE_GS || p->precision != MARS_FP32)
-            return fail(c, MARS_EINVAL, "job %d: batched launches run sequential FP32 sweeps", j);
+        if (p->update != MARS_UPDATE_GS || p->precision != MARS_FP32 || p->method != MARS_METHOD_MARS)
+            return fail(c, MARS_EINVAL, "job %d: batched launches run sequential FP32 MARS sweeps", j);
         if ((size_t)R * n > ((size_t)1 << 40)) return fail(c, MARS_EINVAL, "job %d: R*n too large", j);
         ins[j] = in;
         dins[j] = in->dev;
@@ -1146,6 +1197,7 @@ int mars_autotune(mars_ctx* c, int32_t id, const mars_params* p, int32_t repeats
     const DevInstance& d = in->dev;
     std::vector<LaunchShape> cands;
     if (d.dense && (p->precision == MARS_BF16 || p->precision == MARS_FP8)) {
+        cands.push_back(LaunchShape{});  // the library's plan, following the active replicas
         for (int sched = 0; sched < 3; ++sched)  // plain, overlap, pairs
             for (int rpw : {1, 2, 4}) {
                 LaunchShape sh;

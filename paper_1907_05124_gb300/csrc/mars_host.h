@@ -31,6 +31,11 @@ double levels_bound(const mars_params* p, double t0);
 // needs none.
 bool schedule_ok(const mars_params* p);
 
+// Why p's method settings are refused (null when they are fine), and the
+// method's settings of a descent: NMFA runs synchronous sweeps, one per level.
+const char* method_error(const mars_params* p);
+void set_method(DevSolve& s, const mars_params* p);
+
 template <class S>
 void set_schedule(S& s, const mars_params* p)
 {
@@ -174,6 +179,14 @@ struct TcRun {
     std::vector<cudaEvent_t> ev;
     float* Gbuf[2] = {nullptr, nullptr};
     float* Gx[2] = {nullptr, nullptr};
+    size_t g_floats_max = 0;           // one G buffer at the largest split
+    // The plan follows the active replicas from batch to batch unless the
+    // instance's shape or an environment override fixes it; chain_slots and
+    // gemm_tiles cover the active prefix the plan was made for.
+    bool adaptive = false;
+    int fixed_rpw = -1, fixed_overlap = -1, fixed_pair = -1;
+    int chain_slots = 0, gemm_tiles = 0;
+    int sms = 0, kblocks_total = 0;
     ~TcRun()
     {
         if (exec) cudaGraphExecDestroy(exec);

@@ -62,6 +62,7 @@ struct DevInstance {
     // common
     const float* h = nullptr;          // n floats or null
     const double* h_f64 = nullptr;     // n doubles or null
+    const float* inv_norm = nullptr;   // n: 1 / sqrt(h_i^2 + sum_j J_ij^2), 0 where that is 0 (NMFA)
     const int32_t* new2old = nullptr;  // n
 };
 
@@ -96,6 +97,10 @@ struct DevSolve {
     double cool_ratio = 0.5;
     double t_floor = 0.0;
     int32_t jacobi = 0;
+    // noisy mean-field annealing (synchronous sweeps, one per level) instead
+    // of Algorithm 1's update
+    int32_t nmfa = 0;
+    float nmfa_alpha = 0.5f, nmfa_sigma = 0.f;
     const double* t_first = nullptr;   // optional per-replica temperature of the first level
     int32_t one_level = 0;             // stop after the first level (the FP32 polish)
     int32_t add_counts = 0;            // add sweeps/levels/capped to the outputs' values

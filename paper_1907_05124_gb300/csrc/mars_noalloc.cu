@@ -73,8 +73,8 @@ extern "C" int mars_solve_noalloc(mars_ctx* c, int32_t id, const mars_params* p,
         return noalloc_fail(c, MARS_EINVAL, "need c_step > 0 and t_max / c_step <= 1e6");
     if (!(p->d_min >= 0.0) || p->k_max < 1 || p->fixed_sweeps < 0)
         return noalloc_fail(c, MARS_EINVAL, "need d_min >= 0, k_max >= 1, fixed_sweeps >= 0");
-    if (p->update != MARS_UPDATE_GS || p->precision != MARS_FP32)
-        return noalloc_fail(c, MARS_EINVAL, "mars_solve_noalloc runs sequential FP32 sweeps only");
+    if (p->update != MARS_UPDATE_GS || p->precision != MARS_FP32 || p->method != MARS_METHOD_MARS)
+        return noalloc_fail(c, MARS_EINVAL, "mars_solve_noalloc runs sequential FP32 MARS sweeps only");
     if (p->schedule != MARS_SCHEDULE_LINEAR || p->quench)
         return noalloc_fail(c, MARS_EINVAL, "mars_solve_noalloc runs the paper's linear schedule only");
     if ((p->m0 || p->t0) && !(p->flags & MARS_DEVICE_PTR))

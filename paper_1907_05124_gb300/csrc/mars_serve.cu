@@ -208,7 +208,7 @@ void serve_free_req(mars_ctx* c, Serve* sv, ServeReq* q)
 size_t serve_footprint(const DevInstance& d, const mars_params& p, int device)
 {
     const size_t R = (size_t)p.replicas, n = (size_t)d.n;
-    const bool jacobi = p.update == MARS_UPDATE_JACOBI;
+    const bool jacobi = p.update == MARS_UPDATE_JACOBI || p.method == MARS_METHOD_NMFA;
     // t0, sigma, energies (double and int64), sweeps/levels/capped, the work
     // counter and status, the result record, the best spins, and the replica
     // queue at its widest slot rounding (at most 8 replicas per tile)
@@ -298,6 +298,7 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
     s.fixed_sweeps = p.fixed_sweeps;
     set_schedule(s, &p);
     s.jacobi = p.update == MARS_UPDATE_JACOBI;
+    set_method(s, &p);
     s.m0 = p.m0;
     float* t0 = nullptr;
     if ((rc = get((size_t)R * sizeof(float), (void**)&t0))) return rc;
@@ -572,6 +573,7 @@ int mars_submit(mars_ctx* c, int32_t id, const mars_params* p, int64_t* req)
         p->k_max < 1 || p->fixed_sweeps < 0 ||
         (p->update != MARS_UPDATE_GS && p->update != MARS_UPDATE_JACOBI))
         return fail(c, MARS_EINVAL, "bad parameters");
+    if (const char* e = method_error(p)) return fail(c, MARS_EINVAL, "%s", e);
     const bool tc = p->precision == MARS_BF16 || p->precision == MARS_FP8;
     if (p->precision != MARS_FP32 && !(tc && in->dev.dense && p->update == MARS_UPDATE_GS))
         return fail(c, MARS_EINVAL, "precision %d is not available for this instance", p->precision);

@@ -49,6 +49,64 @@ bool encode_2d(CUtensorMap* m, CUtensorMapDataType dt, uint32_t elem, const void
 
 
 
+// The sweep's launch plan for `active` active replicas whose slots lie below
+// `prefix`: replicas per chain warp, the GEMM schedule (plain, overlapped with
+// the previous panel's chain, or panel pairs) and the split of K.
+//
+// With (nearly) every replica active the GEMMs fill the GPU and panel pairs
+// win: they stream the magnetisations' copy once per two panels. Once fewer
+// replicas remain the SMs are no longer all busy, so panel p+1's GEMM runs
+// beside panel p's chain (the overlap) and the chain's steps are shortened by
+// fewer replicas per warp; most of a solve's sweeps run in that regime (the
+// replicas' sweep counts spread evenly from zero to the longest). K is split
+// until one GEMM wave covers the SMs. A knob the instance's shape or an
+// environment override fixes is kept. A plan change drops the captured
+// sweep graph; the next batch captures the new one.
+int tc_plan(mars_ctx* c, TcRun* run, int32_t active, int32_t prefix)
+{
+    // the count the defaults follow: the active replicas, or (a knob fixed)
+    // the replica count, as measured for whole sweeps at N = 8192
+    const int A = run->adaptive && active > 0 ? active : run->t.R;
+    int rpw = A >= 2048 ? 4 : A >= 512 ? 2 : 1;
+    int ov = run->adaptive ? (A < 2048 ? 1 : 0) : (A >= 512 && A < 2048 ? 1 : 0);
+    int pair = A >= 2048 ? 1 : 0;
+    if (run->fixed_rpw >= 0) rpw = run->fixed_rpw;
+    if (run->fixed_overlap >= 0) ov = run->fixed_overlap;
+    if (run->fixed_pair >= 0) pair = run->fixed_pair;
+    if (rpw != 1 && rpw != 2 && rpw != 4) rpw = 1;
+    const bool pr = run->P >= 2 && pair != 0;
+    const bool ovl = run->P >= 2 && ov != 0 && !pr;
+    const int slots = std::min(std::max(prefix, 1), run->t.R);
+    const int tiles = (slots + kTcBN - 1) / kTcBN;
+    int splitk = 1;
+    const int split_max = env_flag("MARS_TC_SPLITK_MAX", 16);
+    while (splitk < split_max && splitk * 2 <= kChainMaxSplit / rpw && tiles * splitk * 2 <= run->sms &&
+           run->kblocks_total % (splitk * 2) == 0)
+        splitk *= 2;
+    const int chain_slots = std::min(tiles * kTcBN, run->t.R);  // the chains cover [0, chain_slots)
+    if (run->exec && rpw == run->rpw && ovl == run->overlap && pr == run->pair && splitk == run->splitk &&
+        tiles == run->gemm_tiles && chain_slots == run->chain_slots)
+        return MARS_OK;
+    if (run->exec) cudaGraphExecDestroy(run->exec);
+    if (run->graph) cudaGraphDestroy(run->graph);
+    run->exec = nullptr;
+    run->graph = nullptr;
+    run->rpw = rpw;
+    run->overlap = ovl;
+    run->pair = pr;
+    run->splitk = splitk;
+    run->t.splitk = splitk;
+    run->g.kblocks = run->kblocks_total / splitk;
+    run->gemm_tiles = tiles;
+    run->chain_slots = chain_slots;
+    if (ovl && !run->side) {
+        MARS_CUDA(c, cudaStreamCreateWithFlags(&run->side, cudaStreamNonBlocking));
+        run->ev.resize(1 + 2 * (size_t)run->P, nullptr);
+        for (cudaEvent_t& e : run->ev) MARS_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    return MARS_OK;
+}
+
 // Device state of a tensor-core descent; buffers come from `get` so that the
 // blocking path (Scratch) and the serving engine (per-request lists) can own them.
 int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t* rep_dev,
@@ -60,35 +118,21 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     const int32_t R_pad = (R + kTcBN - 1) / kTcBN * kTcBN;
     run->P = n_pad / 128;
     run->ntiles = R_pad / kTcBN;
-    // Replicas per chain warp: several per warp cut the chain's issued
-    // instructions per replica and leave SMs to the overlapped GEMM. The
-    // defaults are the fastest shapes measured on a GB300 at N = 8192 (ms per
-    // sweep): R = 1024, overlap with 2 per warp 1.04 (pairs 1.13, plain 1.26);
-    // R = 4096, panel pairs with 4 per warp 1.94 (plain 2.04, overlap 2.51:
-    // the chain and the GEMM then compete for SMs). mars_autotune picks per
-    // instance.
+    // The launch plan (replicas per chain warp, GEMM schedule, split of K)
+    // follows the active replicas batch by batch (tc_plan) unless the
+    // instance's shape (mars_set_shape, mars_autotune) or an environment
+    // override fixes a knob.
     const LaunchShape& sh = d.shape;
-    int rpw = sh.tc_rpw >= 0 ? sh.tc_rpw : env_flag("MARS_TC_RPW", R >= 2048 ? 4 : R >= 512 ? 2 : 1);
-    if (rpw != 1 && rpw != 2 && rpw != 4) rpw = 1;
-    run->rpw = rpw;
-    const int ov = sh.tc_overlap >= 0 ? sh.tc_overlap
-                                      : env_flag("MARS_TC_OVERLAP", R >= 512 && R < 2048 ? 1 : 0);
-    run->pair = run->P >= 2 && (sh.tc_pair >= 0 ? sh.tc_pair : env_flag("MARS_TC_PAIR", R >= 2048 ? 1 : 0)) != 0;
-    run->overlap = run->P >= 2 && ov != 0 && !run->pair;
-    // Split K until the panel GEMM fills the SMs in one wave (one CTA per SM):
-    // a short GEMM is bound by each CTA's pipeline fill and TMA bytes in
-    // flight, so more, shorter CTAs finish sooner.
-    int splitk = 1;
-    const int split_max = env_flag("MARS_TC_SPLITK_MAX", 16);
-    while (splitk < split_max && splitk * 2 <= kChainMaxSplit / rpw && run->ntiles * splitk * 2 <= c->sms &&
-           (n_pad / (fp8 ? 128 : 64)) % (splitk * 2) == 0)
-        splitk *= 2;
-    run->splitk = splitk;
+    run->fixed_rpw = sh.tc_rpw >= 0 ? sh.tc_rpw : env_flag("MARS_TC_RPW", -1);
+    run->fixed_overlap = sh.tc_overlap >= 0 ? sh.tc_overlap : env_flag("MARS_TC_OVERLAP", -1);
+    run->fixed_pair = sh.tc_pair >= 0 ? sh.tc_pair : env_flag("MARS_TC_PAIR", -1);
+    run->adaptive = run->fixed_rpw < 0 && run->fixed_overlap < 0 && run->fixed_pair < 0;
+    run->sms = c->sms;
+    run->kblocks_total = n_pad / (fp8 ? 128 : 64);
     t.R = R;
     t.R_pad = R_pad;
     t.n = n;
     t.n_pad = n_pad;
-    t.splitk = splitk;
     t.Jdiag = d.Jdiag;
     t.Jsup = d.Jsup;
     t.h = d.h;
@@ -113,20 +157,16 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     } else if ((rc = get((size_t)R_pad * n_pad * sizeof(__nv_bfloat16), (void**)&t.Sb))) {
         return rc;
     }
-    const size_t g_floats = (size_t)splitk * R_pad * 128;
-    if ((rc = get(2 * g_floats * sizeof(float), (void**)&t.G))) return rc;
+    // split-K partials at the largest split any plan may take, two buffers
+    run->g_floats_max = (size_t)kChainMaxSplit * R_pad * 128;
+    if ((rc = get(2 * run->g_floats_max * sizeof(float), (void**)&t.G))) return rc;
     run->Gbuf[0] = t.G;
-    run->Gbuf[1] = t.G + g_floats;
-    if (run->overlap || run->pair) {
+    run->Gbuf[1] = t.G + run->g_floats_max;
+    {
         float* gx = nullptr;
         if ((rc = get(2 * (size_t)R_pad * 128 * sizeof(float), (void**)&gx))) return rc;
         run->Gx[0] = gx;
         run->Gx[1] = gx + (size_t)R_pad * 128;
-    }
-    if (run->overlap) {
-        MARS_CUDA(c, cudaStreamCreateWithFlags(&run->side, cudaStreamNonBlocking));
-        run->ev.resize(1 + 2 * (size_t)run->P, nullptr);
-        for (cudaEvent_t& e : run->ev) MARS_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     if ((rc = get((size_t)R * sizeof(double), (void**)&t.T))) return rc;
     if ((rc = get((size_t)R * sizeof(float), (void**)&t.invT))) return rc;
@@ -150,7 +190,6 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     if (!maps_ok) return fail(c, MARS_EDEVICE, "tensor map encoding failed");
     MARS_CUDA(c, launch_tc_init(t, st));
     MARS_CUDA(c, launch_tc_prefix(t, st));
-    run->g.kblocks = n_pad / (fp8 ? 128 : 64) / splitk;
     run->g.fp8 = fp8 ? 1 : 0;
     run->g.R_pad = R_pad;
     run->g.G = t.G;
@@ -165,7 +204,7 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
     run->sweep_cap = (int64_t)(levels_max * (double)(s.fixed_sweeps > 0 ? s.fixed_sweeps : s.k_max)) + 1;
     run->batch = 1;
     run->done_sweeps = 0;
-    return MARS_OK;
+    return tc_plan(c, run, R, R);
 }
 
 // One sweep as direct launches; with `timed`, event pairs bracket each GEMM.
@@ -178,6 +217,9 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
     const bool ov = run->overlap;
     const int P = run->P;
     if (timed) run->timed_rows.clear();
+    // the chains cover the slots below the active prefix the plan was made for
+    TcState tc = run->t;
+    tc.R = run->chain_slots;
     if (run->pair) {
         // panels in pairs: one GEMM for panels pp and pp+1, chain pp (which
         // adds its new spins to panel pp+1's fields), chain pp+1
@@ -192,18 +234,17 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
             if (two) {
                 g.G1 = run->Gbuf[1];
                 g.skip_kb = kb_per_panel * pp;
-                MARS_CUDA(c, launch_tc_pair_gemm(run->tmJ, run->tmS, g, run->ntiles, run->splitk, st));
+                MARS_CUDA(c, launch_tc_pair_gemm(run->tmJ, run->tmS, g, run->gemm_tiles, run->splitk, st));
             } else {
                 g.skip_kb = -1;
-                MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->ntiles, run->splitk, st));
+                MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->gemm_tiles, run->splitk, st));
             }
             if (timed) {
                 MARS_CUDA(c, cudaEventRecord(c->prof[2 * e + 1], st));
                 run->timed_rows.push_back(two ? 256 : 128);
             }
-            MARS_CUDA(c, launch_tc_chain(run->t, pp, run->rpw, run->Gbuf[0], nullptr, two ? run->Gx[0] : nullptr,
-                                         st));
-            if (two) MARS_CUDA(c, launch_tc_chain(run->t, pp + 1, run->rpw, run->Gbuf[1], run->Gx[0], nullptr, st));
+            MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[0], nullptr, two ? run->Gx[0] : nullptr, st));
+            if (two) MARS_CUDA(c, launch_tc_chain(tc, pp + 1, run->rpw, run->Gbuf[1], run->Gx[0], nullptr, st));
         }
         MARS_CUDA(c, launch_tc_advance(run->t, st));
         return MARS_OK;
@@ -220,7 +261,7 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
         g.skip_kb = ov && pp > 0 ? (g.fp8 ? 1 : 2) * (pp - 1) : -1;  // panel pp-1's K blocks
         if (ov && pp >= 2) MARS_CUDA(c, cudaStreamWaitEvent(gs, run->ev[2 + 2 * (pp - 2)], 0));
         if (timed) MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp], gs));
-        MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->ntiles, run->splitk, gs));
+        MARS_CUDA(c, launch_tc_panel_gemm(run->tmJ, run->tmS, g, kTcBN, run->gemm_tiles, run->splitk, gs));
         if (timed) {
             MARS_CUDA(c, cudaEventRecord(c->prof[2 * pp + 1], gs));
             run->timed_rows.push_back(128);
@@ -231,7 +272,7 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
         }
         const float* gx_in = ov && pp > 0 ? run->Gx[pp & 1] : nullptr;
         float* gx_out = ov && pp + 1 < P ? run->Gx[(pp + 1) & 1] : nullptr;
-        MARS_CUDA(c, launch_tc_chain(run->t, pp, run->rpw, run->Gbuf[pp & 1], gx_in, gx_out, st));
+        MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[pp & 1], gx_in, gx_out, st));
         if (ov) MARS_CUDA(c, cudaEventRecord(run->ev[2 + 2 * pp], st));
     }
     MARS_CUDA(c, launch_tc_advance(run->t, st));
@@ -244,6 +285,9 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
 int tc_enqueue_batch(mars_ctx* c, TcRun* run, cudaStream_t st)
 {
     int rc;
+    if (run->active_at_batch > 0 &&
+        (rc = tc_plan(c, run, run->active_at_batch, run->h_counters ? run->h_counters[0] : run->t.R)))
+        return rc;
     if (run->profile) {
         while ((int)c->prof.size() < 2 * run->P) {
             cudaEvent_t e;

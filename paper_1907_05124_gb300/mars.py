@@ -44,7 +44,20 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("m0", ctypes.c_void_p),
                 ("t0", ctypes.c_void_p), ("flags", ctypes.c_uint32),
                 ("schedule", ctypes.c_int32), ("cool_ratio", ctypes.c_double),
-                ("t_floor", ctypes.c_double), ("quench", ctypes.c_int32)]
+                ("t_floor", ctypes.c_double), ("quench", ctypes.c_int32),
+                ("method", ctypes.c_int32), ("nmfa_alpha", ctypes.c_double),
+                ("nmfa_sigma", ctypes.c_double)]
+
+
+METHOD = {"mars": 0, "nmfa": 1}
+
+
+def _method(p, method="mars", alpha=0.5, sigma=0.0):
+    """Set the method on Params p: MARS (Algorithm 1) or NMFA (noisy mean-field
+    annealing with mixing weight alpha and noise deviation sigma)."""
+    p.method = METHOD[method]
+    p.nmfa_alpha = float(alpha)
+    p.nmfa_sigma = float(sigma)
 
 
 def _schedule(p, geometric=None, t_floor=0.0, quench=False):
@@ -304,14 +317,17 @@ class Context:
     def solve(self, inst: int, replicas: int, t_min: float, t_max: float, *, c_step=1.0,
               d_min=1e-4, k_max=1000, fixed_sweeps=0, seed=0, stream=0, update="gs",
               precision="fp32", m0=None, t0=None, outputs=("energies",), device_outputs=False,
-              polish=False, geometric=None, t_floor=0.0, quench=False):
+              polish=False, geometric=None, t_floor=0.0, quench=False, method="mars", alpha=0.5,
+              sigma=0.0):
         """Run mars_solve; `outputs` names the per-replica arrays to return.
         geometric=r (with t_floor) and quench=True select the labelled
-        schedule variants (the paper's linear schedule by default)."""
+        schedule variants (the paper's linear schedule by default);
+        method="nmfa" runs noisy mean-field annealing with alpha and sigma."""
         n = self._n[inst]
         p = Params()
         self._lib.mars_params_default(ctypes.byref(p))
         _schedule(p, geometric, t_floor, quench)
+        _method(p, method, alpha, sigma)
         p.replicas, p.t_min, p.t_max, p.c_step, p.d_min = int(replicas), t_min, t_max, c_step, d_min
         p.k_max, p.fixed_sweeps, p.seed, p.stream = int(k_max), int(fixed_sweeps), int(seed), int(stream)
         p.update, p.precision = UPDATE[update], PRECISION[precision]
@@ -448,11 +464,13 @@ class Context:
 
     def submit(self, inst: int, replicas: int, t_min: float, t_max: float, *, c_step=1.0,
                d_min=1e-4, k_max=1000, fixed_sweeps=0, seed=0, stream=0, update="gs",
-               precision="fp32", geometric=None, t_floor=0.0, quench=False) -> int:
+               precision="fp32", geometric=None, t_floor=0.0, quench=False, method="mars",
+               alpha=0.5, sigma=0.0) -> int:
         """mars_submit: queue a solve and return its request id."""
         p = Params()
         self._lib.mars_params_default(ctypes.byref(p))
         _schedule(p, geometric, t_floor, quench)
+        _method(p, method, alpha, sigma)
         p.replicas, p.t_min, p.t_max, p.c_step, p.d_min = int(replicas), t_min, t_max, c_step, d_min
         p.k_max, p.fixed_sweeps, p.seed, p.stream = int(k_max), int(fixed_sweeps), int(seed), int(stream)
         p.update, p.precision = UPDATE[update], PRECISION[precision]

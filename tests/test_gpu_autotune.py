@@ -62,7 +62,10 @@ def test_dense_autotune_and_replicas_per_warp(ctx):
     m0, t0 = I.replica_inputs(R, n, 0.0, 24.0, 23)
     kw = dict(m0=m0, t0=t0, precision="bf16", fixed_sweeps=2, c_step=4.0)
     shape, sec = ctx.autotune(inst, R, 0.0, 24.0, repeats=1, **kw)
-    assert shape["tc_rpw"] in (1, 2, 4) and shape["tc_overlap"] in (0, 1) and shape["tc_pair"] in (0, 1)
+    # the winner is the library's own per-batch plan (every knob -1) or a fixed shape
+    planned = shape["tc_rpw"] == shape["tc_overlap"] == shape["tc_pair"] == -1
+    assert planned or (shape["tc_rpw"] in (1, 2, 4) and shape["tc_overlap"] in (0, 1)
+                       and shape["tc_pair"] in (0, 1))
     oi = O.Instance.dense(J)
     for ov, pair in ((0, 0), (1, 0), (0, 1)):
         runs = []
