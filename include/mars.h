@@ -56,7 +56,8 @@ typedef enum {
     MARS_EAGAIN = -3,    /* result not ready yet (non-blocking calls) */
     MARS_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
     MARS_EDEVICE = -5,   /* a CUDA call failed */
-    MARS_ENOTFOUND = -6  /* unknown instance or request id */
+    MARS_ENOTFOUND = -6, /* unknown instance or request id */
+    MARS_ECANCELED = -7  /* the request was cancelled (mars_cancel) */
 } mars_status;
 
 typedef enum { MARS_I8 = 1, MARS_F32 = 2, MARS_F64 = 3 } mars_dtype;
@@ -356,6 +357,15 @@ int mars_submit(mars_ctx* ctx, int32_t inst, const mars_params* params, int64_t*
  */
 int mars_poll(mars_ctx* ctx, int64_t req, int8_t* best_spins, mars_result* result);
 
+/*
+ * Cancel a request. A queued request is dropped at once; a running one keeps
+ * its kernels in flight (a dense tensor-core request stops after its current
+ * batch of sweeps), its results are discarded and its buffers freed when they
+ * end. Either way the request's mars_poll returns MARS_ECANCELED once.
+ * Errors: MARS_ENOTFOUND for an unknown (or already collected) id.
+ */
+int mars_cancel(mars_ctx* ctx, int64_t req);
+
 /* Numbers of queued and running requests (after advancing the engine). */
 int mars_serve_status(mars_ctx* ctx, int32_t* queued, int32_t* running);
 
@@ -368,6 +378,23 @@ int mars_serve_status(mars_ctx* ctx, int32_t* queued, int32_t* running);
  * stream (dense requests and the rest). Either pointer may be NULL.
  */
 int mars_serve_counters(mars_ctx* ctx, int64_t* ring_jobs, int64_t* stream_jobs);
+
+/*
+ * Failure detection: a device-side bounded wait on a host-mapped flag, the
+ * signalling the serving engine's results travel by. One thread of a kernel
+ * polls the flag for at most budget_us microseconds (by its own clock64);
+ * the host raises the flag right after the launch. MARS_OK when the kernel
+ * saw the flag in time; MARS_ETIMEOUT when the wait gave up (the kernel
+ * records that in a status word and exits; the context stays usable);
+ * MARS_EINVAL for budget_us outside [1, 10^7]. The paper has no counterpart
+ * (it is part of the serving engine's failure detection).
+ *
+ * Host-side fault injection for tests reads the environment variable
+ * MARS_FAULT when the context is created: a comma-separated list of
+ *   alloc:K  the K-th device allocation of the context fails (MARS_ENOMEM)
+ *   flag     mars_device_check never raises its flag (its wait runs out)
+ */
+int mars_device_check(mars_ctx* ctx, int32_t budget_us);
 
 /*
  * Exact energies (Section 2, Eq. 2, pairs once) of count spin vectors

@@ -171,4 +171,22 @@ cudaError_t launch_energy(const DevInstance& in, const int8_t* spins, int32_t co
     return cudaGetLastError();
 }
 
+// Failure detection's bounded wait (mars_device_check): poll a flag in
+// host-mapped memory with a clock64 budget. Nothing is in flight while it
+// waits, so giving up is only a status word and a return.
+__global__ void flag_wait_kernel(const volatile int32_t* flag, long long budget_cycles, int32_t* status)
+{
+    const long long t0 = clock64();
+    int32_t seen = 0;
+    while (!(seen = *flag) && clock64() - t0 < budget_cycles) __nanosleep(200);
+    *status = seen ? kDevOk : kDevTimeout;
+}
+
+cudaError_t launch_flag_wait(const int32_t* flag, long long budget_cycles, int32_t* status,
+                             cudaStream_t st)
+{
+    flag_wait_kernel<<<1, 1, 0, st>>>(flag, budget_cycles, status);
+    return cudaGetLastError();
+}
+
 }  // namespace mars

@@ -8,6 +8,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -89,6 +90,9 @@ int dev_alloc(mars_ctx* c, size_t bytes, DevMem* out)
     out->p = nullptr;
     out->bytes = 0;
     if (bytes == 0) return MARS_OK;
+    if (c->fault_alloc_at > 0 && ++c->allocs == c->fault_alloc_at)
+        return fail(c, MARS_ENOMEM, "device allocation %lld failed (injected by MARS_FAULT)",
+                    (long long)c->allocs);
     if (c->budget && c->used + bytes > c->budget)
         return fail(c, MARS_ENOMEM, "HBM budget exceeded: %zu + %zu > %zu bytes", c->used, bytes,
                     c->budget);
@@ -108,6 +112,9 @@ int dev_alloc_on(mars_ctx* c, size_t bytes, DevMem* out, cudaStream_t st)
     out->p = nullptr;
     out->bytes = 0;
     if (bytes == 0) return MARS_OK;
+    if (c->fault_alloc_at > 0 && ++c->allocs == c->fault_alloc_at)
+        return fail(c, MARS_ENOMEM, "device allocation %lld failed (injected by MARS_FAULT)",
+                    (long long)c->allocs);
     if (c->budget && c->used + bytes > c->budget)
         return fail(c, MARS_ENOMEM, "HBM budget exceeded: %zu + %zu > %zu bytes", c->used, bytes,
                     c->budget);
@@ -279,6 +286,23 @@ uint16_t float_to_bf16_bits(float f)
     return (uint16_t)(u >> 16);
 }
 
+// Host-side fault injection for tests (MARS_FAULT, a comma-separated list):
+// "alloc:K" fails the context's K-th device allocation, "flag" withholds
+// mars_device_check's flag. Unknown items are ignored.
+void parse_faults(mars_ctx* c, const char* spec)
+{
+    if (!spec) return;
+    std::string all(spec);
+    size_t pos = 0;
+    while (pos <= all.size()) {
+        const size_t end = std::min(all.find(',', pos), all.size());
+        const std::string item = all.substr(pos, end - pos);
+        if (item.rfind("alloc:", 0) == 0) c->fault_alloc_at = std::atoll(item.c_str() + 6);
+        if (item == "flag") c->fault_flag = true;
+        pos = end + 1;
+    }
+}
+
 // Accessors for mars_noalloc.cu.
 int noalloc_view(mars_ctx* c, int32_t id, NoallocView* v)
 {
@@ -331,6 +355,7 @@ int mars_create(mars_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_
         c->own_stream = true;
     }
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    parse_faults(c.get(), std::getenv("MARS_FAULT"));
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
         cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess)
         return MARS_EDEVICE;
@@ -352,6 +377,8 @@ void mars_destroy(mars_ctx* c)
         if (c->ev1) cudaEventDestroy(c->ev1);
         if (c->ev2) cudaEventDestroy(c->ev2);
         if (c->ev3) cudaEventDestroy(c->ev3);
+        if (c->check_flag) cudaFreeHost(c->check_flag);
+        if (c->check_status) cudaFree(c->check_status);
         if (c->own_stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -1243,6 +1270,35 @@ int mars_autotune(mars_ctx* c, int32_t id, const mars_params* p, int32_t repeats
         *best = mars_shape{win.sell_rt, win.sell_threads, win.sell_smem_table, win.tc_rpw, win.tc_overlap, win.tc_pair};
     if (seconds) *seconds = best_t;
     return MARS_OK;
+}
+
+int mars_device_check(mars_ctx* c, int32_t budget_us)
+{
+    if (!c) return MARS_EINVAL;
+    if (budget_us < 1 || budget_us > 10000000) return fail(c, MARS_EINVAL, "budget_us must be in [1, 1e7]");
+    DeviceGuard g(c->device);
+    if (!c->check_flag) {
+        MARS_CUDA(c, cudaHostAlloc((void**)&c->check_flag, sizeof(int32_t), cudaHostAllocMapped));
+        MARS_CUDA(c, cudaMalloc((void**)&c->check_status, sizeof(int32_t)));
+    }
+    int32_t* dflag = nullptr;
+    MARS_CUDA(c, cudaHostGetDevicePointer((void**)&dflag, c->check_flag, 0));
+    *reinterpret_cast<volatile int32_t*>(c->check_flag) = 0;
+    MARS_CUDA(c, cudaMemsetAsync(c->check_status, 0, sizeof(int32_t), c->stream));
+    int clock_khz = 0;
+    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, c->device);
+    if (clock_khz <= 0) clock_khz = 2000000;
+    const long long budget_cycles = (long long)budget_us * (clock_khz / 1000);
+    MARS_CUDA(c, launch_flag_wait(dflag, budget_cycles, c->check_status, c->stream));
+    if (!c->fault_flag) {
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        *reinterpret_cast<volatile int32_t*>(c->check_flag) = 1;
+    }
+    int32_t status = 0;
+    MARS_CUDA(c, cudaMemcpyAsync(&status, c->check_status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
+    MARS_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (status == kDevTimeout) return fail(c, MARS_ETIMEOUT, "the device gave up waiting for the host's flag");
+    return status == kDevOk ? MARS_OK : fail(c, MARS_EDEVICE, "device status %d", status);
 }
 
 int mars_energy(mars_ctx* c, int32_t id, const int8_t* spins, int32_t count, double* e,

@@ -78,6 +78,13 @@ struct mars_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;  // ev3: end of the descent
     std::vector<cudaEvent_t> prof;  // event pairs around sampled panel GEMM launches
     void* noalloc_base = nullptr;   // device address of mars_solve_noalloc's static array
+    // host-side fault injection (MARS_FAULT, read at creation): the
+    // allocation that fails (1-based count, 0 = none) and a withheld flag
+    int64_t fault_alloc_at = 0, allocs = 0;
+    bool fault_flag = false;
+    // mars_device_check: host-mapped flag and its device status word
+    int32_t* check_flag = nullptr;
+    int32_t* check_status = nullptr;
     ~mars_ctx()
     {
         for (cudaEvent_t e : prof) cudaEventDestroy(e);
@@ -136,6 +143,9 @@ struct Scratch {
 };
 
 Instance* find(mars_ctx* c, int32_t id);
+
+// Reads MARS_FAULT's items into the context (mars_device_check documents them).
+void parse_faults(mars_ctx* c, const char* spec);
 
 // Value of an integer environment override, or dflt.
 int env_flag(const char* name, int dflt);

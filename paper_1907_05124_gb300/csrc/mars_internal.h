@@ -9,7 +9,7 @@
 namespace mars {
 
 // Device-side status words (status[0]); MARS_OK when clean.
-enum DeviceStatus : int32_t { kDevOk = 0, kDevBadIndex = 1 };
+enum DeviceStatus : int32_t { kDevOk = 0, kDevBadIndex = 1, kDevTimeout = 2 };
 
 // Instance data on the device, relabelled so that one sweep is "levels in
 // order, any order within a level": new label a has caller label new2old[a].
@@ -287,6 +287,11 @@ cudaError_t launch_draw(uint64_t seed, uint32_t stream, int32_t r0, int32_t R, i
 
 cudaError_t launch_queue_identity(int32_t* q, int32_t total, int32_t R, int32_t* counters,
                                   cudaStream_t st);
+
+// One thread polls a host-mapped flag until it is nonzero or budget_cycles of
+// its clock64 have passed; then it writes kDevOk or kDevTimeout to *status.
+cudaError_t launch_flag_wait(const int32_t* flag, long long budget_cycles, int32_t* status,
+                             cudaStream_t st);
 
 cudaError_t launch_best(const DevSolve& s, int32_t n, int32_t integer, int8_t* best_spins,
                         DevResult* res, cudaStream_t st);

@@ -47,6 +47,7 @@ struct ServeReq {
     double total_weight = 0.0, err_bound = 0.0;
     int64_t ring_job = -1;  // serving-ring job index, or -1
     size_t footprint = 0;   // the admission bound; what the request may allocate
+    bool cancelled = false; // mars_cancel while it ran: discard its results at the end
 };
 
 struct Serve {
@@ -451,6 +452,12 @@ void serve_progress(mars_ctx* c)
             serve_mark_failed(c, sv, q, MARS_EDEVICE);
             continue;
         }
+        if (q->state == ReqState::TcRunning && q->cancelled) {
+            // its last batch has ended: no more sweeps
+            fail(c, MARS_ECANCELED, "request %lld was cancelled", (long long)q->id);
+            serve_mark_failed(c, sv, q, MARS_ECANCELED);
+            continue;
+        }
         if (q->state == ReqState::TcRunning) {
             const int r = tc_after_batch(c, q->tc.get());
             int rc = MARS_OK;
@@ -477,6 +484,11 @@ void serve_progress(mars_ctx* c)
         if (q->ring_job >= 0) {
             sv->ring_refs -= 1;
             q->ring_job = -1;
+        }
+        if (q->cancelled) {
+            fail(c, MARS_ECANCELED, "request %lld was cancelled", (long long)q->id);
+            serve_mark_failed(c, sv, q, MARS_ECANCELED);
+            continue;
         }
         for (auto& b : q->bufs) dev_free_on(c, &b, q->st);
         q->bufs.clear();
@@ -632,6 +644,39 @@ int mars_poll(mars_ctx* c, int64_t req, int8_t* best_spins, mars_result* result)
     }
     serve_free_req(c, sv, q);
     sv->reqs.erase(it);
+    return MARS_OK;
+}
+
+int mars_cancel(mars_ctx* c, int64_t req)
+{
+    if (!c) return MARS_EINVAL;
+    DeviceGuard g(c->device);
+    Serve* sv = c->serve.get();
+    auto it = sv ? sv->reqs.find(req) : std::map<int64_t, std::unique_ptr<ServeReq>>::iterator();
+    if (!sv || it == sv->reqs.end()) return fail(c, MARS_ENOTFOUND, "unknown request %lld", (long long)req);
+    ServeReq* q = it->second.get();
+    switch (q->state) {
+    case ReqState::Queued: {
+        auto qi = std::find(sv->queue.begin(), sv->queue.end(), req);
+        if (qi != sv->queue.end()) sv->queue.erase(qi);
+        q->rc = MARS_ECANCELED;
+        q->err = "request was cancelled before it ran";
+        q->state = ReqState::Failed;
+        break;
+    }
+    case ReqState::Done:  // finished but not collected: discard the results
+        q->rc = MARS_ECANCELED;
+        q->err = "request was cancelled";
+        q->state = ReqState::Failed;
+        serve_free_req(c, sv, q);
+        break;
+    case ReqState::Failed:
+        break;
+    default:  // on the GPU: its kernels finish, then it is dropped
+        q->cancelled = true;
+        break;
+    }
+    serve_progress(c);
     return MARS_OK;
 }
 

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmars.so")
 
 MARS_OK, MARS_EINVAL, MARS_ENOMEM, MARS_EAGAIN, MARS_ETIMEOUT, MARS_EDEVICE, MARS_ENOTFOUND = \
     0, -1, -2, -3, -4, -5, -6
+MARS_ECANCELED = -7
 MARS_I8, MARS_F32, MARS_F64 = 1, 2, 3
 MARS_DEVICE_PTR = 1
 MARS_POLISH_FP32 = 2
@@ -26,7 +27,8 @@ UPDATE = {"gs": 0, "jacobi": 1}
 PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
 
 _ERRNAMES = {MARS_EINVAL: "EINVAL", MARS_ENOMEM: "ENOMEM", MARS_EAGAIN: "EAGAIN",
-             MARS_ETIMEOUT: "ETIMEOUT", MARS_EDEVICE: "EDEVICE", MARS_ENOTFOUND: "ENOTFOUND"}
+             MARS_ETIMEOUT: "ETIMEOUT", MARS_EDEVICE: "EDEVICE", MARS_ENOTFOUND: "ENOTFOUND",
+             MARS_ECANCELED: "ECANCELED"}
 
 
 class MarsError(RuntimeError):
@@ -128,6 +130,8 @@ SIGNATURES = {
     "mars_poll": (ctypes.c_int, [P, ctypes.c_int64, P, P]),
     "mars_serve_status": (ctypes.c_int, [P, P, P]),
     "mars_serve_counters": (ctypes.c_int, [P, P, P]),
+    "mars_cancel": (ctypes.c_int, [P, ctypes.c_int64]),
+    "mars_device_check": (ctypes.c_int, [P, ctypes.c_int32]),
     "mars_set_shape": (ctypes.c_int, [P, ctypes.c_int32, P]),
     "mars_get_shape": (ctypes.c_int, [P, ctypes.c_int32, P]),
     "mars_autotune": (ctypes.c_int, [P, ctypes.c_int32, P, ctypes.c_int32, P, P]),
@@ -502,6 +506,15 @@ class Context:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         self._check(self._lib.mars_serve_counters(self._ctx, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def cancel(self, req: int):
+        """mars_cancel: drop a queued request, or discard a running one's results."""
+        self._check(self._lib.mars_cancel(self._ctx, int(req)))
+
+    def device_check(self, budget_us: int = 100000):
+        """mars_device_check: a bounded device wait on a host-mapped flag (raises
+        MarsError with MARS_ETIMEOUT when the wait gives up)."""
+        self._check(self._lib.mars_device_check(self._ctx, int(budget_us)))
 
     def serve_status(self):
         q, rn = ctypes.c_int32(), ctypes.c_int32()
