@@ -31,6 +31,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <cstdlib>
+
 namespace mars {
 namespace {
 
@@ -84,6 +86,8 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t* done = empty + kStages;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
 
+    tc::pdl_launch_dependents();
+    tc::pdl_wait();  // the previous kernel's spins and active prefix
     const int n0 = blockIdx.x * BN;
     if (n0 >= *g.active_prefix) return;  // whole CTA, before any barrier
     const int split = blockIdx.y;
@@ -207,6 +211,8 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t* done = empty + kStages;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
 
+    tc::pdl_launch_dependents();
+    tc::pdl_wait();  // the previous kernel's spins and active prefix
     const int n0 = blockIdx.x * BN;
     if (n0 >= *g.active_prefix) return;  // whole CTA, before any barrier
     const int split = blockIdx.y;
@@ -364,15 +370,19 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
     const int grp = lane / LPR, j = lane % LPR;
     const int r = warp * RPW + grp;
     const int slot = slot0 + r;
-    const bool valid = slot < t.R && t.active[slot];
-    const float invT = valid ? t.invT[slot] : 0.f;  // idle groups compute and store nothing
+    tc::pdl_launch_dependents();
     if (tid == 0) {
+        // the instance's blocks do not depend on the previous kernels: their
+        // copy overlaps the previous kernel's end
         tc::mbar_init(bar, 1);
         tc::fence_barrier_init();
         tc::mbar_arrive_expect_tx(bar, L::kBlocks * L::kJ);
         tc::bulk_load(Jb, t.Jdiag + (size_t)p * kBM * kBM, L::kJ, bar);
         if (NEXT) tc::bulk_load(Jn, t.Jsup + (size_t)p * kBM * kBM, L::kJ, bar);
     }
+    tc::pdl_wait();  // the fields, spins and level state the previous kernels wrote
+    const bool valid = slot < t.R && t.active[slot];
+    const float invT = valid ? t.invT[slot] : 0.f;  // idle groups compute and store nothing
     // RPC replicas x 32 four-spin pieces = RPW pieces per thread.
     static_assert(RPC * (kBM / 4) == RPW * kChainWarps * 32, "one piece per thread and replica slot");
     float4 part[RPW][kSplitCap], gx[RPW], so[RPW];
@@ -486,13 +496,15 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
             float jr[SPL];
 #pragma unroll
             for (int q = qa; q < SPL; ++q) jr[q] = Jrow[j + LPR * q];
-            // The critical path: s_a = -tanh(y_a) = -sign(z) (1 - 2 / (1 + 2^|z|)),
-            // SFU ex2 and rcp; -y_a itself below |y| = 4e-3.
+            // The critical path: s_a = -tanh(y_a) = 2 / (1 + 2^z) - 1, SFU ex2
+            // and rcp on the signed z (2^z overflows to +inf for z >> 0, giving
+            // -1, and flushes to 0 for z << 0, giving +1); -y_a itself below
+            // |y| = 4e-3.
             const float z = fmaf(cz, snprev, bz);
             float e, rc;
-            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fabsf(z)));
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(z));
             asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rc) : "f"(1.0f + e));
-            const float big = copysignf(fmaf(-2.0f, rc, 1.0f), -z);
+            const float big = fmaf(2.0f, rc, -1.0f);
             const float sn = fabsf(z) < kSmallZ ? -kKinv * z : big;
             const float delta = sn - c.s_old_bf;
             dloc = fmaxf(dloc, fabsf(sn - c.s_old));
@@ -676,6 +688,29 @@ __global__ void tc_export_kernel(TcState t, DevInstance in, float* m_out, double
 
 }  // namespace
 
+// Launch with programmatic stream serialization (programmatic dependent
+// launch): the kernel may start while the stream's previous kernel still
+// runs, and its griddepcontrol.wait orders it after that kernel. MARS_TC_PDL=0
+// launches plainly.
+cudaError_t launch_pdl(const void* k, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st)
+{
+    static const bool on = [] {
+        const char* v = std::getenv("MARS_TC_PDL");
+        return !(v && *v && std::atoi(v) == 0);
+    }();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = on ? 1 : 0;
+    return cudaLaunchKernelExC(&cfg, k, args);
+}
+
 cudaError_t launch_tc_export(const TcState& t, const DevInstance& in, float* m_out, double* t_last,
                              cudaStream_t st)
 {
@@ -698,7 +733,7 @@ cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS,
     CUtensorMap a = tmJ, b = tmS;
     TcPanel c = g;
     void* args[] = {&a, &b, &c};
-    return cudaLaunchKernel(k, dim3(n_tiles, splitk), dim3(128), args, smem, st);
+    return launch_pdl(k, dim3(n_tiles, splitk), dim3(128), args, smem, st);
 }
 
 cudaError_t launch_tc_pair_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g, int n_tiles,
@@ -712,7 +747,7 @@ cudaError_t launch_tc_pair_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, 
     CUtensorMap a = tmJ, b = tmS;
     TcPanel c = g;
     void* args[] = {&a, &b, &c};
-    return cudaLaunchKernel(k, dim3(n_tiles, splitk), dim3(128), args, smem, st);
+    return launch_pdl(k, dim3(n_tiles, splitk), dim3(128), args, smem, st);
 }
 
 template <int RPW, bool NEXT, bool FP8>
@@ -724,9 +759,14 @@ cudaError_t launch_chain_as(const TcState& t, int p, const float* G, const float
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int per_cta = kChainWarps * RPW;
-    panel_chain_kernel<RPW, NEXT, FP8><<<(t.R + per_cta - 1) / per_cta, kChainWarps * 32, smem, st>>>(
-        t, p, G, gx_in, gx_out);
-    return cudaGetLastError();
+    TcState tt = t;
+    int pp = p;
+    const float* a0 = G;
+    const float* a1 = gx_in;
+    float* a2 = gx_out;
+    void* args[] = {&tt, &pp, &a0, &a1, &a2};
+    return launch_pdl((const void*)panel_chain_kernel<RPW, NEXT, FP8>, dim3((t.R + per_cta - 1) / per_cta),
+                      dim3(kChainWarps * 32), args, smem, st);
 }
 
 template <bool FP8>

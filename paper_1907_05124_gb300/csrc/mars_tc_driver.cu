@@ -67,9 +67,19 @@ int tc_plan(mars_ctx* c, TcRun* run, int32_t active, int32_t prefix)
     // the count the defaults follow: the active replicas, or (a knob fixed)
     // the replica count, as measured for whole sweeps at N = 8192
     const int A = run->adaptive && active > 0 ? active : run->t.R;
-    int rpw = A >= 2048 ? 4 : A >= 512 ? 2 : 1;
-    int ov = run->adaptive ? (A < 2048 ? 1 : 0) : (A >= 512 && A < 2048 ? 1 : 0);
-    int pair = A >= 2048 ? 1 : 0;
+    int rpw, ov, pair;
+    if (run->adaptive) {
+        // fastest all-active sweeps measured on a GB300 at N = 8192 (ms):
+        // A = 4096 pairs/4 2.15; 2048 pairs/2 1.48; 1024 overlap/2 1.19;
+        // 512 and below overlap/1 1.04-1.06
+        rpw = A >= 3072 ? 4 : A >= 768 ? 2 : 1;
+        ov = A < 1536 ? 1 : 0;
+        pair = A >= 1536 ? 1 : 0;
+    } else {
+        rpw = A >= 2048 ? 4 : A >= 512 ? 2 : 1;
+        ov = A >= 512 && A < 2048 ? 1 : 0;
+        pair = A >= 2048 ? 1 : 0;
+    }
     if (run->fixed_rpw >= 0) rpw = run->fixed_rpw;
     if (run->fixed_overlap >= 0) ov = run->fixed_overlap;
     if (run->fixed_pair >= 0) pair = run->fixed_pair;

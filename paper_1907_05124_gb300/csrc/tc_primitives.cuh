@@ -115,6 +115,17 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols)
                  : "memory");
 }
 
+// Programmatic dependent launch: launch_dependents lets the next kernel of
+// the stream start its independent prologue while this one still runs; wait
+// blocks until the previous kernel of the stream has completed and its
+// memory is visible (a no-op when the kernel was launched without the
+// programmatic-serialization attribute).
+__device__ __forceinline__ void pdl_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
