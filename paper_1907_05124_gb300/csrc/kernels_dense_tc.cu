@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t* done = empty + kStages;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
 
-    tc::pdl_launch_dependents();
     tc::pdl_wait();  // the previous kernel's spins and active prefix
+    tc::pdl_launch_dependents();
     const int n0 = blockIdx.x * BN;
     if (n0 >= *g.active_prefix) return;  // whole CTA, before any barrier
     const int split = blockIdx.y;
@@ -211,8 +211,8 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t* done = empty + kStages;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
 
-    tc::pdl_launch_dependents();
     tc::pdl_wait();  // the previous kernel's spins and active prefix
+    tc::pdl_launch_dependents();
     const int n0 = blockIdx.x * BN;
     if (n0 >= *g.active_prefix) return;  // whole CTA, before any barrier
     const int split = blockIdx.y;
@@ -353,7 +353,7 @@ struct ChainSmem {
 template <int RPW, bool NEXT, bool FP8>
 __global__ void __launch_bounds__(kChainWarps * 32, 1)
     panel_chain_kernel(TcState t, int p, const float* __restrict__ G, const float* __restrict__ gx_in,
-                       float* __restrict__ gx_out)
+                       float* __restrict__ gx_out, int g_early)
 {
     using L = ChainSmem<RPW, NEXT>;
     constexpr int LPR = 32 / RPW, SPL = kBM / LPR, RPC = kChainWarps * RPW;
@@ -370,41 +370,63 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
     const int grp = lane / LPR, j = lane % LPR;
     const int r = warp * RPW + grp;
     const int slot = slot0 + r;
-    tc::pdl_launch_dependents();
+    // Programmatic launch: this kernel may start while the stream's previous
+    // kernel still runs (that kernel released its dependents only after its
+    // own predecessor had completed). Everything but that kernel's output is
+    // read first: the instance's blocks, this panel's old spins, the level
+    // state (the level step runs between sweeps, before the sweep's first
+    // kernel) and, when `g_early`, the fields, whose GEMM is not the stream's
+    // previous kernel. The previous chain's next-panel fields (gx_in), and
+    // the fields when the GEMM is the previous kernel, come after the wait.
     if (tid == 0) {
-        // the instance's blocks do not depend on the previous kernels: their
-        // copy overlaps the previous kernel's end
         tc::mbar_init(bar, 1);
         tc::fence_barrier_init();
         tc::mbar_arrive_expect_tx(bar, L::kBlocks * L::kJ);
         tc::bulk_load(Jb, t.Jdiag + (size_t)p * kBM * kBM, L::kJ, bar);
         if (NEXT) tc::bulk_load(Jn, t.Jsup + (size_t)p * kBM * kBM, L::kJ, bar);
     }
-    tc::pdl_wait();  // the fields, spins and level state the previous kernels wrote
     const bool valid = slot < t.R && t.active[slot];
     const float invT = valid ? t.invT[slot] : 0.f;  // idle groups compute and store nothing
     // RPC replicas x 32 four-spin pieces = RPW pieces per thread.
     static_assert(RPC * (kBM / 4) == RPW * kChainWarps * 32, "one piece per thread and replica slot");
     float4 part[RPW][kSplitCap], gx[RPW], so[RPW];
     uint2 sbw[RPW];  // the four spins' low-precision copies (BF16, or E4M3 in .x)
+    auto load_fields = [&]() {
+#pragma unroll
+        for (int k = 0; k < RPW; ++k) {
+            const int e = tid + k * kChainWarps * 32;
+            const int rr = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
+            const int sl = slot0 + rr < t.R ? slot0 + rr : 0;
+#pragma unroll
+            for (int sp = 0; sp < kSplitCap; ++sp)
+                part[k][sp] = sp < t.splitk
+                                  ? *reinterpret_cast<const float4*>(G + ((size_t)sp * t.R_pad + sl) * kBM + a4)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
         const int e = tid + k * kChainWarps * 32;
         const int rr = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
         const int sl = slot0 + rr < t.R ? slot0 + rr : 0;
-#pragma unroll
-        for (int sp = 0; sp < kSplitCap; ++sp)
-            part[k][sp] = sp < t.splitk
-                              ? *reinterpret_cast<const float4*>(G + ((size_t)sp * t.R_pad + sl) * kBM + a4)
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
-        gx[k] = gx_in ? *reinterpret_cast<const float4*>(gx_in + (size_t)sl * kBM + a4)
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
         const size_t idx = (size_t)sl * t.n_pad + p0 + a4;
         so[k] = *reinterpret_cast<const float4*>(t.S + idx);
         if (FP8)
             sbw[k] = make_uint2(*reinterpret_cast<const uint32_t*>(t.S8 + idx), 0u);  // four E4M3
         else
             sbw[k] = *reinterpret_cast<const uint2*>(t.Sb + idx);  // four BF16
+    }
+    if (g_early) load_fields();
+    tc::pdl_wait();
+    tc::pdl_launch_dependents();
+    if (!g_early) load_fields();
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int e = tid + k * kChainWarps * 32;
+        const int rr = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
+        const int sl = slot0 + rr < t.R ? slot0 + rr : 0;
+        gx[k] = gx_in ? *reinterpret_cast<const float4*>(gx_in + (size_t)sl * kBM + a4)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
@@ -752,7 +774,7 @@ cudaError_t launch_tc_pair_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, 
 
 template <int RPW, bool NEXT, bool FP8>
 cudaError_t launch_chain_as(const TcState& t, int p, const float* G, const float* gx_in, float* gx_out,
-                            cudaStream_t st)
+                            int g_early, cudaStream_t st)
 {
     constexpr int smem = ChainSmem<RPW, NEXT>::kBytes;
     cudaError_t e = cudaFuncSetAttribute(panel_chain_kernel<RPW, NEXT, FP8>,
@@ -764,28 +786,29 @@ cudaError_t launch_chain_as(const TcState& t, int p, const float* G, const float
     const float* a0 = G;
     const float* a1 = gx_in;
     float* a2 = gx_out;
-    void* args[] = {&tt, &pp, &a0, &a1, &a2};
+    int ge = g_early;
+    void* args[] = {&tt, &pp, &a0, &a1, &a2, &ge};
     return launch_pdl((const void*)panel_chain_kernel<RPW, NEXT, FP8>, dim3((t.R + per_cta - 1) / per_cta),
                       dim3(kChainWarps * 32), args, smem, st);
 }
 
 template <bool FP8>
 cudaError_t launch_chain_lo(const TcState& t, int p, int rpw, bool next, const float* G, const float* gx_in,
-                            float* gx_out, cudaStream_t st)
+                            float* gx_out, int ge, cudaStream_t st)
 {
     switch (rpw * 2 + (next ? 1 : 0)) {
-    case 2: return launch_chain_as<1, false, FP8>(t, p, G, gx_in, gx_out, st);
-    case 3: return launch_chain_as<1, true, FP8>(t, p, G, gx_in, gx_out, st);
-    case 4: return launch_chain_as<2, false, FP8>(t, p, G, gx_in, gx_out, st);
-    case 5: return launch_chain_as<2, true, FP8>(t, p, G, gx_in, gx_out, st);
-    case 8: return launch_chain_as<4, false, FP8>(t, p, G, gx_in, gx_out, st);
-    case 9: return launch_chain_as<4, true, FP8>(t, p, G, gx_in, gx_out, st);
+    case 2: return launch_chain_as<1, false, FP8>(t, p, G, gx_in, gx_out, ge, st);
+    case 3: return launch_chain_as<1, true, FP8>(t, p, G, gx_in, gx_out, ge, st);
+    case 4: return launch_chain_as<2, false, FP8>(t, p, G, gx_in, gx_out, ge, st);
+    case 5: return launch_chain_as<2, true, FP8>(t, p, G, gx_in, gx_out, ge, st);
+    case 8: return launch_chain_as<4, false, FP8>(t, p, G, gx_in, gx_out, ge, st);
+    case 9: return launch_chain_as<4, true, FP8>(t, p, G, gx_in, gx_out, ge, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, const float* gx_in,
-                            float* gx_out, cudaStream_t st)
+                            float* gx_out, bool g_early, cudaStream_t st)
 {
     if (rpw != 1 && rpw != 2 && rpw != 4) return cudaErrorInvalidValue;
     if (t.splitk < 1 || t.splitk > kChainMaxSplit / rpw) return cudaErrorInvalidValue;
@@ -793,8 +816,8 @@ cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, co
     if (t.R_pad % (kChainWarps * rpw) != 0) return cudaErrorInvalidValue;
     const bool next = gx_out != nullptr;
     if (next && !t.Jsup) return cudaErrorInvalidValue;
-    return t.S8 ? launch_chain_lo<true>(t, p, rpw, next, G, gx_in, gx_out, st)
-                : launch_chain_lo<false>(t, p, rpw, next, G, gx_in, gx_out, st);
+    return t.S8 ? launch_chain_lo<true>(t, p, rpw, next, G, gx_in, gx_out, g_early ? 1 : 0, st)
+                : launch_chain_lo<false>(t, p, rpw, next, G, gx_in, gx_out, g_early ? 1 : 0, st);
 }
 
 cudaError_t launch_tc_init(const TcState& t, cudaStream_t st)

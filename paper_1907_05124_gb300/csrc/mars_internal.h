@@ -259,7 +259,7 @@ constexpr int kChainMaxSplit = 16;
 cudaError_t launch_tc_pair_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g, int n_tiles,
                                 int splitk, cudaStream_t st);
 cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, const float* gx_in,
-                            float* gx_out, cudaStream_t st);
+                            float* gx_out, bool g_early, cudaStream_t st);
 cudaError_t launch_tc_init(const TcState& t, cudaStream_t st);
 cudaError_t launch_tc_advance(const TcState& t, cudaStream_t st);
 cudaError_t launch_tc_prefix(const TcState& t, cudaStream_t st);

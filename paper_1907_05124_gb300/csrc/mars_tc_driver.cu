@@ -253,8 +253,12 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
                 MARS_CUDA(c, cudaEventRecord(c->prof[2 * e + 1], st));
                 run->timed_rows.push_back(two ? 256 : 128);
             }
-            MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[0], nullptr, two ? run->Gx[0] : nullptr, st));
-            if (two) MARS_CUDA(c, launch_tc_chain(tc, pp + 1, run->rpw, run->Gbuf[1], run->Gx[0], nullptr, st));
+            // chain pp's fields come from the GEMM just before it; chain pp+1's
+            // from the same GEMM, two kernels back
+            MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[0], nullptr, two ? run->Gx[0] : nullptr,
+                                         false, st));
+            if (two)
+                MARS_CUDA(c, launch_tc_chain(tc, pp + 1, run->rpw, run->Gbuf[1], run->Gx[0], nullptr, true, st));
         }
         MARS_CUDA(c, launch_tc_advance(run->t, st));
         return MARS_OK;
@@ -282,7 +286,9 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
         }
         const float* gx_in = ov && pp > 0 ? run->Gx[pp & 1] : nullptr;
         float* gx_out = ov && pp + 1 < P ? run->Gx[(pp + 1) & 1] : nullptr;
-        MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[pp & 1], gx_in, gx_out, st));
+        // overlapped: the GEMM ran on the side stream, complete (by its event)
+        // before the chain starts
+        MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[pp & 1], gx_in, gx_out, ov, st));
         if (ov) MARS_CUDA(c, cudaEventRecord(run->ev[2 + 2 * pp], st));
     }
     MARS_CUDA(c, launch_tc_advance(run->t, st));
