@@ -370,14 +370,15 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
     const int grp = lane / LPR, j = lane % LPR;
     const int r = warp * RPW + grp;
     const int slot = slot0 + r;
-    // Programmatic launch: this kernel may start while the stream's previous
-    // kernel still runs (that kernel released its dependents only after its
-    // own predecessor had completed). Everything but that kernel's output is
-    // read first: the instance's blocks, this panel's old spins, the level
-    // state (the level step runs between sweeps, before the sweep's first
-    // kernel) and, when `g_early`, the fields, whose GEMM is not the stream's
-    // previous kernel. The previous chain's next-panel fields (gx_in), and
-    // the fields when the GEMM is the previous kernel, come after the wait.
+    // Programmatic launch: this kernel may start while the kernels it
+    // depends on still run (each released its dependents only after its own
+    // predecessors had completed). What those kernels do not write is read
+    // first: the instance's blocks, this panel's old spins, the level state
+    // (the level step runs between sweeps, before the sweep's first kernel)
+    // and, when `g_early`, the fields, whose GEMM completed before the
+    // previous chain released this one (the second panel of a pair). The
+    // previous chain's next-panel fields (gx_in), and otherwise the fields,
+    // come after the wait.
     if (tid == 0) {
         tc::mbar_init(bar, 1);
         tc::fence_barrier_init();

@@ -286,9 +286,9 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
         }
         const float* gx_in = ov && pp > 0 ? run->Gx[pp & 1] : nullptr;
         float* gx_out = ov && pp + 1 < P ? run->Gx[(pp + 1) & 1] : nullptr;
-        // overlapped: the GEMM ran on the side stream, complete (by its event)
-        // before the chain starts
-        MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[pp & 1], gx_in, gx_out, ov, st));
+        // the GEMM's event edge into the chain may be captured as a
+        // programmatic edge too, so its fields are read after the wait
+        MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[pp & 1], gx_in, gx_out, false, st));
         if (ov) MARS_CUDA(c, cudaEventRecord(run->ev[2 + 2 * pp], st));
     }
     MARS_CUDA(c, launch_tc_advance(run->t, st));

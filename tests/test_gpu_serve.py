@@ -58,9 +58,12 @@ def test_mixed_requests_match_blocking_solves(ctx):
     insts["sk"] = ctx.add_dense(sk)
     gauss = I.sk_gauss(256, 6)
     insts["sk_bf16"] = ctx.add_dense(gauss)
+    big = I.sk_gauss(4096, 7)  # a tensor-core request at N = 4096 in the mix
+    insts["sk4096_bf16"] = ctx.add_dense(big)
     plan = [("lat", 200, 4.0, {}), ("er", 64, 6.0, {}), ("sk", 128, 20.0, {}),
             ("er_one", 96, 10.0, {}), ("lat3", 50, 5.0, {}), ("lat", 33, 4.0, {}),
-            ("sk_bf16", 64, 2.0, {"precision": "bf16", "c_step": 1 / 16.0}), ("er", 7, 6.0, {})]
+            ("sk_bf16", 64, 2.0, {"precision": "bf16", "c_step": 1 / 16.0}), ("er", 7, 6.0, {}),
+            ("sk4096_bf16", 96, 0.4, {"precision": "bf16", "c_step": 1 / 64.0})]
     ctx.serve_limits(4)  # fewer slots than requests: some wait for a slot
     reqs = []
     for j, (k, R, tmax, kw) in enumerate(plan):
@@ -74,6 +77,8 @@ def test_mixed_requests_match_blocking_solves(ctx):
     assert r0.best_energy == O.energy(O.Instance.csr(graphs["lat"]), r0.best_spins)
     r6 = served[reqs[6]]
     assert r6.best_energy == O.energy(O.Instance.dense(gauss), r6.best_spins)
+    r8 = served[reqs[8]]
+    assert r8.best_energy == O.energy(O.Instance.dense(big), r8.best_spins)
     assert ctx.serve_status() == (0, 0)
     for i in insts.values():
         ctx.free(i)
