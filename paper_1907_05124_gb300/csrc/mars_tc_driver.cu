@@ -90,7 +90,8 @@ int tc_plan(mars_ctx* c, TcRun* run, int32_t active, int32_t prefix)
     const int tiles = (slots + kTcBN - 1) / kTcBN;
     int splitk = 1;
     const int split_max = env_flag("MARS_TC_SPLITK_MAX", 16);
-    while (splitk < split_max && splitk * 2 <= kChainMaxSplit / rpw && tiles * splitk * 2 <= run->sms &&
+    const int wave = env_flag("MARS_TC_WAVE_PCT", 100) * run->sms / 100;  // CTAs one GEMM may use
+    while (splitk < split_max && splitk * 2 <= kChainMaxSplit / rpw && tiles * splitk * 2 <= wave &&
            run->kblocks_total % (splitk * 2) == 0)
         splitk *= 2;
     const int chain_slots = std::min(tiles * kTcBN, run->t.R);  // the chains cover [0, chain_slots)
