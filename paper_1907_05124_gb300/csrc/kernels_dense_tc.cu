@@ -66,17 +66,108 @@ struct GemmSmem {
     static constexpr size_t kBytes = 1024 + kStages * (kA + kB) + (2 * kStages + 1) * 8 + 16;
 };
 
-// G_part[split][slot][a] = sum over this split's K range of J[p0 + a][k] S[slot][k].
-// FP8: E4M3 operands (kind::f8f6f4); a stage's 128-byte rows then hold 128
-// K values instead of 64, and a 128-spin panel is one K block instead of two.
+// One (tile, split) item of a panel GEMM, on the CTA's warps 0..3:
+// G_part[split][slot][a] = sum over this split's K range of J[p0 + a][k] S[slot][k]
+// for the BN replica slots from n0. Warp 0's lane 0 is the TMA producer, warp
+// 1's lane 0 issues the MMAs (accumulator in TMEM), and warps 0..3 run the
+// epilogue (TMEM lane = panel row); other warps only count. `it` is the
+// number of stage-ring uses before this item (its phases continue across
+// items) and `commits` the number of earlier items that issued MMAs (the done
+// barrier's phase). Returns the stage uses after this item; *committed says
+// whether it issued MMAs. A split whose K blocks were all left out writes
+// zeros. FP8: E4M3 operands (kind::f8f6f4); a stage's 128-byte rows then hold
+// 128 K values instead of 64, and a 128-spin panel is one K block instead of two.
+template <int BN, bool FP8>
+__device__ __forceinline__ int gemm_item(const CUtensorMap* tmJ, const CUtensorMap* tmS, const TcPanel& g,
+                                         int n0, int split, unsigned char* sA, unsigned char* sB,
+                                         uint64_t* full, uint64_t* empty, uint64_t* done, uint32_t tmem,
+                                         int it0, int commits, bool* committed)
+{
+    using L = GemmSmem<BN>;
+    constexpr int kKE = FP8 ? 2 * kBK : kBK;  // K values per stage
+    constexpr int kSkipN = kBM / kKE;         // K blocks of one panel
+    const int kb0 = split * g.kblocks;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // K blocks [skip_kb, skip_kb + kSkipN), one 128-spin panel, may be left
+    // out; every thread counts the blocks this split keeps.
+    auto skipped = [&](int kb) {
+        return g.skip_kb >= 0 && kb0 + kb >= g.skip_kb && kb0 + kb < g.skip_kb + kSkipN;
+    };
+    int issued = 0;
+    for (int kb = 0; kb < g.kblocks; ++kb) issued += skipped(kb) ? 0 : 1;
+
+    if (issued > 0 && warp == 0 && lane == 0) {
+        // TMA producer: stage s is free once the MMAs that read it completed.
+        int it = it0;
+        for (int kb = 0; kb < g.kblocks; ++kb) {
+            if (skipped(kb)) continue;
+            const int s = it % kStages;
+            if (it >= kStages && !tc::mbar_wait(&empty[s], ((it / kStages) - 1) & 1, g.err)) break;
+            tc::mbar_arrive_expect_tx(&full[s], L::kA + L::kB);
+            tc::tma_load_2d(sA + s * L::kA, tmJ, &full[s], (kb0 + kb) * kKE, g.p0);
+            tc::tma_load_2d(sB + s * L::kB, tmS, &full[s], (kb0 + kb) * kKE, n0);
+            ++it;
+        }
+    } else if (issued > 0 && warp == 1 && lane == 0) {
+        // MMA issuer: four 32-byte K steps per stage (K = 16 BF16 or 32 E4M3),
+        // accumulator in TMEM; the item's first MMA overwrites it.
+        constexpr uint32_t idesc = FP8 ? tc::idesc_e4m3_f32(kBM, BN) : tc::idesc_bf16_f32(kBM, BN);
+        int it = it0;
+        for (int kb = 0; kb < g.kblocks; ++kb) {
+            if (skipped(kb)) continue;
+            const int s = it % kStages;
+            if (!tc::mbar_wait(&full[s], (it / kStages) & 1, g.err)) break;
+            tc::tc_fence_after();
+            const uint32_t a0 = tc::smem_addr(sA + s * L::kA), b0 = tc::smem_addr(sB + s * L::kB);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t acc = ((it - it0) | k) != 0;
+                if (FP8)
+                    tc::mma_e4m3(tmem, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
+                                 idesc, acc);
+                else
+                    tc::mma_bf16(tmem, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
+                                 idesc, acc);
+            }
+            tc::mma_commit(&empty[s]);
+            ++it;
+        }
+        tc::mma_commit(done);
+    }
+    __syncwarp();
+
+    if (warp < 4) {
+        const bool ok = issued > 0 ? tc::mbar_wait(done, (uint32_t)commits & 1u, g.err) : true;
+        tc::tc_fence_after();
+        const int row = warp * 32 + lane;
+        float* dst = g.G + ((size_t)split * g.R_pad + n0) * kBM + row;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            if (issued > 0) {
+                tc::tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.f;
+            }
+            if (ok) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) dst[(size_t)(c0 + j) * kBM] = v[j];
+            }
+        }
+    }
+    *committed = issued > 0;
+    return it0 + issued;
+}
+
+// The panel GEMM as its own launch: a grid of (replica tile, split) items
+// over the active prefix.
 template <int BN, bool FP8>
 __global__ void __launch_bounds__(128, 1)
     panel_gemm_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmS,
                       TcPanel g)
 {
     using L = GemmSmem<BN>;
-    constexpr int kKE = FP8 ? 2 * kBK : kBK;  // K values per stage
-    constexpr int kSkipN = kBM / kKE;         // K blocks of one panel
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
@@ -90,17 +181,7 @@ __global__ void __launch_bounds__(128, 1)
     tc::pdl_launch_dependents();
     const int n0 = blockIdx.x * BN;
     if (n0 >= *g.active_prefix) return;  // whole CTA, before any barrier
-    const int split = blockIdx.y;
-    const int kb0 = split * g.kblocks;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // K blocks [skip_kb, skip_kb + 2), one 128-spin panel, may be left out;
-    // every thread counts the blocks this split keeps.
-    auto skipped = [&](int kb) {
-        return g.skip_kb >= 0 && kb0 + kb >= g.skip_kb && kb0 + kb < g.skip_kb + kSkipN;
-    };
-    int issued = 0;
-    for (int kb = 0; kb < g.kblocks; ++kb) issued += skipped(kb) ? 0 : 1;
-
+    const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(&full[s], 1);
@@ -116,66 +197,8 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-
-    if (issued > 0 && warp == 0 && lane == 0) {
-        // TMA producer: stage s is free once the MMAs that read it completed.
-        int it = 0;
-        for (int kb = 0; kb < g.kblocks; ++kb) {
-            if (skipped(kb)) continue;
-            const int s = it % kStages;
-            if (it >= kStages && !tc::mbar_wait(&empty[s], ((it / kStages) - 1) & 1, g.err)) break;
-            tc::mbar_arrive_expect_tx(&full[s], L::kA + L::kB);
-            tc::tma_load_2d(sA + s * L::kA, &tmJ, &full[s], (kb0 + kb) * kKE, g.p0);
-            tc::tma_load_2d(sB + s * L::kB, &tmS, &full[s], (kb0 + kb) * kKE, n0);
-            ++it;
-        }
-    } else if (issued > 0 && warp == 1 && lane == 0) {
-        // MMA issuer: four 32-byte K steps per stage (K = 16 BF16 or 32 E4M3),
-        // accumulator in TMEM.
-        constexpr uint32_t idesc = FP8 ? tc::idesc_e4m3_f32(kBM, BN) : tc::idesc_bf16_f32(kBM, BN);
-        int it = 0;
-        for (int kb = 0; kb < g.kblocks; ++kb) {
-            if (skipped(kb)) continue;
-            const int s = it % kStages;
-            if (!tc::mbar_wait(&full[s], (it / kStages) & 1, g.err)) break;
-            tc::tc_fence_after();
-            const uint32_t a0 = tc::smem_addr(sA + s * L::kA), b0 = tc::smem_addr(sB + s * L::kB);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (FP8)
-                    tc::mma_e4m3(tmem, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
-                                 idesc, (it | k) != 0);
-                else
-                    tc::mma_bf16(tmem, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
-                                 idesc, (it | k) != 0);
-            }
-            tc::mma_commit(&empty[s]);
-            ++it;
-        }
-        tc::mma_commit(done);
-    }
-    __syncwarp();
-
-    // Epilogue: TMEM lane = panel row, columns = replica slots. A split
-    // whose K blocks were all left out writes zeros and waits for nothing.
-    const bool ok = issued > 0 ? tc::mbar_wait(done, 0, g.err) : true;
-    tc::tc_fence_after();
-    const int row = warp * 32 + lane;
-    float* dst = g.G + ((size_t)split * g.R_pad + n0) * kBM + row;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-        float v[32];
-        if (issued > 0) {
-            tc::tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = 0.f;
-        }
-        if (ok) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) dst[(size_t)(c0 + j) * kBM] = v[j];
-        }
-    }
+    bool committed;
+    gemm_item<BN, FP8>(&tmJ, &tmS, g, n0, blockIdx.y, sA, sB, full, empty, done, tmem, 0, 0, &committed);
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, BN);
@@ -350,42 +373,33 @@ struct ChainSmem {
 // could run beside this chain; each new s_a goes into the next panel's
 // fields here instead, in FP32 (gx_out), from the block J[p][p+1]. Lane j
 // owns next-panel spins 4 (32/RPW) u + 4 j + i, read as float4.
+// The chain of panel p for the RPC = kChainWarps * RPW replica slots from
+// slot0, on the CTA's first kChainWarps warps. Jb (and Jn when NEXT) hold the
+// panel's blocks once `bar` completes its phase of parity `parity`; the caller
+// issued their copies. With `pdl` the function orders itself after the
+// stream's previous kernel (griddepcontrol) between the loads that kernel
+// does not write and those it does. *s_ok is a shared word.
 template <int RPW, bool NEXT, bool FP8>
-__global__ void __launch_bounds__(kChainWarps * 32, 1)
-    panel_chain_kernel(TcState t, int p, const float* __restrict__ G, const float* __restrict__ gx_in,
-                       float* __restrict__ gx_out, int g_early)
+__device__ __forceinline__ void chain_body(const TcState& t, int p, const float* __restrict__ G,
+                                           const float* __restrict__ gx_in, float* __restrict__ gx_out,
+                                           bool g_early, bool pdl, int slot0, const float* Jb, const float* Jn,
+                                           ChainSpin* cs_all, uint64_t* bar, uint32_t parity, int* s_ok)
 {
-    using L = ChainSmem<RPW, NEXT>;
     constexpr int LPR = 32 / RPW, SPL = kBM / LPR, RPC = kChainWarps * RPW;
     constexpr int kSplitCap = kChainMaxSplit / RPW;
-    extern __shared__ __align__(16) unsigned char chain_smem[];
-    float* Jb = reinterpret_cast<float*>(chain_smem);  // J[p][p] (symmetric)
-    float* Jn = Jb + kBM * kBM;                         // NEXT: J[p][p+1], row a = this panel's spin
-    ChainSpin* cs_all = reinterpret_cast<ChainSpin*>(chain_smem + L::kBlocks * L::kJ);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(chain_smem + L::kBlocks * L::kJ + L::kCs);
-    __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int slot0 = blockIdx.x * RPC;
     const int p0 = p * kBM;
     const int grp = lane / LPR, j = lane % LPR;
     const int r = warp * RPW + grp;
     const int slot = slot0 + r;
-    // Programmatic launch: this kernel may start while the kernels it
-    // depends on still run (each released its dependents only after its own
+    // Programmatic launch: the kernel may start while the kernels it depends
+    // on still run (each released its dependents only after its own
     // predecessors had completed). What those kernels do not write is read
-    // first: the instance's blocks, this panel's old spins, the level state
-    // (the level step runs between sweeps, before the sweep's first kernel)
-    // and, when `g_early`, the fields, whose GEMM completed before the
-    // previous chain released this one (the second panel of a pair). The
-    // previous chain's next-panel fields (gx_in), and otherwise the fields,
-    // come after the wait.
-    if (tid == 0) {
-        tc::mbar_init(bar, 1);
-        tc::fence_barrier_init();
-        tc::mbar_arrive_expect_tx(bar, L::kBlocks * L::kJ);
-        tc::bulk_load(Jb, t.Jdiag + (size_t)p * kBM * kBM, L::kJ, bar);
-        if (NEXT) tc::bulk_load(Jn, t.Jsup + (size_t)p * kBM * kBM, L::kJ, bar);
-    }
+    // first: this panel's old spins, the level state (the level step runs
+    // between sweeps, before the sweep's first kernel) and, when `g_early`,
+    // the fields, whose GEMM completed before the previous chain released
+    // this one (the second panel of a pair). The previous chain's next-panel
+    // fields (gx_in), and otherwise the fields, come after the wait.
     const bool valid = slot < t.R && t.active[slot];
     const float invT = valid ? t.invT[slot] : 0.f;  // idle groups compute and store nothing
     // RPC replicas x 32 four-spin pieces = RPW pieces per thread.
@@ -418,8 +432,10 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
             sbw[k] = *reinterpret_cast<const uint2*>(t.Sb + idx);  // four BF16
     }
     if (g_early) load_fields();
-    tc::pdl_wait();
-    tc::pdl_launch_dependents();
+    if (pdl) {
+        tc::pdl_wait();
+        tc::pdl_launch_dependents();
+    }
     if (!g_early) load_fields();
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
@@ -476,9 +492,9 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
         d[2] = ChainSpin{f.z, so[k].z, lo[2], 0.f};
         d[3] = ChainSpin{f.w, so[k].w, lo[3], 0.f};
     }
-    if (tid == 0) s_ok = tc::mbar_wait(bar, 0, t.counters + 2) ? 1 : 0;
+    if (tid == 0) *s_ok = tc::mbar_wait(bar, parity, t.counters + 2) ? 1 : 0;
     __syncthreads();
-    if (!s_ok) return;  // the error flag is set; the host reports it
+    if (!*s_ok) return;  // the error flag is set; the host reports it
     if (!__any_sync(0xffffffffu, valid)) return;  // the whole warp idle
     const ChainSpin* cs = cs_all + r * kBM;
     float g[SPL], sf[SPL], gn[NEXT ? SPL : 1];
@@ -574,6 +590,32 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
     if (j == 0) t.d[slot] = fmaxf(t.d[slot], dloc);
 }
 
+// The chain as its own launch, one CTA per RPC replica slots. Thread 0 starts
+// the copies of the panel's blocks (instance data, independent of the
+// previous kernels) before chain_body's programmatic wait.
+template <int RPW, bool NEXT, bool FP8>
+__global__ void __launch_bounds__(kChainWarps * 32, 1)
+    panel_chain_kernel(TcState t, int p, const float* __restrict__ G, const float* __restrict__ gx_in,
+                       float* __restrict__ gx_out, int g_early)
+{
+    using L = ChainSmem<RPW, NEXT>;
+    extern __shared__ __align__(16) unsigned char chain_smem[];
+    float* Jb = reinterpret_cast<float*>(chain_smem);  // J[p][p] (symmetric)
+    float* Jn = Jb + kBM * kBM;                         // NEXT: J[p][p+1], row a = this panel's spin
+    ChainSpin* cs_all = reinterpret_cast<ChainSpin*>(chain_smem + L::kBlocks * L::kJ);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(chain_smem + L::kBlocks * L::kJ + L::kCs);
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_barrier_init();
+        tc::mbar_arrive_expect_tx(bar, L::kBlocks * L::kJ);
+        tc::bulk_load(Jb, t.Jdiag + (size_t)p * kBM * kBM, L::kJ, bar);
+        if (NEXT) tc::bulk_load(Jn, t.Jsup + (size_t)p * kBM * kBM, L::kJ, bar);
+    }
+    chain_body<RPW, NEXT, FP8>(t, p, G, gx_in, gx_out, g_early != 0, true, blockIdx.x * (kChainWarps * RPW), Jb,
+                               Jn, cs_all, bar, 0u, &s_ok);
+}
+
 // Start states in slot order: slot j holds replica rep[j].
 __global__ void tc_init_kernel(TcState t)
 {
@@ -608,31 +650,243 @@ __global__ void tc_init_kernel(TcState t)
 }
 
 // End of a sweep: the stopping rule and the level schedule per slot.
+// The stopping rule and the level schedule of one active slot after a sweep.
+__device__ __forceinline__ void advance_slot(const TcState& t, int slot)
+{
+    if (!t.active[slot]) return;
+    const float dd = t.d[slot];
+    t.d[slot] = 0.f;
+    const int ls = t.lvl_sweeps[slot] + 1;
+    t.sweeps[slot] += 1;
+    double T = t.T[slot];
+    const bool fixed = sched_fixed(t, T);
+    const bool level_done = fixed ? ls >= t.fixed_sweeps : (dd <= t.d_min || ls >= t.k_max);
+    if (level_done) {
+        if (!fixed && !(dd <= t.d_min)) t.capped[slot] += 1;
+        t.lvl_sweeps[slot] = 0;
+        if (sched_advance(t, &T)) {
+            t.T[slot] = T;
+            t.levels[slot] += 1;
+            t.invT[slot] = sched_inv_t(T);
+        } else {
+            t.active[slot] = 0;
+        }
+    } else {
+        t.lvl_sweeps[slot] = ls;
+    }
+}
+
 __global__ void tc_advance_kernel(TcState t)
 {
-    for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < t.R; slot += gridDim.x * blockDim.x) {
-        if (!t.active[slot]) continue;
-        const float dd = t.d[slot];
-        t.d[slot] = 0.f;
-        const int ls = t.lvl_sweeps[slot] + 1;
-        t.sweeps[slot] += 1;
-        double T = t.T[slot];
-        const bool fixed = sched_fixed(t, T);
-        const bool level_done = fixed ? ls >= t.fixed_sweeps : (dd <= t.d_min || ls >= t.k_max);
-        if (level_done) {
-            if (!fixed && !(dd <= t.d_min)) t.capped[slot] += 1;
-            t.lvl_sweeps[slot] = 0;
-            if (sched_advance(t, &T)) {
-                t.T[slot] = T;
-                t.levels[slot] += 1;
-                t.invT[slot] = sched_inv_t(T);
-            } else {
-                t.active[slot] = 0;
+    for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < t.R; slot += gridDim.x * blockDim.x)
+        advance_slot(t, slot);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent sweeps for a partly active solve.
+//
+// Once fewer replicas are active than fill the GPU, a sweep is bound by its 64
+// dependent panels (N = 8192) and, with one launch per GEMM and per chain, by
+// the kernel boundaries between them. This kernel runs a whole batch of
+// sweeps in one cooperative launch instead. Its first n_chain CTAs each own
+// replica groups of kChainWarps * RPW slots and run their chains panel after
+// panel; the other n_gemm CTAs run the panel GEMMs' (tile, split) items. The
+// schedule is the overlap's: panel p's GEMM leaves panel p-1's K range out,
+// so it needs the chains up to panel p-2 only, and chain p-1 supplies panel
+// p-1's part of panel p's fields in FP32. The roles meet through two
+// monotonic counters per panel of the batch (s = sweep * P + p):
+//   gemm_done[s]  GEMM CTAs that finished their items of panel s (the chains
+//                 of panel s wait for n_gemm);
+//   chain_done[s] chain CTAs that finished panel s (panel s+2's GEMM waits
+//                 for n_chain; a sweep's first panel, which leaves nothing
+//                 out, waits for the previous sweep's last chain).
+// Each role handles the panels in order, so every wait is for work that an
+// earlier panel's waits did not depend on, and the cooperative launch keeps
+// every CTA resident: the waits end. Each wait is bounded (a clock64 budget):
+// on a timeout the CTA records the error, raises the shared abort word that
+// every wait also watches, lets its copies in flight land and returns.
+// ---------------------------------------------------------------------------
+struct PersistSmem {
+    static constexpr size_t kGemm = GemmSmem<128>::kBytes;
+    template <int RPW>
+    static constexpr size_t bytes()
+    {
+        return ChainSmem<RPW, true>::kBytes > kGemm ? (size_t)ChainSmem<RPW, true>::kBytes : kGemm;
+    }
+};
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Thread 0 waits until *ctr >= target (acquire), giving up after the budget
+// or when another CTA raised the abort word; the CTA learns the outcome.
+__device__ bool wait_count(const int32_t* ctr, int32_t target, const TcPersist& pp, int32_t* err, int* s_flag)
+{
+    if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        int ok = 0;
+        for (;;) {
+            if (ld_acquire(ctr) >= target) { ok = 1; break; }
+            if (*(volatile int32_t*)pp.abort) break;
+            if (clock64() - t0 > pp.spin_budget) {
+                atomicExch(err, tc::kErrTimeout);
+                atomicExch(pp.abort, 1);
+                break;
             }
-        } else {
-            t.lvl_sweeps[slot] = ls;
+            __nanosleep(40);
+        }
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// Publishes this CTA's completion of a panel: its writes (made visible to
+// the tensor maps' async proxy too) before the counter's increment.
+__device__ __forceinline__ void publish(int32_t* ctr)
+{
+    fence_proxy_async_global();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1);
+    }
+}
+
+template <int RPW, bool FP8>
+__global__ void __launch_bounds__(kChainWarps * 32, 1)
+    tc_sweeps_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmS, TcState t,
+                     TcPanel g, TcPersist pp)
+{
+    extern __shared__ __align__(1024) unsigned char psm[];
+    __shared__ int s_flag;
+    const int P = pp.P;
+    int32_t* err = t.counters + 2;
+    if (blockIdx.x < pp.n_chain) {
+        // ---- chain role --------------------------------------------------
+        using L = ChainSmem<RPW, true>;
+        constexpr int RPC = kChainWarps * RPW;
+        float* Jb = reinterpret_cast<float*>(psm);
+        float* Jn = Jb + kBM * kBM;
+        ChainSpin* cs_all = reinterpret_cast<ChainSpin*>(psm + L::kBlocks * L::kJ);
+        uint64_t* bar = reinterpret_cast<uint64_t*>(psm + L::kBlocks * L::kJ + L::kCs);
+        auto load_blocks = [&](int p) {
+            tc::mbar_arrive_expect_tx(bar, L::kBlocks * L::kJ);
+            tc::bulk_load(Jb, t.Jdiag + (size_t)p * kBM * kBM, L::kJ, bar);
+            tc::bulk_load(Jn, t.Jsup + (size_t)p * kBM * kBM, L::kJ, bar);
+        };
+        if (threadIdx.x == 0) {
+            tc::mbar_init(bar, 1);
+            tc::fence_barrier_init();
+            load_blocks(0);
+        }
+        __syncthreads();
+        uint32_t loads = 1;  // block copies issued; the current one has parity (loads - 1) & 1
+        bool failed = false;
+        for (int w = 0; w < pp.sweeps && !failed; ++w) {
+            for (int p = 0; p < P; ++p) {
+                const int sidx = w * P + p;
+                if (!wait_count(pp.gemm_done + sidx, pp.n_gemm, pp, err, &s_flag)) { failed = true; break; }
+                for (int item = blockIdx.x; item < pp.chain_items; item += pp.n_chain) {
+                    chain_body<RPW, true, FP8>(t, p, pp.G[sidx & 1], p > 0 ? pp.Gx[p & 1] : nullptr,
+                                               p + 1 < P ? pp.Gx[(p + 1) & 1] : nullptr, true, false, item * RPC,
+                                               Jb, Jn, cs_all, bar, (loads - 1) & 1u, &s_flag);
+                    __syncthreads();
+                    if (!s_flag) {
+                        if (threadIdx.x == 0) atomicExch(pp.abort, 1);
+                        failed = true;
+                        break;
+                    }
+                }
+                if (failed) break;
+                if (p == P - 1) {
+                    // the sweep's end for this CTA's slots: stopping rule and levels
+                    for (int item = blockIdx.x; item < pp.chain_items; item += pp.n_chain)
+                        for (int q = threadIdx.x; q < RPC; q += blockDim.x)
+                            if (item * RPC + q < t.R) advance_slot(t, item * RPC + q);
+                }
+                __syncthreads();
+                // the loops no longer read the blocks: copy the next panel's
+                if (threadIdx.x == 0 && (w + 1 < pp.sweeps || p + 1 < P)) {
+                    load_blocks(p + 1 < P ? p + 1 : 0);
+                    ++loads;
+                }
+                publish(pp.chain_done + sidx);
+            }
+        }
+        // a copy in flight lands before the CTA leaves
+        if (threadIdx.x == 0) tc::mbar_wait(bar, (loads - 1) & 1u, err);
+        __syncthreads();
+        return;
+    }
+    // ---- GEMM role ---------------------------------------------------------
+    using G = GemmSmem<128>;
+    unsigned char* smem = (unsigned char*)(((uintptr_t)psm + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + kStages * G::kA;
+    uint64_t* full = (uint64_t*)(sB + kStages * G::kB);
+    uint64_t* empty = full + kStages;
+    uint64_t* done = empty + kStages;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kStages; ++q) {
+            tc::mbar_init(&full[q], 1);
+            tc::mbar_init(&empty[q], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_barrier_init();
+        tc::tma_prefetch_desc(&tmJ);
+        tc::tma_prefetch_desc(&tmS);
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, 128);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int kb_panel = g.fp8 ? 1 : 2;
+    const int items = pp.gemm_tiles * pp.splitk;
+    int it = 0, commits = 0;
+    bool failed = false;
+    for (int w = 0; w < pp.sweeps && !failed; ++w) {
+        for (int p = 0; p < P; ++p) {
+            const int sidx = w * P + p;
+            // spins of every panel this GEMM reads: up to p-2 (panel p-1 is
+            // left out), or up to the previous sweep's last panel for p = 0
+            const int need = p == 0 ? sidx - 1 : sidx - 2;
+            if (need >= 0 && !wait_count(pp.chain_done + need, pp.n_chain, pp, err, &s_flag)) {
+                failed = true;
+                break;
+            }
+            if (threadIdx.x == 0) fence_proxy_async_global();  // the chains' BF16 spins, for the TMA
+            TcPanel gp = g;
+            gp.p0 = p * kBM;
+            gp.G = pp.G[sidx & 1];
+            gp.skip_kb = p > 0 ? kb_panel * (p - 1) : -1;
+            for (int item = blockIdx.x - pp.n_chain; item < items; item += pp.n_gemm) {
+                bool committed = false;
+                it = gemm_item<128, FP8>(&tmJ, &tmS, gp, (item / pp.splitk) * 128, item % pp.splitk, sA, sB, full,
+                                         empty, done, tmem, it, commits, &committed);
+                commits += committed ? 1 : 0;
+                tc::tc_fence_before();
+                __syncthreads();
+                tc::tc_fence_after();
+            }
+            publish(pp.gemm_done + sidx);
         }
     }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
 
 // Active prefix (one past the last active slot) and active count.
@@ -825,6 +1079,41 @@ cudaError_t launch_tc_init(const TcState& t, cudaStream_t st)
 {
     tc_init_kernel<<<1024, 256, 0, st>>>(t);
     return cudaGetLastError();
+}
+
+size_t tc_sweeps_smem(int rpw)
+{
+    return rpw == 1 ? PersistSmem::bytes<1>() : rpw == 2 ? PersistSmem::bytes<2>() : PersistSmem::bytes<4>();
+}
+
+template <int RPW, bool FP8>
+cudaError_t launch_sweeps_as(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcState& t, const TcPanel& g,
+                             const TcPersist& pp, cudaStream_t st)
+{
+    const void* k = (const void*)tc_sweeps_kernel<RPW, FP8>;
+    const size_t smem = PersistSmem::bytes<RPW>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    CUtensorMap a = tmJ, b = tmS;
+    TcState c = t;
+    TcPanel d = g;
+    TcPersist q = pp;
+    void* args[] = {&a, &b, &c, &d, &q};
+    return cudaLaunchCooperativeKernel(k, dim3(pp.n_chain + pp.n_gemm), dim3(kChainWarps * 32), args, smem, st);
+}
+
+cudaError_t launch_tc_sweeps(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcState& t, const TcPanel& g,
+                             const TcPersist& pp, int rpw, cudaStream_t st)
+{
+    if (pp.n_chain < 1 || pp.n_gemm < 1 || pp.sweeps < 1 || pp.splitk < 1 || pp.splitk > kChainMaxSplit / rpw)
+        return cudaErrorInvalidValue;
+    const bool fp8 = g.fp8 != 0;
+    switch (rpw) {
+    case 1: return fp8 ? launch_sweeps_as<1, true>(tmJ, tmS, t, g, pp, st) : launch_sweeps_as<1, false>(tmJ, tmS, t, g, pp, st);
+    case 2: return fp8 ? launch_sweeps_as<2, true>(tmJ, tmS, t, g, pp, st) : launch_sweeps_as<2, false>(tmJ, tmS, t, g, pp, st);
+    case 4: return fp8 ? launch_sweeps_as<4, true>(tmJ, tmS, t, g, pp, st) : launch_sweeps_as<4, false>(tmJ, tmS, t, g, pp, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tc_advance(const TcState& t, cudaStream_t st)

@@ -197,6 +197,12 @@ struct TcRun {
     int fixed_rpw = -1, fixed_overlap = -1, fixed_pair = -1;
     int chain_slots = 0, gemm_tiles = 0;
     int sms = 0, kblocks_total = 0;
+    // Persistent batches (tc_sweeps_kernel) for a partly active solve: the
+    // launch's shape and its counters (2 x kMaxBatch x P + 1 words).
+    bool persist = false;
+    bool allow_persist = false;        // blocking solves only (not served requests)
+    TcPersist pp;
+    int32_t* flags = nullptr;
     ~TcRun()
     {
         if (exec) cudaGraphExecDestroy(exec);
@@ -208,6 +214,8 @@ struct TcRun {
 
 // Replicas per GEMM tile of the tensor-core path (the MMA's N).
 constexpr int kTcBN = 128;
+// Most sweeps one batch (one graph replay series or one persistent launch) runs.
+constexpr int kTcMaxBatch = 32;
 
 // Allocator the tensor-core set-up draws its buffers from.
 using TcGet = std::function<int(size_t, void**)>;

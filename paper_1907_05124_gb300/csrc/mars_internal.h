@@ -244,6 +244,23 @@ struct TcState {
     int32_t* capped = nullptr;
     int32_t* counters = nullptr;       // [0] active prefix, [1] active count, [2] error
 };
+// A batch of sweeps in one cooperative launch (tc_sweeps_kernel): n_chain
+// chain CTAs, then n_gemm GEMM CTAs, meeting through per-panel counters.
+struct TcPersist {
+    int32_t n_chain = 0, n_gemm = 0;
+    int32_t chain_items = 0;           // replica groups of 8 * rpw slots below the prefix
+    int32_t gemm_tiles = 0, splitk = 1;
+    int32_t sweeps = 0, P = 0;
+    float* G[2] = {nullptr, nullptr};  // split-K partials by panel parity
+    float* Gx[2] = {nullptr, nullptr}; // the previous panel's FP32 part of the fields
+    int32_t* gemm_done = nullptr;      // [sweeps * P], zero at launch
+    int32_t* chain_done = nullptr;     // [sweeps * P], zero at launch
+    int32_t* abort = nullptr;          // zero at launch
+    long long spin_budget = 0;         // clock64 cycles one wait may take
+};
+size_t tc_sweeps_smem(int rpw);
+cudaError_t launch_tc_sweeps(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcState& t, const TcPanel& g,
+                             const TcPersist& pp, int rpw, cudaStream_t st);
 size_t tc_gemm_smem(int bn);
 cudaError_t launch_tc_panel_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g,
                                  int bn, int n_tiles, int splitk, cudaStream_t st);

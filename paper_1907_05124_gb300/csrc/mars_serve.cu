@@ -221,6 +221,7 @@ size_t serve_footprint(const DevInstance& d, const mars_params& p, int device)
         b += 2 * (size_t)kChainMaxSplit * Rp * 128 * 4;             // split-K partials, two buffers
         b += 2 * Rp * 128 * 4;                                      // next-panel fields
         b += R * (8 + 4 + 4 + 5 * 4) + 16;                          // per-slot state, counters
+        b += (2 * (size_t)kTcMaxBatch * (np / 128) + 1) * 4;        // persistent batches' counters
     } else if (d.dense) {
         const DensePlan dp = plan_dense(d, (int)R, jacobi ? 1 : 0, device);
         b += dp.scratch_floats * sizeof(float);

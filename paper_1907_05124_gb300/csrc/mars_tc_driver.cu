@@ -95,6 +95,52 @@ int tc_plan(mars_ctx* c, TcRun* run, int32_t active, int32_t prefix)
            run->kblocks_total % (splitk * 2) == 0)
         splitk *= 2;
     const int chain_slots = std::min(tiles * kTcBN, run->t.R);  // the chains cover [0, chain_slots)
+    // Persistent batches once the active replicas leave SMs free: chain CTAs
+    // for every replica group (one group each) beside GEMM CTAs for the
+    // panel's (tile, split) items, all resident (measured on a GB300 at
+    // N = 8192 against the launched sweeps above).
+    if (run->adaptive && run->allow_persist && run->P >= 2 && A <= env_flag("MARS_TC_PERSIST_MAX", 2048) &&
+        run->flags) {
+        const int prpw = A <= 512 ? 1 : A <= 1024 ? 2 : 4;
+        TcPersist q;
+        q.chain_items = (chain_slots + 8 * prpw - 1) / (8 * prpw);
+        q.n_chain = std::min(q.chain_items, run->sms - 16);
+        q.gemm_tiles = tiles;
+        q.splitk = 1;
+        while (q.splitk * 2 <= kChainMaxSplit / prpw && tiles * q.splitk * 2 <= run->sms - q.n_chain &&
+               run->kblocks_total % (q.splitk * 2) == 0)
+            q.splitk *= 2;
+        q.n_gemm = std::min(tiles * q.splitk, run->sms - q.n_chain);
+        q.P = run->P;
+        if (q.n_chain >= 1 && q.n_gemm >= 1) {
+            if (run->exec) cudaGraphExecDestroy(run->exec);
+            if (run->graph) cudaGraphDestroy(run->graph);
+            run->exec = nullptr;
+            run->graph = nullptr;
+            run->persist = true;
+            run->rpw = prpw;
+            run->overlap = true;
+            run->pair = false;
+            run->splitk = q.splitk;
+            run->t.splitk = q.splitk;
+            run->g.kblocks = run->kblocks_total / q.splitk;
+            run->gemm_tiles = tiles;
+            run->chain_slots = chain_slots;
+            q.G[0] = run->Gbuf[0];
+            q.G[1] = run->Gbuf[1];
+            q.Gx[0] = run->Gx[0];
+            q.Gx[1] = run->Gx[1];
+            q.gemm_done = run->flags;
+            q.chain_done = run->flags + kTcMaxBatch * run->P;
+            q.abort = run->flags + 2 * kTcMaxBatch * run->P;
+            int khz = 0;
+            cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->device);
+            q.spin_budget = 10LL * (khz > 0 ? khz : 2000000) * 1000;  // about ten seconds
+            run->pp = q;
+            return MARS_OK;
+        }
+    }
+    run->persist = false;
     if (run->exec && rpw == run->rpw && ovl == run->overlap && pr == run->pair && splitk == run->splitk &&
         tiles == run->gemm_tiles && chain_slots == run->chain_slots)
         return MARS_OK;
@@ -179,6 +225,11 @@ int tc_setup(mars_ctx* c, const DevInstance& d, const DevSolve& s, const int32_t
         run->Gx[0] = gx;
         run->Gx[1] = gx + (size_t)R_pad * 128;
     }
+    // the persistent batches' counters, when cooperative launches are available
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    if (coop && (rc = get((2 * (size_t)kTcMaxBatch * run->P + 1) * sizeof(int32_t), (void**)&run->flags)))
+        return rc;
     if ((rc = get((size_t)R * sizeof(double), (void**)&t.T))) return rc;
     if ((rc = get((size_t)R * sizeof(float), (void**)&t.invT))) return rc;
     if ((rc = get((size_t)R * sizeof(float), (void**)&t.d))) return rc;
@@ -312,6 +363,19 @@ int tc_enqueue_batch(mars_ctx* c, TcRun* run, cudaStream_t st)
             c->prof.push_back(e);
         }
     }
+    if (run->persist) {
+        // one cooperative launch for the whole batch, then the active prefix
+        TcPersist q = run->pp;
+        q.sweeps = run->batch;
+        MARS_CUDA(c, cudaMemsetAsync(run->flags, 0, (2 * (size_t)kTcMaxBatch * run->P + 1) * sizeof(int32_t), st));
+        MARS_CUDA(c, launch_tc_sweeps(run->tmJ, run->tmS, run->t, run->g, q, run->rpw, st));
+        MARS_CUDA(c, launch_tc_prefix(run->t, st));
+        run->timed_rows.clear();
+        run->done_sweeps += run->batch;
+        MARS_CUDA(c, cudaMemcpyAsync(run->h_counters, run->t.counters, 4 * sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, st));
+        return MARS_OK;
+    }
     for (int b = 0; b < run->batch; ++b) {
         if (b == 0 && run->profile) {
             if ((rc = tc_enqueue_sweep(c, run, st, true))) return rc;
@@ -342,7 +406,7 @@ int tc_after_batch(mars_ctx* c, TcRun* run)
     if (run->h_counters[1] == 0) return 0;
     if (run->done_sweeps > run->sweep_cap) return fail(c, MARS_EDEVICE, "descent exceeded its sweep bound");
     run->active_at_batch = run->h_counters[1];
-    run->batch = std::min(run->batch * 2, 32);
+    run->batch = std::min(run->batch * 2, kTcMaxBatch);
     return 1;
 }
 
@@ -361,6 +425,10 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     if ((rc = S.get(s.R, &rep))) return rc;
     MARS_CUDA(c, cudaMemcpyAsync(rep, reps.data(), s.R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     TcRun run;
+    // A blocking solve may run its partly active batches as one cooperative
+    // launch each; served requests share the device with other requests'
+    // kernels, which could keep such a launch from being resident at once.
+    run.allow_persist = env_flag("MARS_TC_PERSIST", 1) != 0;
     auto get = [&](size_t bytes, void** out) -> int {
         unsigned char* q = nullptr;
         int r = S.get(bytes, &q);
@@ -381,9 +449,10 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     while (state == 1) {
         const int32_t active_now = run.active_at_batch;
         if ((rc = tc_enqueue_batch(c, &run, st))) { cudaFreeHost(pinned); return rc; }
-        // per sweep: the GEMMs (one per panel, or per pair), P chains, the level step and prefix
+        // per sweep: the GEMMs (one per panel, or per pair), P chains, the level step and
+        // prefix; a persistent batch is one kernel and the prefix
         const int gemms = run.pair ? (run.P + 1) / 2 : run.P;
-        prof->launches += (int64_t)run.batch * (gemms + run.P + 2);
+        prof->launches += run.persist ? 2 : (int64_t)run.batch * (gemms + run.P + 2);
         se = cudaStreamSynchronize(st);
         if (se != cudaSuccess) break;
         for (size_t e = 0; e < run.timed_rows.size(); ++e) {
