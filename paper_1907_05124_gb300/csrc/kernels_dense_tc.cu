@@ -580,7 +580,7 @@ __device__ __forceinline__ void chain_body(const TcState& t, int p, const float*
                 t.Sb[idx] = __float2bfloat16_rn(sf[q]);
         }
     }
-    if (NEXT) {
+    if (NEXT && gx_out) {  // the persistent sweeps' last panel has no next panel
 #pragma unroll
         for (int u = 0; u < SPL / 4; ++u)
             *reinterpret_cast<float4*>(gx_out + (size_t)slot * kBM + 4 * (LPR * u + j)) =

@@ -112,7 +112,8 @@ int tc_plan(mars_ctx* c, TcRun* run, int32_t active, int32_t prefix)
             q.splitk *= 2;
         q.n_gemm = std::min(tiles * q.splitk, run->sms - q.n_chain);
         q.P = run->P;
-        if (q.n_chain >= 1 && q.n_gemm >= 1) {
+        // every replica group and every GEMM item has a CTA of its own
+        if (q.n_chain >= 1 && q.n_gemm >= 1 && q.chain_items <= q.n_chain && tiles * q.splitk <= q.n_gemm) {
             if (run->exec) cudaGraphExecDestroy(run->exec);
             if (run->graph) cudaGraphDestroy(run->graph);
             run->exec = nullptr;
