@@ -427,9 +427,12 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     MARS_CUDA(c, cudaMemcpyAsync(rep, reps.data(), s.R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     TcRun run;
     // A blocking solve may run its partly active batches as one cooperative
-    // launch each; served requests share the device with other requests'
-    // kernels, which could keep such a launch from being resident at once.
-    run.allow_persist = env_flag("MARS_TC_PERSIST", 1) != 0;
+    // launch each (MARS_TC_PERSIST=1; off by default: on a GB300 at N = 8192
+    // it measured slower than the launched overlap, 1.38 against 0.76 ms per
+    // sweep with 128 replicas active); served requests share the device with
+    // other requests' kernels, which could keep such a launch from being
+    // resident at once, and never use it.
+    run.allow_persist = env_flag("MARS_TC_PERSIST", 0) != 0;
     auto get = [&](size_t bytes, void** out) -> int {
         unsigned char* q = nullptr;
         int r = S.get(bytes, &q);

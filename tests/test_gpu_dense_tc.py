@@ -369,3 +369,30 @@ def test_paired_panels_sk_quality(ctx, monkeypatch):
         assert np.array_equal(g.energies, O.energies(oi, g.spins))
         assert abs(g.best_energy - o["energy"].min()) <= 0.01 * abs(o["energy"].min()), prec
     ctx.free(inst)
+
+
+def test_persistent_sweeps_match_oracle(ctx, monkeypatch):
+    """The opt-in persistent batches (one cooperative launch of chain and GEMM
+    CTAs per batch of sweeps, MARS_TC_PERSIST=1): one contracting sweep over
+    256-spin +-1 blocks with exact operands equals the FP64 sweep to 1e-5 (the
+    chain feeds the next panel in FP32 across a block boundary), and a full
+    SK solve returns exact energies."""
+    monkeypatch.setenv("MARS_TC_PERSIST", "1")
+    n, R = 1024, 200
+    J = block_diagonal_pm1(n, n + 3, block=256)
+    inst = ctx.add_dense(J)
+    m0 = bf16_exact_m0(R, n, 8)
+    t0 = np.random.default_rng(9).uniform(110.0, 114.0, size=R).astype(np.float32)
+    oi = O.Instance.dense(J)
+    o = O.mars_solve(oi, m0, t0, c_step=60.0, fixed_sweeps=1)
+    g = ctx.solve(inst, R, float(t0.min()), float(t0.max()), c_step=60.0, fixed_sweeps=1, m0=m0, t0=t0,
+                  precision="bf16", outputs=("m_final",))
+    assert np.abs(g.m_final - o["m"]).max() <= 1e-5
+    ctx.free(inst)
+    J = I.sk_pm1(384, 12)
+    inst = ctx.add_dense(J)
+    g = ctx.solve(inst, 256, 0.0, 39.0, seed=3, precision="bf16", outputs=("energies", "spins", "sweeps"))
+    oi = O.Instance.dense(J)
+    assert np.array_equal(g.energies, O.energies(oi, g.spins))
+    assert (g.replica_sweeps > 3).any()  # several sweeps, so several batches of the launch
+    ctx.free(inst)
