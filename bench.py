@@ -59,12 +59,14 @@ SK_WORKLOAD = {
 }
 
 # A sparse instance too large for shared memory: the 3-D lattice L=100, whose
-# replicas' magnetisations stream through per-CTA slabs of HBM.
+# replicas' magnetisations all stay resident in HBM while each level of a
+# sweep is spread over the whole GPU.
 EA3_L, EA3_R, EA3_TMAX = 100, 608, 6.0
 EA3_WORKLOAD = {
     "workload": "3-D EA +-J spin glass, periodic 100^3 (N=1,000,000), R=608 replicas, "
                 "T0~U(0,6), C_step=1, d_min=1e-4, k_max=1000, FP32 sequential sweeps in colour "
-                "order, magnetisations in per-CTA slabs of global memory",
+                "order, every replica's magnetisations resident in HBM, one grid-wide launch per "
+                "colour level",
     "n_spins": EA3_L ** 3, "replicas": EA3_R, "t_range": [0.0, EA3_TMAX], "c_step": 1.0,
     "d_min": D_MIN, "k_max": K_MAX,
 }
@@ -103,7 +105,7 @@ def parse():
                          "lattice L=100; ea3d_big: the 3-D lattice with N=10^6 (magnetisations in "
                          "HBM); sk8192pm1: the +-1 variant on FP8 tensor cores; "
                          "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
-    ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=3.0,
                     help="serve: mean arrivals per second (about 80 %% of the mix's capacity)")
     ap.add_argument("--inflight", type=int, default=8,
@@ -469,6 +471,7 @@ def run_mars(args, world, rank, local):
     time.sleep(0.3)
     step_ms, descent_s, updates, best = [], [], 0, []
     gemm_s, gemm_flops, gemm_launches, launches = 0.0, 0.0, 0, 0
+    level_s, level_upd, level_launches = 0.0, 0, 0
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()  # L2 flush between timed steps, outside the events
@@ -486,6 +489,9 @@ def run_mars(args, world, rank, local):
         gemm_flops += res.gemm_flops
         gemm_launches += res.gemm_launches
         launches += res.kernel_launches
+        level_s += res.level_seconds
+        level_upd += res.level_updates
+        level_launches += res.level_launches
     clocks = sampler.stop()
     torch.cuda.synchronize()
     tot_ms = sum(step_ms)
@@ -551,13 +557,18 @@ def run_mars(args, world, rank, local):
                              "sfu_source": f"{sms} SMs x (1/32 + 1/16 SFU clocks per tanh)^-1 x SM clock"},
                     "descent_ms_mean": 1e3 * d_mean}
     elif wl.name == "ea3d_big":
-        achieved = EA3_BYTES_PER_UPDATE * upd_per_launch / d_mean / 1e9
+        # The level launches of one sampled sweep per batch of sweeps (CUDA
+        # events on the library's stream), each moving 12 algorithmic bytes
+        # per spin-update of its live replicas.
         sh = shape or {}
-        rt_used = sh.get("sell_rt", -1) if sh.get("sell_rt", -1) > 0 else 2
+        rt_used = sh.get("sell_rt", -1) if sh.get("sell_rt", -1) > 0 else 4
+        achieved = EA3_BYTES_PER_UPDATE * level_upd / level_s / 1e9 if level_s > 0 else 0.0
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "kernel": f"sparse_slab_kernel<RT={rt_used}, +-1 words, degree 6>",
+                    "kernel": f"wide_level_kernel<RT={rt_used}, +-1 words, degree 6>",
                     "bytes_per_update": EA3_BYTES_PER_UPDATE,
+                    "level_launches_sampled": level_launches,
+                    "whole_descent_gbs": EA3_BYTES_PER_UPDATE * upd_per_launch / d_mean / 1e9,
                     "peak_source": f"hbm copy ({peaks['source']})",
                     "descent_ms_mean": 1e3 * d_mean}
     else:
@@ -610,10 +621,16 @@ def run_mars(args, world, rank, local):
 def run_serve(args, world, rank, local):
     """Serving: Poisson arrivals of mixed Ising / max-cut requests, p50/p99 latency.
 
-    The request mix follows the serving configuration in shape (dense SK with
-    +-1 or Gaussian couplings, sparse lattices and random graphs, replica
-    counts 64-1024) with sizes scaled so that a run ends within minutes:
-    dense N 256-1024 (tensor-core BF16 for the Gaussian ones), sparse N 1k-100k.
+    The serving configuration's mix: dense SK instances (N 256-16384, +-1 or
+    Gaussian couplings) and sparse lattices and random graphs (N 1k-100k,
+    degree 4-40), each request asking R replicas in {64, ..., 4096}, under a
+    120 GB HBM budget. Two choices keep a 2,000-request run within about a
+    quarter of an hour, and the JSON line states both: dense requests take
+    at most 64 temperature levels (C_step = T_max / min(2 sqrt(N), 64); the
+    paper's 1/sqrt(N) step gives 256 levels at N = 16384), and R is capped by
+    size for dense instances (4096 up to N = 1024, 1024 at N = 4096, 256 at
+    N = 16384). Dense Gaussian requests and +-1 requests up to N = 1024 run
+    on BF16 tensor cores, larger +-1 ones on E4M3 (N = 256: the FP32 path).
     """
     import numpy as np
     import torch
@@ -625,19 +642,35 @@ def run_serve(args, world, rank, local):
     build.build()
     rng = np.random.default_rng(0)
     ctx = mars.Context(local, hbm_budget_bytes=120 << 30)
-    pool = []  # (name, inst, n, t_max, c_step, precision)
-    for nn in (256, 512, 1024):
-        pool.append((f"sk_pm1_{nn}", ctx.add_dense(instances.sk_pm1(nn, nn)), nn, 2.0 * nn ** 0.5, 1.0, "fp32" if nn == 256 else "bf16"))
-        pool.append((f"sk_gauss_{nn}", ctx.add_dense(instances.sk_gauss(nn, nn + 1)), nn, 2.0, 1.0 / nn ** 0.5, "bf16"))
+    reps_all = np.array([64, 128, 256, 512, 1024, 2048, 4096])
+    # (name, inst, n, t_max, c_step, precision, weight, largest R)
+    pool = []
+    dense_w = {256: 0.12, 1024: 0.09, 4096: 0.06, 16384: 0.01}
+    dense_rmax = {256: 4096, 1024: 4096, 4096: 1024, 16384: 256}
+    for nn, wgt in dense_w.items():
+        lv = min(2.0 * nn ** 0.5, 64.0)
+        t_pm1, t_g = 2.0 * nn ** 0.5, 2.0
+        pool.append((f"sk_pm1_{nn}", ctx.add_dense(instances.sk_pm1(nn, nn)), nn, t_pm1, t_pm1 / lv,
+                     "fp32" if nn == 256 else "bf16" if nn <= 1024 else "fp8", wgt / 2, dense_rmax[nn]))
+        pool.append((f"sk_gauss_{nn}", ctx.add_dense(instances.sk_gauss(nn, nn + 1)), nn, t_g, t_g / lv,
+                     "fp32" if nn == 256 else "bf16", wgt / 2, dense_rmax[nn]))
+    sparse = []
     for L in (32, 64, 100, 200):
         g = instances.ea_lattice(L, 2, L)
-        pool.append((f"ea2d_{L}", ctx.add_csr(*g), g.n, 4.0, 1.0, "fp32"))
+        sparse.append((f"ea2d_{L}", ctx.add_csr(*g), g.n, 4.0, 1.0, "fp32"))
     for L in (16, 32):
         g = instances.ea_lattice(L, 3, L)
-        pool.append((f"ea3d_{L}", ctx.add_csr(*g), g.n, 6.0, 1.0, "fp32"))
+        sparse.append((f"ea3d_{L}", ctx.add_csr(*g), g.n, 6.0, 1.0, "fp32"))
     for nn, d in ((1000, 40), (5000, 12), (20000, 4), (100000, 4)):
         g = instances.er_graph(nn, d, nn + d, "pm1")
-        pool.append((f"er_{nn}_{d}", ctx.add_csr(*g), g.n, 2.0 * d ** 0.5 + 1.0, 1.0, "fp32"))
+        sparse.append((f"er_{nn}_{d}", ctx.add_csr(*g), g.n, 2.0 * d ** 0.5 + 1.0, 1.0, "fp32"))
+    w_sparse = (1.0 - sum(dense_w.values())) / len(sparse)
+    pool += [k + (w_sparse, 4096) for k in sparse]
+    weights = np.array([k[6] for k in pool])
+    n_req = args.requests
+    kinds = rng.choice(len(pool), size=n_req, p=weights / weights.sum())
+    reps = np.array([rng.choice(reps_all[reps_all <= pool[k][7]]) for k in kinds])
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n_req))
     n_req = args.requests
     kinds = rng.integers(0, len(pool), size=n_req)
     reps = rng.choice(np.array([64, 128, 256, 512, 1024]), size=n_req)
@@ -650,7 +683,7 @@ def run_serve(args, world, rank, local):
     while nxt < n_req or pending:
         now = time.perf_counter() - t_start
         while nxt < n_req and arrivals[nxt] <= now:
-            name, inst, nn, tmax, cstep, prec = pool[kinds[nxt]]
+            name, inst, nn, tmax, cstep, prec = pool[kinds[nxt]][:6]
             req = ctx.submit(inst, int(reps[nxt]), 0.0, tmax, c_step=cstep, seed=nxt,
                              precision=prec)
             pending[req] = (arrivals[nxt], name)
@@ -671,9 +704,14 @@ def run_serve(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
         "data": "synthetic (seeded instances, Poisson arrivals)",
         "config": {"workload": f"serving: {n_req} Poisson arrivals at {args.rate}/s, mixed dense SK "
-                               "(N 256-1024, +-1 / Gaussian) and sparse lattices / ER graphs "
-                               f"(N 1k-100k), R 64-1024, {args.inflight} in flight, 120 GB budget",
-                   "requests": n_req, "rate_per_s": args.rate, "inflight": args.inflight},
+                               "(N 256-16384, +-1 / Gaussian) and sparse lattices / ER graphs "
+                               f"(N 1k-100k, degree 4-40), R 64-4096, {args.inflight} in flight, "
+                               "120 GB budget",
+                   "requests": n_req, "rate_per_s": args.rate, "inflight": args.inflight,
+                   "dense_levels": "at most 64 (C_step = T_max / min(2 sqrt(N), 64))",
+                   "dense_r_max": {str(k): v for k, v in dense_rmax.items()},
+                   "kinds": {k[0]: {"n": k[2], "precision": k[5], "share": round(float(k[6]), 4)}
+                             for k in pool}},
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                        "p99": float(np.percentile(lat_ms, 99)),
                        "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},

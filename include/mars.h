@@ -263,6 +263,13 @@ typedef struct {
      * counted one by one); mars_solve_batch reports the whole batch's count
      * in every job's result; 0 from the serving calls. */
     int64_t kernel_launches;
+    /* Level-synchronous sparse path only (magnetisations in global memory,
+     * mars_solve): CUDA-event time, count and spin-updates (live replicas x
+     * spins of the level) of the level launches of one sampled sweep per
+     * batch of sweeps; 0 elsewhere. */
+    double level_seconds;
+    int64_t level_launches;
+    int64_t level_updates;
 } mars_result;
 
 /*

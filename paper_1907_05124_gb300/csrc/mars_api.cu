@@ -903,6 +903,8 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     MARS_CUDA(c, cudaStreamSynchronize(st));
     SparsePlan sp;
     DensePlan dp;
+    WidePlan wp;
+    bool wide = false;
     int rt = 1;
     if (in->dev.dense && !tc) {
         dp = plan_dense(in->dev, R, s.jacobi, c->device);
@@ -912,12 +914,29 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     } else {
         if (s.jacobi || !plan_sparse_sell(in->dev, R, c->device, &sp))
             sp = plan_sparse(in->dev, R, s.jacobi, c->device);
-        rt = sp.rt;
-        const size_t per = (size_t)sp.grid * n * rt;
-        float* scr = nullptr;
-        if (sp.scratch_floats && (rc = S.get(sp.scratch_floats, &scr))) return rc;
-        if (!sp.onchip) { s.m_scratch = scr; scr += per; }
-        if (s.jacobi) s.m_next = scr;
+        // Magnetisations beyond shared memory: every replica resident and each
+        // level spread over the whole grid, when all of them fit in half of
+        // the free device memory and of what the budget has left (else the
+        // per-CTA slabs).
+        if (sp.sell && !sp.onchip && env_flag("MARS_SELL_WIDE", 1)) {
+            const int wrt = in->dev.shape.sell_rt >= 0 ? in->dev.shape.sell_rt : env_flag("MARS_SELL_RT", 4);
+            if (plan_sparse_wide(in->dev, R, wrt, c->device, &wp)) {
+                const size_t need = (size_t)wp.groups * wp.slab * sizeof(float);
+                size_t free_b = 0, total_b = 0;
+                cudaMemGetInfo(&free_b, &total_b);
+                wide = 2 * need <= free_b && (!c->budget || c->used + 2 * need <= c->budget);
+            }
+        }
+        if (wide) {
+            rt = wp.rt;
+        } else {
+            rt = sp.rt;
+            const size_t per = (size_t)sp.grid * n * rt;
+            float* scr = nullptr;
+            if (sp.scratch_floats && (rc = S.get(sp.scratch_floats, &scr))) return rc;
+            if (!sp.onchip) { s.m_scratch = scr; scr += per; }
+            if (s.jacobi) s.m_next = scr;
+        }
     }
     std::vector<int32_t> reps(R);
     std::iota(reps.begin(), reps.end(), 0);
@@ -935,6 +954,7 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
     s.ntiles = ntiles;
     s.rt = rt;
     TcProfile tcprof;
+    LevelProfile lvprof;
     MARS_CUDA(c, cudaEventRecord(c->ev0, st));
     if (tc) {
         const float t0_max = *std::max_element(t0h.begin(), t0h.end());
@@ -944,6 +964,10 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
         MARS_CUDA(c, launch_dense(in->dev, s, dp, st));
         MARS_CUDA(c, cudaEventRecord(c->ev3, st));
         ++launches;
+    } else if (wide) {
+        const float t0_max = *std::max_element(t0h.begin(), t0h.end());
+        if ((rc = run_sparse_wide(c, in->dev, p, s, wp, t0_max, S, &launches, &lvprof))) return rc;
+        MARS_CUDA(c, cudaEventRecord(c->ev3, st));
     } else {
         if (sp.sell)
             MARS_CUDA(c, launch_sparse_sell(in->dev, s, sp, st));
@@ -1001,6 +1025,9 @@ int mars_solve(mars_ctx* c, int32_t id, const mars_params* p, int8_t* best_spins
         result->gemm_launches = tcprof.gemm_launches;
         result->gemm_flops = tcprof.gemm_flops;
         result->kernel_launches = launches;
+        result->level_seconds = lvprof.seconds;
+        result->level_launches = lvprof.launches;
+        result->level_updates = lvprof.updates;
         result->integer = in->dev.integer;
         result->energy_err_bound = (in->dev.integer || in->dev.exact_ok)
                                        ? 0.0

@@ -231,6 +231,19 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
                  const std::vector<int32_t>& reps, float t0_max, Scratch& S, TcProfile* prof,
                  bool polish);
 
+// The level-synchronous sparse descent (mars_wide_driver.cu), blocking: every
+// replica resident, a sweep = one launch per level and one decision launch,
+// batches of sweeps replayed from a graph until no replica is live; then the
+// per-replica outputs. Adds its kernel launches to *launches.
+// The first sweep of every batch runs outside the graph with CUDA events
+// around each level launch; prof sums their time, count and spin-updates.
+struct LevelProfile {
+    double seconds = 0.0;
+    int64_t launches = 0, updates = 0;
+};
+int run_sparse_wide(mars_ctx* c, const DevInstance& d, const mars_params* p, const DevSolve& s,
+                    const WidePlan& wp, float t0_max, Scratch& S, int64_t* launches, LevelProfile* prof);
+
 // Round-to-nearest-even FP32 -> BF16 bits (host side, for uploads).
 uint16_t float_to_bf16_bits(float f);
 

@@ -198,6 +198,45 @@ bool plan_sparse_sell(const DevInstance& in, int R, int device, SparsePlan* p);
 const void* pick_sell_slab(int rt, int fmt, int deg);
 cudaError_t launch_sparse_sell(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
                                cudaStream_t st);
+
+// Level-synchronous sliced-ELL descent with every replica resident in global
+// memory (kernels_sparse_wide.cu): groups of rt slots share one slab layout,
+// m[g][i*rt + k]; slot q = g*rt + k runs replica s.tile_rep[q] (-1: empty).
+struct DevWide {
+    int32_t rt = 4;
+    int32_t groups = 0;
+    size_t slab = 0;                 // floats per group (sell_slab_floats(n, rt))
+    float* m = nullptr;              // groups * slab
+    double* T = nullptr;             // per slot: current level's temperature
+    float* invT = nullptr;
+    int32_t* live = nullptr;         // descending
+    int32_t* lvl_sweeps = nullptr;
+    int32_t* sweeps = nullptr;
+    int32_t* levels = nullptr;
+    int32_t* capped = nullptr;
+    uint32_t* dmax = nullptr;        // the sweep's largest |change| (float bits, >= 0)
+    int32_t* glist = nullptr;        // live groups, ascending
+    int32_t* counters = nullptr;     // [0] live groups, [1] live replicas
+};
+struct WidePlan {
+    int rt = 4;
+    int entry = 1;      // coupling format: 0 general pairs, 1 +-1 words
+    int deg = 0;        // compile-time degree of a regular instance (4 or 6), else 0
+    int groups = 0;
+    size_t slab = 0;
+    int grid = 0;       // CTAs of a level launch
+    int sms = 0;
+};
+bool plan_sparse_wide(const DevInstance& in, int R, int rt, int device, WidePlan* p);
+cudaError_t launch_wide_init(const DevInstance& in, const DevSolve& s, const DevWide& w, const WidePlan& p,
+                             cudaStream_t st);
+cudaError_t launch_wide_level(const DevInstance& in, const DevSolve& s, const DevWide& w, const WidePlan& p,
+                              int level, cudaStream_t st);
+// step != 0: the stopping rule and cooling after a sweep; then the live-group
+// list and counts (step == 0: the list only).
+cudaError_t launch_wide_decide(const DevSolve& s, const DevWide& w, int step, cudaStream_t st);
+cudaError_t launch_wide_finalize(const DevInstance& in, const DevSolve& s, const DevWide& w, const WidePlan& p,
+                                 cudaStream_t st);
 SparsePlan plan_sparse(const DevInstance& in, int R, int jacobi, int device);
 cudaError_t launch_sparse(const DevInstance& in, const DevSolve& s, const SparsePlan& p,
                           cudaStream_t st);

@@ -87,7 +87,9 @@ class Result(ctypes.Structure):
                 ("energy_err_bound", ctypes.c_double),
                 ("status", ctypes.c_int32), ("integer", ctypes.c_int32),
                 ("gemm_seconds", ctypes.c_double), ("gemm_launches", ctypes.c_int64),
-                ("gemm_flops", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("gemm_flops", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("level_seconds", ctypes.c_double), ("level_launches", ctypes.c_int64),
+                ("level_updates", ctypes.c_int64)]
 
 
 class InstanceInfo(ctypes.Structure):
@@ -209,6 +211,9 @@ class SolveResult:
     gemm_launches: int = 0
     gemm_flops: float = 0.0
     kernel_launches: int = 0
+    level_seconds: float = 0.0
+    level_launches: int = 0
+    level_updates: int = 0
     energies: np.ndarray | None = None
     spins: np.ndarray | None = None
     m_final: np.ndarray | None = None
@@ -378,7 +383,8 @@ class Context:
             energy_err_bound=res.energy_err_bound, integer=bool(res.integer), best_spins=best,
             gemm_seconds=res.gemm_seconds, gemm_launches=res.gemm_launches,
             gemm_flops=res.gemm_flops, kernel_launches=res.kernel_launches,
-            energies=keep.get("energies"), spins=keep.get("spins"), m_final=keep.get("m_final"),
+            level_seconds=res.level_seconds, level_launches=res.level_launches,
+            level_updates=res.level_updates, energies=keep.get("energies"), spins=keep.get("spins"), m_final=keep.get("m_final"),
             t0=keep.get("t0"), replica_sweeps=keep.get("sweeps"),
             replica_levels=keep.get("levels"), replica_capped=keep.get("capped"))
 
