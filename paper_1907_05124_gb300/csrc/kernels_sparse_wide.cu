@@ -104,6 +104,98 @@ __global__ void __launch_bounds__(kWideThreads, 1) wide_level_kernel(DevInstance
     float* m = nullptr;
 #pragma unroll
     for (int k = 0; k < RT; ++k) { invT[k] = 0.f; dloc[k] = 0.f; }
+    if constexpr (FMT == 1 && DEG > 0) {
+        // Every row has degree DEG, so every slice does: slice sl of the level
+        // starts at row dA.x + 32 (sl - s0) and its couplings at
+        // dA.w + 32 DEG (sl - s0). With no descriptor to wait for, the next
+        // item's coupling words and group are loaded while this item's
+        // neighbour gathers are in flight, leaving one round trip per item.
+        const int4 dA = __ldg(in.slices + s0);
+        const int4 dB = __ldg(in.slices + s1 - 1);
+        const int row_end = dB.x + dB.y;
+        const uint32_t* ew = in.sell_pm1 + dA.w + lane;
+        int64_t it = b0 + warp;
+        uint32_t cw[DEG];
+        int g = 0, sl = 0;
+        if (it < b1) {
+            const int gi = (int)(it / nsl);
+            sl = (int)(it - (int64_t)gi * nsl);
+            g = __ldg(w.glist + gi);
+#pragma unroll
+            for (int q = 0; q < DEG; ++q) cw[q] = __ldg(ew + (size_t)sl * 32 * DEG + 32 * q);
+        }
+        while (it < b1) {
+            const int64_t itn = it + kWarps;
+            uint32_t cn[DEG];
+            int gn = g, sln = 0;
+            if (itn < b1) {
+                const int gi = (int)(itn / nsl);
+                sln = (int)(itn - (int64_t)gi * nsl);
+                gn = __ldg(w.glist + gi);
+#pragma unroll
+                for (int q = 0; q < DEG; ++q) cn[q] = __ldg(ew + (size_t)sln * 32 * DEG + 32 * q);
+            } else {
+#pragma unroll
+                for (int q = 0; q < DEG; ++q) cn[q] = 0u;
+            }
+            if (g != cur) {
+                if (cur >= 0) flush_d<RT>(w, cur, live, dloc, lane);
+                cur = g;
+                m = w.m + (size_t)g * w.slab;
+                live = 0;
+#pragma unroll
+                for (int k = 0; k < RT; ++k) {
+                    invT[k] = w.invT[g * RT + k];
+                    live |= w.live[g * RT + k] ? 1 << k : 0;
+                }
+                lean = live == (1 << RT) - 1 && !in.h;
+            }
+            const int i = dA.x + 32 * sl + lane;
+            if (i < row_end) {
+                const typename V::T old = V::load(m + i * RT);
+                const float hv = in.h ? __ldg(in.h + i) : 0.f;
+                typename V::T acc;
+#pragma unroll
+                for (int k = 0; k < RT; ++k) V::set(acc, k, 0.f);
+#pragma unroll
+                for (int q = 0; q < DEG; ++q) {
+                    const int c = (int)(cw[q] & 0x7fffffffu);
+                    const float wt = (cw[q] >> 31) ? -1.f : 1.f;
+                    const typename V::T mv = V::load(m + c * RT);
+#pragma unroll
+                    for (int k = 0; k < RT; ++k) V::set(acc, k, fmaf(wt, V::get(mv, k), V::get(acc, k)));
+                }
+                typename V::T nv;
+                if (lean) {
+#pragma unroll
+                    for (int k = 0; k < RT; ++k) {
+                        const float sn = -tanh_sfu(V::get(acc, k) * invT[k]);
+                        dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(old, k)));
+                        V::set(nv, k, sn);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < RT; ++k) {
+                        if ((live >> k) & 1) {
+                            const float sn = -tanh_sfu((V::get(acc, k) + hv) * invT[k]);
+                            dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(old, k)));
+                            V::set(nv, k, sn);
+                        } else {
+                            V::set(nv, k, V::get(old, k));
+                        }
+                    }
+                }
+                V::store(m + i * RT, nv);
+            }
+            it = itn;
+            g = gn;
+            sl = sln;
+#pragma unroll
+            for (int q = 0; q < DEG; ++q) cw[q] = cn[q];
+        }
+        if (cur >= 0) flush_d<RT>(w, cur, live, dloc, lane);
+        return;
+    }
     for (int64_t it = b0 + warp; it < b1; it += kWarps) {
         const int gi = (int)(it / nsl);
         const int sl = s0 + (int)(it - (int64_t)gi * nsl);
