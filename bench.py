@@ -106,10 +106,13 @@ def parse():
                          "HBM); sk8192pm1: the +-1 variant on FP8 tensor cores; "
                          "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
     ap.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
-    ap.add_argument("--rate", type=float, default=3.0,
-                    help="serve: mean arrivals per second (about 80 %% of the mix's capacity)")
-    ap.add_argument("--inflight", type=int, default=8,
+    ap.add_argument("--rate", type=float, default=2.0,
+                    help="serve: mean arrivals per second")
+    ap.add_argument("--inflight", type=int, default=16,
                     help="serve: requests admitted at once (mars_serve_limits)")
+    ap.add_argument("--serve-deadline", type=float, default=1500.0,
+                    help="serve: seconds after which requests still pending are cancelled "
+                         "(counted in the line, excluded from the latencies)")
     ap.add_argument("--replicas", type=int, default=0, help="override R (profiling runs)")
     ap.add_argument("--fixed-sweeps", type=int, default=0,
                     help="profiling runs only: exactly this many sweeps per level")
@@ -645,7 +648,7 @@ def run_serve(args, world, rank, local):
     reps_all = np.array([64, 128, 256, 512, 1024, 2048, 4096])
     # (name, inst, n, t_max, c_step, precision, weight, largest R)
     pool = []
-    dense_w = {256: 0.12, 1024: 0.09, 4096: 0.06, 16384: 0.01}
+    dense_w = {256: 0.12, 1024: 0.09, 4096: 0.06, 16384: 0.005}
     dense_rmax = {256: 4096, 1024: 4096, 4096: 1024, 16384: 256}
     for nn, wgt in dense_w.items():
         lv = min(2.0 * nn ** 0.5, 64.0)
@@ -671,17 +674,28 @@ def run_serve(args, world, rank, local):
     kinds = rng.choice(len(pool), size=n_req, p=weights / weights.sum())
     reps = np.array([rng.choice(reps_all[reps_all <= pool[k][7]]) for k in kinds])
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n_req))
-    n_req = args.requests
-    kinds = rng.integers(0, len(pool), size=n_req)
-    reps = rng.choice(np.array([64, 128, 256, 512, 1024]), size=n_req)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n_req))
     ctx.serve_limits(args.inflight)
     pending, lat, upd = {}, [], 0
     by_kind = {}  # request kind -> latencies (s)
     t_start = time.perf_counter()
     nxt = 0
+    cancelled = []
     while nxt < n_req or pending:
         now = time.perf_counter() - t_start
+        if now > args.serve_deadline:
+            for req, (t_arr, name) in list(pending.items()):
+                ctx.cancel(req)
+                cancelled.append(name)
+            for req in list(pending):
+                while True:
+                    try:
+                        if ctx.poll(req) is not None:
+                            break
+                    except mars.MarsError:
+                        break
+                    time.sleep(0.001)
+            pending.clear()
+            break
         while nxt < n_req and arrivals[nxt] <= now:
             name, inst, nn, tmax, cstep, prec = pool[kinds[nxt]][:6]
             req = ctx.submit(inst, int(reps[nxt]), 0.0, tmax, c_step=cstep, seed=nxt,
@@ -716,6 +730,8 @@ def run_serve(args, world, rank, local):
                        "p99": float(np.percentile(lat_ms, 99)),
                        "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
         "served_by": dict(zip(("persistent_ring_kernel", "own_stream"), ctx.serve_counters())),
+        "completed": len(lat), "cancelled_at_deadline": len(cancelled),
+        "not_submitted": n_req - nxt,
         "latency_ms_by_kind": {k: {"count": len(v), "p50": float(np.percentile(1e3 * np.array(v), 50)),
                                    "p99": float(np.percentile(1e3 * np.array(v), 99))}
                                for k, v in sorted(by_kind.items())},
