@@ -106,7 +106,7 @@ def parse():
                          "HBM); sk8192pm1: the +-1 variant on FP8 tensor cores; "
                          "serve: Poisson arrivals of mixed requests through mars_submit/mars_poll")
     ap.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
-    ap.add_argument("--rate", type=float, default=2.0,
+    ap.add_argument("--rate", type=float, default=1.5,
                     help="serve: mean arrivals per second")
     ap.add_argument("--inflight", type=int, default=16,
                     help="serve: requests admitted at once (mars_serve_limits)")
@@ -648,7 +648,7 @@ def run_serve(args, world, rank, local):
     reps_all = np.array([64, 128, 256, 512, 1024, 2048, 4096])
     # (name, inst, n, t_max, c_step, precision, weight, largest R)
     pool = []
-    dense_w = {256: 0.12, 1024: 0.09, 4096: 0.06, 16384: 0.005}
+    dense_w = {256: 0.10, 1024: 0.06, 4096: 0.03, 16384: 0.005}
     dense_rmax = {256: 4096, 1024: 4096, 4096: 1024, 16384: 256}
     for nn, wgt in dense_w.items():
         lv = min(2.0 * nn ** 0.5, 64.0)

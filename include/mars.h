@@ -345,7 +345,11 @@ int mars_autotune(mars_ctx* ctx, int32_t inst, const mars_params* params, int32_
  * (mars_serve_limits, default 8) and the context's HBM budget holds the
  * request's buffers; each admitted request runs on its own CUDA stream, so
  * requests that arrive while others are on the GPU start as soon as slots
- * and memory free up and their kernels overlap on the device. A request's
+ * and memory free up and their kernels overlap on the device. Sparse
+ * requests run on persistent CTAs that stay resident while work lasts; they
+ * hold at most half of the SMs (MARS_SERVE_SPARSE_SMS, read when the engine
+ * starts, sets another count), so dense requests' kernels always find SMs
+ * free. A request's
  * result is the same as mars_solve's with the same parameters, except that
  * replicas run in index order (the per-replica results are identical).
  * m0/t0 must be device pointers (MARS_DEVICE_PTR) or NULL; the instance must

@@ -15,6 +15,8 @@
 // so a replica's trajectory does not depend on which kernel ran it.
 #include "sell_job.cuh"
 
+#include <cstdlib>
+
 namespace mars {
 namespace {
 
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(kWideThreads, 1) wide_level_kernel(DevInstance
         }
         if (cur >= 0) flush_d<RT>(w, cur, live, dloc, lane);
         return;
-    }
+    } else {
     for (int64_t it = b0 + warp; it < b1; it += kWarps) {
         const int gi = (int)(it / nsl);
         const int sl = s0 + (int)(it - (int64_t)gi * nsl);
@@ -253,6 +255,197 @@ __global__ void __launch_bounds__(kWideThreads, 1) wide_level_kernel(DevInstance
             V::store(m + i * RT, nv);
         }
     }
+    if (cur >= 0) flush_d<RT>(w, cur, live, dloc, lane);
+    }
+}
+
+// Shared memory of the staged level kernel: two stages per warp, each holding
+// one item's DEG x 32 RT-wide neighbour gathers.
+template <int RT, int DEG>
+constexpr size_t staged_smem_bytes()
+{
+    return (size_t)(kWideThreads / 32) * 2 * DEG * 32 * RT * sizeof(float);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_ca(uint32_t dst, const float* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// The level kernel for regular +-1 lattices with the neighbour gathers staged
+// in shared memory: while a warp computes item j from its stage, the
+// asynchronous copies of item j+1's gathers (which hold no registers) and the
+// coupling words of item j+2 are in flight, so each SM keeps about twice the
+// loads of the register-pipelined kernel outstanding. The arithmetic per spin
+// is the same: the couplings in order, the same tanh.
+template <int RT, int DEG>
+__global__ void __launch_bounds__(kWideThreads, 1) wide_level_staged_kernel(DevInstance in, DevSolve s,
+                                                                               DevWide w, int l)
+{
+    (void)s;
+    using V = Vec<RT>;
+    constexpr int kWarps = kWideThreads / 32;
+    constexpr int kStage = DEG * 32 * RT;  // floats of one stage
+    extern __shared__ float4 wide_stage_smem[];
+    const int ng = w.counters[0];
+    if (ng == 0) return;
+    const int s0 = __ldg(in.lvl_slice + l), s1 = __ldg(in.lvl_slice + l + 1);
+    const int nsl = s1 - s0;
+    if (nsl <= 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t items = (int64_t)ng * nsl;
+    const int64_t per = (items + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per;
+    const int64_t b1 = b0 + per < items ? b0 + per : items;
+    int64_t itA = b0 + warp;
+    if (itA >= b1) return;  // no barrier follows: a warp without items may leave
+
+    // Slice sl of the level: rows dA.x + 32 sl .., couplings at dA.w + 32 DEG sl.
+    const int4 dA = __ldg(in.slices + s0);
+    const int4 dB = __ldg(in.slices + s1 - 1);
+    const int row_end = dB.x + dB.y;
+    const uint32_t* ew = in.sell_pm1 + dA.w + lane;
+    float* const stage0 = reinterpret_cast<float*>(wide_stage_smem) + (size_t)warp * 2 * kStage;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage0);
+
+    // Copies item (g, sl)'s gathers into stage st; returns the sign bits.
+    uint32_t cw[DEG];
+    auto issue = [&](int g, int st) -> uint32_t {
+        const float* mg = w.m + (size_t)g * w.slab;
+        uint32_t signs = 0;
+#pragma unroll
+        for (int q = 0; q < DEG; ++q) {
+            const int c = (int)(cw[q] & 0x7fffffffu);
+            signs |= (cw[q] >> 31) << q;
+            cp_async_ca<RT * 4>(sbase + (uint32_t)((st * kStage + (q * 32 + lane) * RT) * sizeof(float)),
+                                mg + (size_t)c * RT);
+        }
+        return signs;
+    };
+    auto couplings = [&](int sl) {
+#pragma unroll
+        for (int q = 0; q < DEG; ++q) cw[q] = __ldg(ew + (size_t)sl * 32 * DEG + 32 * q);
+    };
+    auto old_of = [&](int g, int sl) {
+        typename V::T v;
+        const int i = dA.x + 32 * sl + lane;
+        if (i < row_end) {
+            v = V::load(w.m + (size_t)g * w.slab + (size_t)i * RT);
+        } else {
+#pragma unroll
+            for (int k = 0; k < RT; ++k) V::set(v, k, 0.f);
+        }
+        return v;
+    };
+
+    int gA = 0, slA = 0;
+    {
+        const int gi = (int)(itA / nsl);
+        slA = (int)(itA - (int64_t)gi * nsl);
+        gA = __ldg(w.glist + gi);
+    }
+    couplings(slA);
+    uint32_t signA = issue(gA, 0);
+    cp_async_commit();
+    typename V::T oldA = old_of(gA, slA);
+    int64_t itB = itA + kWarps;
+    bool hasB = itB < b1;
+    int gB = gA, slB = 0;
+    if (hasB) {
+        const int gi = (int)(itB / nsl);
+        slB = (int)(itB - (int64_t)gi * nsl);
+        gB = __ldg(w.glist + gi);
+        couplings(slB);
+    }
+
+    int cur = -1, live = 0, st = 0;
+    bool lean = false;
+    float invT[RT], dloc[RT];
+    float* m = nullptr;
+#pragma unroll
+    for (int k = 0; k < RT; ++k) { invT[k] = 0.f; dloc[k] = 0.f; }
+    for (;;) {
+        uint32_t signB = 0;
+        typename V::T oldB;
+        if (hasB) {
+            signB = issue(gB, st ^ 1);
+            oldB = old_of(gB, slB);
+        }
+        cp_async_commit();
+        const int64_t itC = itB + kWarps;
+        const bool hasC = hasB && itC < b1;
+        int gC = gB, slC = 0;
+        if (hasC) {
+            const int gi = (int)(itC / nsl);
+            slC = (int)(itC - (int64_t)gi * nsl);
+            gC = __ldg(w.glist + gi);
+            couplings(slC);
+        }
+        cp_async_wait<1>();  // item A's copies have landed
+        if (gA != cur) {
+            if (cur >= 0) flush_d<RT>(w, cur, live, dloc, lane);
+            cur = gA;
+            m = w.m + (size_t)gA * w.slab;
+            live = 0;
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                invT[k] = w.invT[gA * RT + k];
+                live |= w.live[gA * RT + k] ? 1 << k : 0;
+            }
+            lean = live == (1 << RT) - 1 && !in.h;
+        }
+        const int i = dA.x + 32 * slA + lane;
+        if (i < row_end) {
+            const float* sg = stage0 + st * kStage + lane * RT;
+            const float hv = in.h ? __ldg(in.h + i) : 0.f;
+            typename V::T acc;
+#pragma unroll
+            for (int k = 0; k < RT; ++k) V::set(acc, k, 0.f);
+#pragma unroll
+            for (int q = 0; q < DEG; ++q) {
+                const float wt = ((signA >> q) & 1u) ? -1.f : 1.f;
+                const typename V::T mv = V::load(sg + q * 32 * RT);
+#pragma unroll
+                for (int k = 0; k < RT; ++k) V::set(acc, k, fmaf(wt, V::get(mv, k), V::get(acc, k)));
+            }
+            typename V::T nv;
+            if (lean) {
+#pragma unroll
+                for (int k = 0; k < RT; ++k) {
+                    const float sn = -tanh_sfu(V::get(acc, k) * invT[k]);
+                    dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(oldA, k)));
+                    V::set(nv, k, sn);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < RT; ++k) {
+                    if ((live >> k) & 1) {
+                        const float sn = -tanh_sfu((V::get(acc, k) + hv) * invT[k]);
+                        dloc[k] = fmaxf(dloc[k], fabsf(sn - V::get(oldA, k)));
+                        V::set(nv, k, sn);
+                    } else {
+                        V::set(nv, k, V::get(oldA, k));
+                    }
+                }
+            }
+            V::store(m + (size_t)i * RT, nv);
+        }
+        if (!hasB) break;
+        gA = gB;
+        slA = slB;
+        signA = signB;
+        oldA = oldB;
+        gB = gC;
+        slB = slC;
+        hasB = hasC;
+        itB = itC;
+        st ^= 1;
+    }
+    cp_async_wait<0>();
     if (cur >= 0) flush_d<RT>(w, cur, live, dloc, lane);
 }
 
@@ -422,6 +615,27 @@ const void* pick_level(int rt, int fmt, int deg)
     return nullptr;
 }
 
+// The staged kernel (regular +-1 lattices) and its shared memory, or null.
+template <int RT>
+const void* pick_staged_rt(int deg, size_t* smem)
+{
+    if (deg == 4) { *smem = staged_smem_bytes<RT, 4>(); return (const void*)wide_level_staged_kernel<RT, 4>; }
+    if (deg == 6) { *smem = staged_smem_bytes<RT, 6>(); return (const void*)wide_level_staged_kernel<RT, 6>; }
+    return nullptr;
+}
+
+const void* pick_staged(int rt, int fmt, int deg, size_t* smem)
+{
+    *smem = 0;
+    if (fmt != 1) return nullptr;
+    switch (rt) {
+    case 1: return pick_staged_rt<1>(deg, smem);
+    case 2: return pick_staged_rt<2>(deg, smem);
+    case 4: return pick_staged_rt<4>(deg, smem);
+    }
+    return nullptr;
+}
+
 const void* pick_init(int rt)
 {
     return rt == 1 ? (const void*)wide_init_kernel<1> : rt == 2 ? (const void*)wide_init_kernel<2>
@@ -449,8 +663,20 @@ bool plan_sparse_wide(const DevInstance& in, int R, int rt, int device, WidePlan
     p->groups = (R + rt - 1) / rt;
     p->slab = sell_slab_floats(in.n, rt);
     const void* k = pick_level(rt, p->entry, p->deg);
+    p->smem = 0;
+    p->staged = 0;
+    if (const char* e = std::getenv("MARS_WIDE_STAGED"); !e || std::atoi(e) != 0) {
+        size_t sm = 0;
+        if (const void* ks = pick_staged(rt, p->entry, p->deg, &sm)) {
+            if (cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess) {
+                k = ks;
+                p->smem = sm;
+                p->staged = 1;
+            }
+        }
+    }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWideThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWideThreads, p->smem);
     p->grid = sms * (per_sm > 0 ? per_sm : 1);
     p->sms = sms;
     return true;
@@ -474,7 +700,10 @@ cudaError_t launch_wide_level(const DevInstance& in, const DevSolve& s, const De
     DevWide c = w;
     int l = level;
     void* args[] = {&a, &b, &c, &l};
-    return cudaLaunchKernel(pick_level(p.rt, p.entry, p.deg), dim3(p.grid), dim3(kWideThreads), args, 0, st);
+    size_t sm = 0;
+    const void* k = p.staged ? pick_staged(p.rt, p.entry, p.deg, &sm) : pick_level(p.rt, p.entry, p.deg);
+    if (!k) return cudaErrorInvalidValue;
+    return cudaLaunchKernel(k, dim3(p.grid), dim3(kWideThreads), args, p.smem, st);
 }
 
 cudaError_t launch_wide_decide(const DevSolve& s, const DevWide& w, int step, cudaStream_t st)

@@ -226,6 +226,8 @@ struct WidePlan {
     size_t slab = 0;
     int grid = 0;       // CTAs of a level launch
     int sms = 0;
+    int staged = 0;     // regular +-1 lattices: neighbour gathers staged in shared memory
+    size_t smem = 0;    // the level launch's dynamic shared memory
 };
 bool plan_sparse_wide(const DevInstance& in, int R, int rt, int device, WidePlan* p);
 cudaError_t launch_wide_init(const DevInstance& in, const DevSolve& s, const DevWide& w, const WidePlan& p,

@@ -47,6 +47,7 @@ struct ServeReq {
     double total_weight = 0.0, err_bound = 0.0;
     int64_t ring_job = -1;  // serving-ring job index, or -1
     size_t footprint = 0;   // the admission bound; what the request may allocate
+    bool light = false;     // admitted as a serving-ring job (its own in-flight limit)
     bool cancelled = false; // mars_cancel while it ran: discard its results at the end
 };
 
@@ -58,6 +59,7 @@ struct Serve {
     int64_t next_id = 1;
     int max_inflight = 8;
     int inflight = 0;
+    int light_inflight = 0;  // serving-ring jobs in flight (limit kServeLight)
     // The serving ring: sparse requests run as jobs of one persistent kernel
     // (continuous batching: a job published while the kernel runs is picked
     // up by CTAs as they free up). Descriptors are staged in pinned memory
@@ -79,7 +81,22 @@ struct Serve {
     int64_t ring_jobs = 0;          // jobs served through the ring
     int64_t stream_jobs = 0;        // jobs served on their own streams
     int idle_polls = 50;            // about 100 us without work before the kernel exits
+    // SMs the persistent serving kernel, and each sparse request on its own
+    // stream, may hold at once (MARS_SERVE_SPARSE_SMS, default half the
+    // device): their CTAs stay resident while work lasts, and the rest of
+    // the device is left to the dense requests' kernels.
+    int sparse_sms = 0;
+    int sms = 0;
 };
+
+// The grid of a persistent sparse launch planned for the whole device, cut to
+// the serving engine's share of the SMs.
+int serve_sparse_grid(const Serve* sv, int grid)
+{
+    if (sv->sms <= 0 || sv->sparse_sms >= sv->sms) return grid;
+    const int g = (int)((int64_t)grid * sv->sparse_sms / sv->sms);
+    return g > 0 ? g : 1;
+}
 
 void serve_delete(Serve* sv) { delete sv; }
 
@@ -89,6 +106,7 @@ bool serve_ring_init(mars_ctx* c, Serve* sv)
 {
     if (sv->ring) return true;
     if (!env_flag("MARS_SERVE_RING", 1) || !plan_serve_ring(c->device, &sv->plan)) return false;
+    sv->plan.grid = serve_sparse_grid(sv, sv->plan.grid);
     bool ok = cudaMalloc((void**)&sv->ring, sizeof(ServeRing)) == cudaSuccess &&
               cudaMemset(sv->ring, 0, sizeof(ServeRing)) == cudaSuccess &&
               cudaMallocHost((void**)&sv->stage_jobs, sizeof(BatchJob) * kRingCap) == cudaSuccess &&
@@ -146,9 +164,31 @@ int serve_ring_ensure_kernel(mars_ctx* c, Serve* sv)
     return MARS_OK;
 }
 
+// Serving-ring jobs admitted at once, besides the in-flight limit of the
+// other requests.
+constexpr int kServeLight = 64;
+
+bool serve_ring_init(mars_ctx* c, Serve* sv);
+
+// Whether a request runs as a job of the persistent serving kernel: a
+// sequential MARS solve of a sparse integer instance whose magnetisations fit
+// on chip, while the ring has room.
+bool serve_ring_eligible(mars_ctx* c, Serve* sv, const DevInstance& d, const mars_params& p)
+{
+    if (d.dense || !d.integer || p.update != MARS_UPDATE_GS || p.method != MARS_METHOD_MARS) return false;
+    if (!serve_ring_init(c, sv) || sv->tail >= kRingCap) return false;
+    int rt = 1;
+    return ring_job_format(d, sv->plan, &rt) >= 0;
+}
+
 Serve* serve_get(mars_ctx* c)
 {
-    if (!c->serve) c->serve = std::unique_ptr<Serve, void (*)(Serve*)>(new Serve(), serve_delete);
+    if (!c->serve) {
+        c->serve = std::unique_ptr<Serve, void (*)(Serve*)>(new Serve(), serve_delete);
+        Serve* nv = c->serve.get();
+        cudaDeviceGetAttribute(&nv->sms, cudaDevAttrMultiProcessorCount, c->device);
+        nv->sparse_sms = std::max(1, std::min(nv->sms, env_flag("MARS_SERVE_SPARSE_SMS", nv->sms / 2)));
+    }
     Serve* sv = c->serve.get();
     while ((int)sv->streams.size() < sv->max_inflight) {
         cudaStream_t st;
@@ -196,7 +236,7 @@ void serve_free_req(mars_ctx* c, Serve* sv, ServeReq* q)
     }
     if (q->slot >= 0) {
         sv->free_slots.push_back(q->slot);
-        sv->inflight -= 1;
+        (q->light ? sv->light_inflight : sv->inflight) -= 1;
         q->slot = -1;
     }
     q->tc.reset();
@@ -267,9 +307,15 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
     q->err_bound = (in->dev.integer || in->dev.exact_ok)
                        ? 0.0
                        : std::ldexp(in->abs_weight, -53) * (double)(in->info.nnz / 2 + in->dev.n);
+    if (sv->free_slots.empty()) {
+        cudaStream_t ns;
+        MARS_CUDA(c, cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking));
+        sv->free_slots.push_back((int)sv->streams.size());
+        sv->streams.push_back(ns);
+    }
     q->slot = sv->free_slots.back();
     sv->free_slots.pop_back();
-    sv->inflight += 1;
+    (q->light ? sv->light_inflight : sv->inflight) += 1;
     q->st = sv->streams[q->slot];
     cudaStream_t st = q->st;
     const mars_params& p = q->p;
@@ -381,6 +427,7 @@ int serve_launch(mars_ctx* c, Serve* sv, ServeReq* q)
         }
         if (s.jacobi || !plan_sparse_sell(q->dev, R, c->device, &sp))
             sp = plan_sparse(q->dev, R, s.jacobi, c->device);
+        sp.grid = serve_sparse_grid(sv, sp.grid);  // the per-CTA buffers below follow the grid
         rt = sp.rt;
         float* scr = nullptr;
         if (sp.scratch_floats && (rc = get(sp.scratch_floats * sizeof(float), (void**)&scr))) return rc;
@@ -495,7 +542,7 @@ void serve_progress(mars_ctx* c)
         q->bufs.clear();
         if (q->slot >= 0) {
             sv->free_slots.push_back(q->slot);
-            sv->inflight -= 1;
+            (q->light ? sv->light_inflight : sv->inflight) -= 1;
             q->slot = -1;
         }
     }
@@ -519,31 +566,43 @@ void serve_progress(mars_ctx* c)
             }
         }
     }
-    // admit, in arrival order
-    while (!sv->queue.empty() && !sv->free_slots.empty()) {
-        const int64_t id = sv->queue.front();
-        auto it = sv->reqs.find(id);
-        if (it == sv->reqs.end()) { sv->queue.pop_front(); continue; }
+    // admit: serving-ring jobs (small sparse requests) whenever fewer than
+    // kServeLight are in flight, passing requests queued before them; the
+    // others in arrival order while fewer than max_inflight of them run. Both
+    // wait for the HBM budget.
+    bool heavy_blocked = false;
+    for (auto qi = sv->queue.begin(); qi != sv->queue.end();) {
+        auto it = sv->reqs.find(*qi);
+        if (it == sv->reqs.end()) { qi = sv->queue.erase(qi); continue; }
         ServeReq* q = it->second.get();
         Instance* in = find(c, q->inst);
         if (!in) {
-            sv->queue.pop_front();
+            qi = sv->queue.erase(qi);
             fail(c, MARS_ENOTFOUND, "instance %d was freed before its request ran", q->inst);
             serve_mark_failed(c, sv, q, MARS_ENOTFOUND);
             continue;
         }
+        const bool light = serve_ring_eligible(c, sv, in->dev, q->p);
+        if (light ? sv->light_inflight >= kServeLight : heavy_blocked || sv->inflight >= sv->max_inflight) {
+            heavy_blocked |= !light;
+            ++qi;
+            continue;
+        }
         const size_t need = serve_footprint(in->dev, q->p, c->device);
         if (c->budget && c->used + need > c->budget) {
-            if (sv->inflight == 0) {  // it will never fit
-                sv->queue.pop_front();
+            if (sv->inflight + sv->light_inflight == 0) {  // it will never fit
+                qi = sv->queue.erase(qi);
                 fail(c, MARS_ENOMEM, "request needs about %zu bytes; the HBM budget is %zu", need, c->budget);
                 serve_mark_failed(c, sv, q, MARS_ENOMEM);
                 continue;
             }
-            break;  // wait for memory to free up
+            heavy_blocked |= !light;  // wait for memory to free up
+            ++qi;
+            continue;
         }
-        sv->queue.pop_front();
+        qi = sv->queue.erase(qi);
         q->footprint = need;
+        q->light = light;
         const int rc = serve_launch(c, sv, q);
         if (rc) serve_mark_failed(c, sv, q, rc);
     }
@@ -688,7 +747,7 @@ int mars_serve_status(mars_ctx* c, int32_t* queued, int32_t* running)
     serve_progress(c);
     Serve* sv = c->serve.get();
     if (queued) *queued = sv ? (int32_t)sv->queue.size() : 0;
-    if (running) *running = sv ? sv->inflight : 0;
+    if (running) *running = sv ? sv->inflight + sv->light_inflight : 0;
     return MARS_OK;
 }
 

@@ -220,3 +220,42 @@ def test_served_quench_matches_blocking(ctx):
     out = _wait(ctx, [r])
     _same(out[r], ctx.solve(inst, 64, 0.0, 5.0, seed=9, quench=True, geometric=0.75, t_floor=0.5))
     ctx.free(inst)
+
+
+def test_ring_jobs_pass_queued_dense_requests():
+    """Admission by class: with one in-flight slot for the other requests, a
+    dense tensor-core request runs and a second one waits for the slot; a
+    small sparse request submitted after both runs at once as a job of the
+    persistent serving kernel and finishes first. Every result equals its
+    blocking solve."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_05124_gb300 import build, mars
+    build.build()
+    c = mars.Context(0)
+    try:
+        dense = c.add_dense(I.sk_gauss(2048, 21))
+        lat = c.add_csr(*I.ea_lattice(32, 2, 22))
+        c.serve_limits(1)
+        kw = {"precision": "bf16", "c_step": 1 / 32.0}
+        d1 = c.submit(dense, 256, 0.0, 2.0, seed=1, **kw)
+        d2 = c.submit(dense, 256, 0.0, 2.0, seed=2, **kw)
+        small = c.submit(lat, 64, 0.0, 4.0, seed=3)
+        done, order, t0 = {}, [], time.time()
+        while len(done) < 3:
+            for r in (d1, d2, small):
+                if r not in done:
+                    res = c.poll(r)
+                    if res is not None:
+                        done[r] = res
+                        order.append(r)
+            assert time.time() - t0 < 300.0, "served requests did not finish"
+            time.sleep(0.0005)
+        assert order[0] == small and order.index(d1) < order.index(d2)
+        _same(done[d1], c.solve(dense, 256, 0.0, 2.0, seed=1, **kw))
+        _same(done[d2], c.solve(dense, 256, 0.0, 2.0, seed=2, **kw))
+        _same(done[small], c.solve(lat, 64, 0.0, 4.0, seed=3))
+        assert c.serve_status() == (0, 0)
+    finally:
+        c.close()
