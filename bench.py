@@ -74,6 +74,10 @@ EA3_WORKLOAD = {
 # far larger than L2: every magnetisation is read twice per sweep (as the
 # other colour's neighbour and as its own old value) and written once.
 EA3_BYTES_PER_UPDATE = 12.0
+# DRAM bytes per live spin-update of the staged level kernel, from one ncu
+# capture of a launch of the N=10^6 lattice (dram__bytes_read.sum +
+# dram__bytes_write.sum = 3.328 GB for 510 live replicas x 500,000 spins).
+EA3_DRAM_BYTES_PER_UPDATE = 3.328e9 / (510 * 500_000)
 
 # The FP8 variant: dense SK with +-1 couplings (exact in E4M3) on E4M3 tensor
 # cores; the same schedule in units of the couplings' scale sqrt(N).
@@ -566,9 +570,15 @@ def run_mars(args, world, rank, local):
         sh = shape or {}
         rt_used = sh.get("sell_rt", -1) if sh.get("sell_rt", -1) > 0 else 4
         achieved = EA3_BYTES_PER_UPDATE * level_upd / level_s / 1e9 if level_s > 0 else 0.0
+        # DRAM bytes per launch: one ncu capture of the staged kernel at RT=4
+        # (3.328 GB for a launch of 510 live replicas x 500,000 spins, 13.05 B
+        # per live update) scaled by the live updates of a sampled launch;
+        # null for another slot width, whose counters were not taken.
+        upd_launch = level_upd / level_launches if level_launches else 0.0
+        traffic = EA3_DRAM_BYTES_PER_UPDATE * upd_launch if rt_used == 4 else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "kernel": f"wide_level_kernel<RT={rt_used}, +-1 words, degree 6>",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "kernel": f"wide_level_staged_kernel<RT={rt_used}, degree 6> (+-1 words)",
                     "bytes_per_update": EA3_BYTES_PER_UPDATE,
                     "level_launches_sampled": level_launches,
                     "whole_descent_gbs": EA3_BYTES_PER_UPDATE * upd_per_launch / d_mean / 1e9,
