@@ -396,45 +396,67 @@ class Workload:
                          fixed_sweeps=self.fixed, outputs=())
 
 
-def fp32_path_comparison(ctx, n=1024, R=256):
+def fp32_path_comparison(ctx, n=1024, R=256, seeds=range(10)):
     """Time to target energy of the BF16 tensor-core path against the plain
     FP32 SIMT path, on an instance of the default workload's family small
     enough for the FP32 path to finish in seconds: dense SK with
-    J_ij ~ Normal(0, 1/N), T0 ~ U(0, 2), C_step = 1/sqrt(N), the same
-    replicas (seed) on both paths.
+    J_ij ~ Normal(0, 1/N) (instances.sk_gauss(1024, 3)), T0 ~ U(0, 2),
+    C_step = 1/sqrt(N), d_min = 1e-4, k_max = 1000.
 
-    The target the metric names is the FP64 oracle's best energy with a large
-    budget; the oracle cannot reach it within a benchmark run, so the target
-    is the FP32 path's 10th-percentile replica energy (a stated fallback). A
-    path whose fraction p of replicas reach the target in a solve of T
-    seconds needs T ln(0.01) / ln(1 - p) to reach it with probability 0.99."""
+    The target is the FP64 oracle's best energy on the instance with a large
+    budget (1024 replicas), stored by tests/golden/make_sk_gauss1024_target.py.
+    Each path runs one solve of R replicas for every seed 0-9; a seed's time
+    to target is its solve's wall time when the solve's best energy is at or
+    below the target (within 1e-9 relative), else it is not reached. The
+    median over the seeds is reported when at least half reach the target;
+    with P the fraction of all replicas that reach it and t the mean solve
+    time, t ln(0.01) / ln(1 - P) (the time to reach it with probability 0.99)
+    is reported beside it, and the speedup uses the median where both paths
+    have one."""
     import numpy as np
     import torch
 
     from paper_1907_05124_gb300 import instances
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                           "sk_gauss1024_target.json")) as f:
+        golden = json.load(f)
+    target = float(golden["best_energy"])
+    tol = 1e-9 * abs(target)
     inst = ctx.add_dense(instances.sk_gauss(n, 3))
     c = 1.0 / n ** 0.5
-    runs = {}
+    out = {"workload": f"dense SK N={n}, J_ij ~ Normal(0, 1/N), R={R} per solve, T0~U(0,2), "
+                       "C_step=1/sqrt(N), d_min=1e-4, k_max=1000, seeds 0-9 on both paths",
+           "target": f"FP64 oracle's best over {golden['replicas']} replicas "
+                     "(tests/golden/sk_gauss1024_target.json)",
+           "target_energy": target}
     for prec in ("fp32", "bf16"):
         kw = dict(c_step=c, d_min=D_MIN, k_max=K_MAX, precision=prec, outputs=("energies",))
-        ctx.solve(inst, R, 0.0, 2.0, seed=2, fixed_sweeps=1, **kw)  # warm-up (short)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        res = ctx.solve(inst, R, 0.0, 2.0, seed=1, **kw)
-        runs[prec] = (time.perf_counter() - t, res)
+        ctx.solve(inst, R, 0.0, 2.0, seed=100, fixed_sweeps=1, **kw)  # warm-up (short)
+        secs, hit, reached, upd = [], [], 0, 0
+        for sd in seeds:
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            res = ctx.solve(inst, R, 0.0, 2.0, seed=sd, **kw)
+            secs.append(time.perf_counter() - t)
+            hit.append(res.best_energy <= target + tol)
+            reached += int(np.sum(res.energies <= target + tol))
+            upd += res.spin_updates
+        P = reached / (R * len(secs))
+        t_sim = float(np.mean(secs))
+        ttt99 = t_sim * np.log(0.01) / np.log1p(-P) if 0 < P < 1 else (t_sim if P >= 1 else float("inf"))
+        ttt = sorted(s_ if h else float("inf") for s_, h in zip(secs, hit))
+        med = float(np.median(ttt)) if sum(hit) * 2 >= len(hit) else None
+        out[prec] = {"solve_s_mean": t_sim, "seeds_reaching_target": int(sum(hit)), "P": P,
+                     "ttt_median_s": med, "ttt99_s": ttt99,
+                     "spin_updates_per_s": upd / float(np.sum(secs))}
     ctx.free(inst)
-    target = float(np.percentile(runs["fp32"][1].energies, 10))
-    out = {"workload": f"dense SK N={n}, J_ij ~ Normal(0, 1/N), R={R}, T0~U(0,2), C_step=1/sqrt(N), "
-                       "d_min=1e-4, k_max=1000, the same replicas on both paths",
-           "target": "FP32 path's 10th-percentile replica energy (fallback: the FP64 oracle's "
-                     "large-budget best is out of reach within a benchmark run)",
-           "target_energy": target}
-    for prec, (sec, res) in runs.items():
-        p = float(np.mean(res.energies <= target))
-        ttt = sec * np.log(0.01) / np.log1p(-p) if 0 < p < 1 else (sec if p >= 1 else float("inf"))
-        out[prec] = {"solve_s": sec, "p_target": p, "ttt99_s": ttt, "best_energy": res.best_energy,
-                     "spin_updates_per_s": res.spin_updates / sec}
-    out["speedup_at_equal_ttt"] = out["fp32"]["ttt99_s"] / out["bf16"]["ttt99_s"]
+    a, b_ = out["fp32"], out["bf16"]
+    if a["ttt_median_s"] is not None and b_["ttt_median_s"] is not None:
+        out["speedup_at_equal_ttt"] = a["ttt_median_s"] / b_["ttt_median_s"]
+        out["speedup_from"] = "median over seeds 0-9"
+    else:
+        out["speedup_at_equal_ttt"] = a["ttt99_s"] / b_["ttt99_s"] if b_["ttt99_s"] > 0 else None
+        out["speedup_from"] = "t ln(0.01) / ln(1 - P)"
     return out
 
 

@@ -614,3 +614,23 @@ def test_nmfa_noise_enters_with_scale_sigma():
     z2 = (0.5 * np.arctanh(-r2["m"]) / 0.3).ravel()
     assert stats.kstest(z2, "norm").pvalue > 1e-3
     assert abs(np.corrcoef(z, z2)[0, 1]) < 0.06
+
+
+def test_time_to_target_golden_is_the_oracles_own():
+    """The stored time-to-target energy of the dense SK instance N = 1024 is
+    what the oracle returns for the stored best replica: re-running that one
+    replica (its start state from the oracle's draw, seed 0) reproduces the
+    energy exactly, and no replica is stored as better than that."""
+    import json
+    import os
+    from paper_1907_05124_gb300 import instances
+    path = os.path.join(os.path.dirname(__file__), "golden", "sk_gauss1024_target.json")
+    rec = json.load(open(path))
+    r = rec["best_replica"]
+    m0, t0 = O.draw_replicas(0, r + 1, 1024, 0.0, 2.0)
+    assert float(t0[r]) == rec["best_replica_t0"]
+    oi = O.Instance.dense(instances.sk_gauss(1024, 3))
+    o = O.mars_solve(oi, m0[r:r + 1], t0[r:r + 1], c_step=1.0 / np.sqrt(1024), d_min=1e-4, k_max=1000,
+                     want_m=False)
+    assert float(o["energy"][0]) == rec["best_energy"]
+    assert rec["hits"] >= 1 and rec["energy_p10"] >= rec["best_energy"]
