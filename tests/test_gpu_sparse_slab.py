@@ -166,3 +166,24 @@ def test_full_size_lattice_level_synchronous(ctx, monkeypatch):
     assert (r.replica_sweeps >= r.replica_levels).all()
     assert r.level_launches > 0 and r.level_seconds > 0
     ctx.free(inst)
+
+
+@pytest.mark.parametrize("rt", [1, 4])
+def test_staged_and_register_level_kernels_agree(ctx, monkeypatch, rt):
+    """On a regular lattice the level launch stages the next slice's neighbour
+    rows in shared memory by asynchronous copies; MARS_WIDE_STAGED=0 keeps
+    them in registers. Both sum each field in the same order: identical
+    outputs under the paper's stopping rule."""
+    monkeypatch.setenv("MARS_SELL_WIDE", "1")
+    csr = I.ea_lattice(40, 3, 8)
+    inst = ctx.add_csr(*csr, order=I.greedy_colour_order(csr))
+    ctx.set_shape(inst, sell_rt=rt)
+    R = 21
+    m0, t0 = I.replica_inputs(R, csr.n, 0.0, 5.0, 81)
+    out = {}
+    for staged in ("1", "0"):
+        monkeypatch.setenv("MARS_WIDE_STAGED", staged)
+        out[staged] = ctx.solve(inst, R, 0.0, 5.0, m0=m0, t0=t0,
+                                outputs=("m_final", "sweeps", "levels", "capped", "energies", "spins"))
+    _same(out["1"], out["0"])
+    ctx.free(inst)
