@@ -343,11 +343,11 @@ struct ChainSpin {
 // Shared memory of the chain: the FP32 block J[p][p] (and J[p][p+1] when the
 // chain feeds the next panel), the CTA's ChainSpin rows and the mbarrier of
 // the bulk copies.
-template <int RPW, bool NEXT>
+template <int RPW, bool NEXT, int CW = kChainWarps>
 struct ChainSmem {
     static constexpr int kJ = kBM * kBM * (int)sizeof(float);
     static constexpr int kBlocks = NEXT ? 2 : 1;
-    static constexpr int kCs = kChainWarps * RPW * kBM * (int)sizeof(ChainSpin);
+    static constexpr int kCs = CW * RPW * kBM * (int)sizeof(ChainSpin);
     static constexpr int kBytes = kBlocks * kJ + kCs + 16;
 };
 
@@ -373,19 +373,19 @@ struct ChainSmem {
 // could run beside this chain; each new s_a goes into the next panel's
 // fields here instead, in FP32 (gx_out), from the block J[p][p+1]. Lane j
 // owns next-panel spins 4 (32/RPW) u + 4 j + i, read as float4.
-// The chain of panel p for the RPC = kChainWarps * RPW replica slots from
-// slot0, on the CTA's first kChainWarps warps. Jb (and Jn when NEXT) hold the
+// The chain of panel p for the RPC = CW * RPW replica slots from slot0, on
+// the CTA's first CW warps. Jb (and Jn when NEXT) hold the
 // panel's blocks once `bar` completes its phase of parity `parity`; the caller
 // issued their copies. With `pdl` the function orders itself after the
 // stream's previous kernel (griddepcontrol) between the loads that kernel
 // does not write and those it does. *s_ok is a shared word.
-template <int RPW, bool NEXT, bool FP8>
+template <int RPW, bool NEXT, bool FP8, int CW = kChainWarps>
 __device__ __forceinline__ void chain_body(const TcState& t, int p, const float* __restrict__ G,
                                            const float* __restrict__ gx_in, float* __restrict__ gx_out,
                                            bool g_early, bool pdl, int slot0, const float* Jb, const float* Jn,
                                            ChainSpin* cs_all, uint64_t* bar, uint32_t parity, int* s_ok)
 {
-    constexpr int LPR = 32 / RPW, SPL = kBM / LPR, RPC = kChainWarps * RPW;
+    constexpr int LPR = 32 / RPW, SPL = kBM / LPR, RPC = CW * RPW;
     constexpr int kSplitCap = kChainMaxSplit / RPW;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int p0 = p * kBM;
@@ -403,13 +403,13 @@ __device__ __forceinline__ void chain_body(const TcState& t, int p, const float*
     const bool valid = slot < t.R && t.active[slot];
     const float invT = valid ? t.invT[slot] : 0.f;  // idle groups compute and store nothing
     // RPC replicas x 32 four-spin pieces = RPW pieces per thread.
-    static_assert(RPC * (kBM / 4) == RPW * kChainWarps * 32, "one piece per thread and replica slot");
+    static_assert(RPC * (kBM / 4) == RPW * CW * 32, "one piece per thread and replica slot");
     float4 part[RPW][kSplitCap], gx[RPW], so[RPW];
     uint2 sbw[RPW];  // the four spins' low-precision copies (BF16, or E4M3 in .x)
     auto load_fields = [&]() {
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
-            const int e = tid + k * kChainWarps * 32;
+            const int e = tid + k * CW * 32;
             const int rr = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
             const int sl = slot0 + rr < t.R ? slot0 + rr : 0;
 #pragma unroll
@@ -421,7 +421,7 @@ __device__ __forceinline__ void chain_body(const TcState& t, int p, const float*
     };
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
-        const int e = tid + k * kChainWarps * 32;
+        const int e = tid + k * CW * 32;
         const int rr = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
         const int sl = slot0 + rr < t.R ? slot0 + rr : 0;
         const size_t idx = (size_t)sl * t.n_pad + p0 + a4;
@@ -439,7 +439,7 @@ __device__ __forceinline__ void chain_body(const TcState& t, int p, const float*
     if (!g_early) load_fields();
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
-        const int e = tid + k * kChainWarps * 32;
+        const int e = tid + k * CW * 32;
         const int rr = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
         const int sl = slot0 + rr < t.R ? slot0 + rr : 0;
         gx[k] = gx_in ? *reinterpret_cast<const float4*>(gx_in + (size_t)sl * kBM + a4)
@@ -447,7 +447,7 @@ __device__ __forceinline__ void chain_body(const TcState& t, int p, const float*
     }
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
-        const int e = tid + k * kChainWarps * 32;
+        const int e = tid + k * CW * 32;
         const int rr = e / (kBM / 4), a4 = (e % (kBM / 4)) * 4;
         float4 f = part[k][0];
 #pragma unroll
@@ -593,12 +593,12 @@ __device__ __forceinline__ void chain_body(const TcState& t, int p, const float*
 // The chain as its own launch, one CTA per RPC replica slots. Thread 0 starts
 // the copies of the panel's blocks (instance data, independent of the
 // previous kernels) before chain_body's programmatic wait.
-template <int RPW, bool NEXT, bool FP8>
-__global__ void __launch_bounds__(kChainWarps * 32, 1)
+template <int RPW, bool NEXT, bool FP8, int CW>
+__global__ void __launch_bounds__(CW * 32, 1)
     panel_chain_kernel(TcState t, int p, const float* __restrict__ G, const float* __restrict__ gx_in,
                        float* __restrict__ gx_out, int g_early)
 {
-    using L = ChainSmem<RPW, NEXT>;
+    using L = ChainSmem<RPW, NEXT, CW>;
     extern __shared__ __align__(16) unsigned char chain_smem[];
     float* Jb = reinterpret_cast<float*>(chain_smem);  // J[p][p] (symmetric)
     float* Jn = Jb + kBM * kBM;                         // NEXT: J[p][p+1], row a = this panel's spin
@@ -612,8 +612,8 @@ __global__ void __launch_bounds__(kChainWarps * 32, 1)
         tc::bulk_load(Jb, t.Jdiag + (size_t)p * kBM * kBM, L::kJ, bar);
         if (NEXT) tc::bulk_load(Jn, t.Jsup + (size_t)p * kBM * kBM, L::kJ, bar);
     }
-    chain_body<RPW, NEXT, FP8>(t, p, G, gx_in, gx_out, g_early != 0, true, blockIdx.x * (kChainWarps * RPW), Jb,
-                               Jn, cs_all, bar, 0u, &s_ok);
+    chain_body<RPW, NEXT, FP8, CW>(t, p, G, gx_in, gx_out, g_early != 0, true, blockIdx.x * (CW * RPW), Jb,
+                                   Jn, cs_all, bar, 0u, &s_ok);
 }
 
 // Start states in slot order: slot j holds replica rep[j].
@@ -1027,15 +1027,15 @@ cudaError_t launch_tc_pair_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, 
     return launch_pdl(k, dim3(n_tiles, splitk), dim3(128), args, smem, st);
 }
 
-template <int RPW, bool NEXT, bool FP8>
+template <int RPW, bool NEXT, bool FP8, int CW>
 cudaError_t launch_chain_as(const TcState& t, int p, const float* G, const float* gx_in, float* gx_out,
                             int g_early, cudaStream_t st)
 {
-    constexpr int smem = ChainSmem<RPW, NEXT>::kBytes;
-    cudaError_t e = cudaFuncSetAttribute(panel_chain_kernel<RPW, NEXT, FP8>,
+    constexpr int smem = ChainSmem<RPW, NEXT, CW>::kBytes;
+    cudaError_t e = cudaFuncSetAttribute(panel_chain_kernel<RPW, NEXT, FP8, CW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int per_cta = kChainWarps * RPW;
+    const int per_cta = CW * RPW;
     TcState tt = t;
     int pp = p;
     const float* a0 = G;
@@ -1043,36 +1043,45 @@ cudaError_t launch_chain_as(const TcState& t, int p, const float* G, const float
     float* a2 = gx_out;
     int ge = g_early;
     void* args[] = {&tt, &pp, &a0, &a1, &a2, &ge};
-    return launch_pdl((const void*)panel_chain_kernel<RPW, NEXT, FP8>, dim3((t.R + per_cta - 1) / per_cta),
-                      dim3(kChainWarps * 32), args, smem, st);
+    return launch_pdl((const void*)panel_chain_kernel<RPW, NEXT, FP8, CW>, dim3((t.R + per_cta - 1) / per_cta),
+                      dim3(CW * 32), args, smem, st);
 }
 
-template <bool FP8>
-cudaError_t launch_chain_lo(const TcState& t, int p, int rpw, bool next, const float* G, const float* gx_in,
+template <bool FP8, int CW>
+cudaError_t launch_chain_cw(const TcState& t, int p, int rpw, bool next, const float* G, const float* gx_in,
                             float* gx_out, int ge, cudaStream_t st)
 {
     switch (rpw * 2 + (next ? 1 : 0)) {
-    case 2: return launch_chain_as<1, false, FP8>(t, p, G, gx_in, gx_out, ge, st);
-    case 3: return launch_chain_as<1, true, FP8>(t, p, G, gx_in, gx_out, ge, st);
-    case 4: return launch_chain_as<2, false, FP8>(t, p, G, gx_in, gx_out, ge, st);
-    case 5: return launch_chain_as<2, true, FP8>(t, p, G, gx_in, gx_out, ge, st);
-    case 8: return launch_chain_as<4, false, FP8>(t, p, G, gx_in, gx_out, ge, st);
-    case 9: return launch_chain_as<4, true, FP8>(t, p, G, gx_in, gx_out, ge, st);
+    case 2: return launch_chain_as<1, false, FP8, CW>(t, p, G, gx_in, gx_out, ge, st);
+    case 3: return launch_chain_as<1, true, FP8, CW>(t, p, G, gx_in, gx_out, ge, st);
+    case 4: return launch_chain_as<2, false, FP8, CW>(t, p, G, gx_in, gx_out, ge, st);
+    case 5: return launch_chain_as<2, true, FP8, CW>(t, p, G, gx_in, gx_out, ge, st);
+    case 8: return launch_chain_as<4, false, FP8, CW>(t, p, G, gx_in, gx_out, ge, st);
+    case 9: return launch_chain_as<4, true, FP8, CW>(t, p, G, gx_in, gx_out, ge, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, const float* gx_in,
+template <bool FP8>
+cudaError_t launch_chain_lo(const TcState& t, int p, int rpw, int cw, bool next, const float* G,
+                            const float* gx_in, float* gx_out, int ge, cudaStream_t st)
+{
+    return cw == 4 ? launch_chain_cw<FP8, 4>(t, p, rpw, next, G, gx_in, gx_out, ge, st)
+                   : launch_chain_cw<FP8, kChainWarps>(t, p, rpw, next, G, gx_in, gx_out, ge, st);
+}
+
+cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, int cw, const float* G, const float* gx_in,
                             float* gx_out, bool g_early, cudaStream_t st)
 {
     if (rpw != 1 && rpw != 2 && rpw != 4) return cudaErrorInvalidValue;
+    if (cw != 4 && cw != kChainWarps) return cudaErrorInvalidValue;
     if (t.splitk < 1 || t.splitk > kChainMaxSplit / rpw) return cudaErrorInvalidValue;
     // the CTA's slots must lie inside G's R_pad rows (R_pad is a multiple of 128)
-    if (t.R_pad % (kChainWarps * rpw) != 0) return cudaErrorInvalidValue;
+    if (t.R_pad % (cw * rpw) != 0) return cudaErrorInvalidValue;
     const bool next = gx_out != nullptr;
     if (next && !t.Jsup) return cudaErrorInvalidValue;
-    return t.S8 ? launch_chain_lo<true>(t, p, rpw, next, G, gx_in, gx_out, g_early ? 1 : 0, st)
-                : launch_chain_lo<false>(t, p, rpw, next, G, gx_in, gx_out, g_early ? 1 : 0, st);
+    return t.S8 ? launch_chain_lo<true>(t, p, rpw, cw, next, G, gx_in, gx_out, g_early ? 1 : 0, st)
+                : launch_chain_lo<false>(t, p, rpw, cw, next, G, gx_in, gx_out, g_early ? 1 : 0, st);
 }
 
 cudaError_t launch_tc_init(const TcState& t, cudaStream_t st)

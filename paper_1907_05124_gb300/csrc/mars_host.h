@@ -182,6 +182,7 @@ struct TcRun {
     // chain done). G and the chains' next-panel fields Gx alternate between
     // two buffers by panel parity.
     int rpw = 1;
+    int chain_warps = 8;               // warps per chain CTA (8, or 4 with few replicas active)
     bool overlap = false;
     bool pair = false;                 // panels 2q, 2q+1 share one GEMM
     std::vector<int> timed_rows;       // rows of each GEMM the profiled sweep timed

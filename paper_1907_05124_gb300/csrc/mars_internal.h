@@ -316,7 +316,9 @@ constexpr int kChainMaxSplit = 16;
 // panel q's K blocks (from g.skip_kb) out; partials to g.G and g.G1.
 cudaError_t launch_tc_pair_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, const TcPanel& g, int n_tiles,
                                 int splitk, cudaStream_t st);
-cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, const float* G, const float* gx_in,
+// cw: warps per chain CTA, 8 or 4 (fewer replica slots per CTA, so a few
+// active replicas spread over more SMs); the per-replica arithmetic is the same.
+cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, int cw, const float* G, const float* gx_in,
                             float* gx_out, bool g_early, cudaStream_t st);
 cudaError_t launch_tc_init(const TcState& t, cudaStream_t st);
 cudaError_t launch_tc_advance(const TcState& t, cudaStream_t st);

@@ -142,14 +142,22 @@ int tc_plan(mars_ctx* c, TcRun* run, int32_t active, int32_t prefix)
         }
     }
     run->persist = false;
+    // Four warps per chain CTA when those CTAs fit in half of the SMs: with
+    // two warps per scheduler the 128-step chain is partly issue-bound (on a
+    // GB300 at N = 8192 with 128 replicas active a step took 55 ns with 8
+    // warps per CTA and 42 ns with 4); with more replicas the extra CTAs
+    // crowd out the GEMM (1024 active: 12.8 against 18.1 us per panel).
+    int cw = (chain_slots + 4 * rpw - 1) / (4 * rpw) <= run->sms / 2 ? 4 : 8;
+    if (const int f = env_flag("MARS_TC_CHAIN_WARPS", 0); f == 4 || f == 8) cw = f;
     if (run->exec && rpw == run->rpw && ovl == run->overlap && pr == run->pair && splitk == run->splitk &&
-        tiles == run->gemm_tiles && chain_slots == run->chain_slots)
+        tiles == run->gemm_tiles && chain_slots == run->chain_slots && cw == run->chain_warps)
         return MARS_OK;
     if (run->exec) cudaGraphExecDestroy(run->exec);
     if (run->graph) cudaGraphDestroy(run->graph);
     run->exec = nullptr;
     run->graph = nullptr;
     run->rpw = rpw;
+    run->chain_warps = cw;
     run->overlap = ovl;
     run->pair = pr;
     run->splitk = splitk;
@@ -308,10 +316,10 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
             }
             // chain pp's fields come from the GEMM just before it; chain pp+1's
             // from the same GEMM, two kernels back
-            MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[0], nullptr, two ? run->Gx[0] : nullptr,
+            MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->chain_warps, run->Gbuf[0], nullptr, two ? run->Gx[0] : nullptr,
                                          false, st));
             if (two)
-                MARS_CUDA(c, launch_tc_chain(tc, pp + 1, run->rpw, run->Gbuf[1], run->Gx[0], nullptr, true, st));
+                MARS_CUDA(c, launch_tc_chain(tc, pp + 1, run->rpw, run->chain_warps, run->Gbuf[1], run->Gx[0], nullptr, true, st));
         }
         MARS_CUDA(c, launch_tc_advance(run->t, st));
         return MARS_OK;
@@ -341,7 +349,7 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
         float* gx_out = ov && pp + 1 < P ? run->Gx[(pp + 1) & 1] : nullptr;
         // the GEMM's event edge into the chain may be captured as a
         // programmatic edge too, so its fields are read after the wait
-        MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->Gbuf[pp & 1], gx_in, gx_out, false, st));
+        MARS_CUDA(c, launch_tc_chain(tc, pp, run->rpw, run->chain_warps, run->Gbuf[pp & 1], gx_in, gx_out, false, st));
         if (ov) MARS_CUDA(c, cudaEventRecord(run->ev[2 + 2 * pp], st));
     }
     MARS_CUDA(c, launch_tc_advance(run->t, st));

@@ -396,3 +396,29 @@ def test_persistent_sweeps_match_oracle(ctx, monkeypatch):
     assert np.array_equal(g.energies, O.energies(oi, g.spins))
     assert (g.replica_sweeps > 3).any()  # several sweeps, so several batches of the launch
     ctx.free(inst)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_chain_warps_do_not_change_results(ctx, monkeypatch, precision):
+    """With few replicas active the plan runs each chain CTA with 4 warps
+    instead of 8 (more CTAs, one warp per scheduler). A replica's chain is
+    the same arithmetic either way: a whole solve under the paper's stopping
+    rule returns identical spins, final magnetisations, energies and counts
+    with 4 and with 8 chain warps forced."""
+    n, R = 1024, 200
+    J = I.sk_pm1(n, 41)
+    inst = ctx.add_dense(J)
+    m0, t0 = I.replica_inputs(R, n, 0.0, 8.0, 42)
+    out = {}
+    for cw in ("4", "8"):
+        monkeypatch.setenv("MARS_TC_CHAIN_WARPS", cw)
+        out[cw] = ctx.solve(inst, R, 0.0, 8.0, c_step=0.5, m0=m0, t0=t0, precision=precision,
+                            outputs=("energies", "spins", "m_final", "sweeps", "levels", "capped"))
+    a, b = out["4"], out["8"]
+    assert np.array_equal(a.energies, b.energies) and np.array_equal(a.spins, b.spins)
+    assert np.array_equal(a.m_final, b.m_final)
+    assert np.array_equal(a.replica_sweeps, b.replica_sweeps)
+    assert np.array_equal(a.replica_levels, b.replica_levels)
+    assert np.array_equal(a.replica_capped, b.replica_capped)
+    assert a.replica_sweeps.max() > a.replica_levels.max()
+    ctx.free(inst)
