@@ -904,6 +904,76 @@ __global__ void tc_prefix_kernel(TcState t)
     if (threadIdx.x == 0) { t.counters[0] = s_max; t.counters[1] = s_cnt; }
 }
 
+// The compaction's order of the slots below the prefix: active ones first,
+// then finished ones, each in slot order (a block scan), and the new active
+// prefix. One CTA of 1024 threads; thread k owns a contiguous run of slots.
+__global__ void __launch_bounds__(1024) tc_compact_perm_kernel(TcState t, TcCompact cp, int prefix)
+{
+    __shared__ int s_warp[32];
+    __shared__ int s_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (prefix + 1023) / 1024;
+    const int q0 = min(prefix, tid * per), q1 = min(prefix, q0 + per);
+    int cnt = 0;
+    for (int q = q0; q < q1; ++q) cnt += t.active[q] != 0;
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int v = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        s_warp[lane] = v;
+        if (lane == 31) s_total = v;
+    }
+    __syncthreads();
+    const int before = x - cnt + (warp > 0 ? s_warp[warp - 1] : 0);  // active slots before q0
+    const int total = s_total;
+    int a = before, f = total + (q0 - before);  // finished slots before q0 go after every active one
+    for (int q = q0; q < q1; ++q) {
+        if (t.active[q]) cp.perm[a++] = q;
+        else cp.perm[f++] = q;
+    }
+    if (tid == 0) t.counters[0] = total;
+}
+
+// Gather every per-slot array of the slots below the prefix into the
+// scratch in the new order.
+__global__ void tc_compact_gather_kernel(TcState t, const int32_t* rep, TcCompact cp, int prefix)
+{
+    const size_t total = (size_t)prefix * t.n_pad;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(idx / t.n_pad), a = (int)(idx % t.n_pad);
+        const size_t src = (size_t)cp.perm[q] * t.n_pad + a;
+        cp.S[idx] = t.S[src];
+        if (t.S8)
+            cp.S8[idx] = t.S8[src];
+        else
+            cp.Sb[idx] = t.Sb[src];
+    }
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < prefix; q += gridDim.x * blockDim.x) {
+        const int o = cp.perm[q];
+        cp.T[q] = t.T[o];
+        cp.invT[q] = t.invT[o];
+        cp.d[q] = t.d[o];
+        cp.active[q] = t.active[o];
+        cp.levels[q] = t.levels[o];
+        cp.lvl_sweeps[q] = t.lvl_sweeps[o];
+        cp.sweeps[q] = t.sweeps[o];
+        cp.capped[q] = t.capped[o];
+        cp.rep[q] = rep[o];
+    }
+}
+
 // Sign-round, outputs in caller labels and exact energy, one CTA per slot.
 __global__ void __launch_bounds__(256) tc_finalize_kernel(TcState t, DevInstance in, DevSolve s)
 {
@@ -1132,6 +1202,36 @@ cudaError_t launch_tc_advance(const TcState& t, cudaStream_t st)
     if (e != cudaSuccess) return e;
     tc_prefix_kernel<<<1, 1024, 0, st>>>(t);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tc_compact(const TcState& t, int32_t* rep, const TcCompact& cp, int prefix, cudaStream_t st)
+{
+    if (prefix <= 0 || prefix > t.R) return cudaErrorInvalidValue;
+    tc_compact_perm_kernel<<<1, 1024, 0, st>>>(t, cp, prefix);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    tc_compact_gather_kernel<<<1024, 256, 0, st>>>(t, rep, cp, prefix);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t rows = (size_t)prefix * t.n_pad;
+    auto back = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+    };
+    if ((e = back(t.S, cp.S, rows * sizeof(float))) != cudaSuccess) return e;
+    if (t.S8) {
+        if ((e = back(t.S8, cp.S8, rows)) != cudaSuccess) return e;
+    } else if ((e = back(t.Sb, cp.Sb, rows * sizeof(__nv_bfloat16))) != cudaSuccess) {
+        return e;
+    }
+    const size_t q = (size_t)prefix;
+    if ((e = back(t.T, cp.T, q * sizeof(double))) != cudaSuccess) return e;
+    if ((e = back(t.invT, cp.invT, q * sizeof(float))) != cudaSuccess) return e;
+    if ((e = back(t.d, cp.d, q * sizeof(float))) != cudaSuccess) return e;
+    if ((e = back(t.active, cp.active, q * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = back(t.levels, cp.levels, q * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = back(t.lvl_sweeps, cp.lvl_sweeps, q * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = back(t.sweeps, cp.sweeps, q * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = back(t.capped, cp.capped, q * sizeof(int32_t))) != cudaSuccess) return e;
+    return back(rep, cp.rep, q * sizeof(int32_t));
 }
 
 cudaError_t launch_tc_prefix(const TcState& t, cudaStream_t st)

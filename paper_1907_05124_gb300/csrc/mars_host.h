@@ -202,6 +202,13 @@ struct TcRun {
     // launch's shape and its counters (2 x kMaxBatch x P + 1 words).
     bool persist = false;
     bool allow_persist = false;        // blocking solves only (not served requests)
+    // Between batches the active replicas move to the first slots, so that
+    // the plan (GEMM tiles, chain CTAs) covers only them: blocking solves,
+    // whose scratch `cp` the solve allocates; rep_mut is t.rep's buffer.
+    bool compact = false;
+    TcCompact cp;
+    int32_t* rep_mut = nullptr;
+    int64_t compactions = 0;
     TcPersist pp;
     int32_t* flags = nullptr;
     ~TcRun()

@@ -320,6 +320,29 @@ cudaError_t launch_tc_pair_gemm(const CUtensorMap& tmJ, const CUtensorMap& tmS, 
 // active replicas spread over more SMs); the per-replica arithmetic is the same.
 cudaError_t launch_tc_chain(const TcState& t, int p, int rpw, int cw, const float* G, const float* gx_in,
                             float* gx_out, bool g_early, cudaStream_t st);
+// Compaction of the active replicas into the first slots: scratch of the
+// same shapes as TcState's per-slot arrays (rows of n_pad spins for S and its
+// low-precision copy) and the permutation.
+struct TcCompact {
+    int32_t* perm = nullptr;          // new slot -> old slot, below the prefix
+    float* S = nullptr;
+    __nv_bfloat16* Sb = nullptr;
+    uint8_t* S8 = nullptr;
+    double* T = nullptr;
+    float* invT = nullptr;
+    float* d = nullptr;
+    int32_t* active = nullptr;
+    int32_t* levels = nullptr;
+    int32_t* lvl_sweeps = nullptr;
+    int32_t* sweeps = nullptr;
+    int32_t* capped = nullptr;
+    int32_t* rep = nullptr;
+};
+// Move the active slots of [0, prefix) to the front, in slot order, and the
+// finished ones behind them, in slot order; every per-slot array (magnetisations,
+// their low-precision copy, level state, counts, slot -> replica) moves with
+// its slot. rep is t.rep's writable buffer. Sets t.counters[0] to the active count.
+cudaError_t launch_tc_compact(const TcState& t, int32_t* rep, const TcCompact& cp, int prefix, cudaStream_t st);
 cudaError_t launch_tc_init(const TcState& t, cudaStream_t st);
 cudaError_t launch_tc_advance(const TcState& t, cudaStream_t st);
 cudaError_t launch_tc_prefix(const TcState& t, cudaStream_t st);

@@ -362,6 +362,14 @@ int tc_enqueue_sweep(mars_ctx* c, TcRun* run, cudaStream_t st, bool timed)
 int tc_enqueue_batch(mars_ctx* c, TcRun* run, cudaStream_t st)
 {
     int rc;
+    // Finished replicas below the active prefix: move the active ones to the
+    // front (a replica's arithmetic does not depend on its slot).
+    if (run->compact && run->h_counters && run->h_counters[1] > 0 &&
+        run->h_counters[0] - run->h_counters[1] >= 16) {
+        MARS_CUDA(c, launch_tc_compact(run->t, run->rep_mut, run->cp, run->h_counters[0], st));
+        run->h_counters[0] = run->h_counters[1];
+        run->compactions += 1;
+    }
     if (run->active_at_batch > 0 &&
         (rc = tc_plan(c, run, run->active_at_batch, run->h_counters ? run->h_counters[0] : run->t.R)))
         return rc;
@@ -449,6 +457,18 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     };
     if ((rc = tc_setup(c, in->dev, s, rep, t0_max, p->precision == MARS_FP8, st, get, &run))) return rc;
     prof->launches += 2;  // start states, active prefix
+    if (env_flag("MARS_TC_COMPACT", 1) != 0 && s.R > kTcBN) {
+        const size_t R = (size_t)s.R, rows = R * run.t.n_pad;
+        TcCompact& cp = run.cp;
+        if ((rc = S.get(R, &cp.perm)) || (rc = S.get(rows, &cp.S)) ||
+            (run.t.S8 ? (rc = S.get(rows, &cp.S8)) : (rc = S.get(rows, &cp.Sb))) || (rc = S.get(R, &cp.T)) ||
+            (rc = S.get(R, &cp.invT)) || (rc = S.get(R, &cp.d)) || (rc = S.get(R, &cp.active)) ||
+            (rc = S.get(R, &cp.levels)) || (rc = S.get(R, &cp.lvl_sweeps)) || (rc = S.get(R, &cp.sweeps)) ||
+            (rc = S.get(R, &cp.capped)) || (rc = S.get(R, &cp.rep)))
+            return rc;
+        run.compact = true;
+        run.rep_mut = rep;
+    }
     int32_t* pinned = nullptr;
     MARS_CUDA(c, cudaMallocHost((void**)&pinned, 4 * sizeof(int32_t)));
     run.h_counters = pinned;
@@ -458,6 +478,7 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     cudaError_t se = cudaStreamSynchronize(st);
     run.active_at_batch = run.h_counters[1];
     int state = se == cudaSuccess ? (run.h_counters[1] > 0 ? 1 : 0) : -1;
+    int64_t compactions_seen = 0;
     while (state == 1) {
         const int32_t active_now = run.active_at_batch;
         if ((rc = tc_enqueue_batch(c, &run, st))) { cudaFreeHost(pinned); return rc; }
@@ -465,6 +486,8 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
         // prefix; a persistent batch is one kernel and the prefix
         const int gemms = run.pair ? (run.P + 1) / 2 : run.P;
         prof->launches += run.persist ? 2 : (int64_t)run.batch * (gemms + run.P + 2);
+        prof->launches += 2 * (run.compactions - compactions_seen);  // order and gather
+        compactions_seen = run.compactions;
         se = cudaStreamSynchronize(st);
         if (se != cudaSuccess) break;
         for (size_t e = 0; e < run.timed_rows.size(); ++e) {

@@ -422,3 +422,31 @@ def test_chain_warps_do_not_change_results(ctx, monkeypatch, precision):
     assert np.array_equal(a.replica_capped, b.replica_capped)
     assert a.replica_sweeps.max() > a.replica_levels.max()
     ctx.free(inst)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_compaction_does_not_change_results(ctx, monkeypatch, precision):
+    """Between batches of sweeps the active replicas move to the first slots,
+    so that the GEMM tiles and chain CTAs cover only them. Start temperatures
+    spread over U(0, 8) with C_step 0.5 make replicas finish at different
+    times; the whole solve with compaction equals the one without (spins,
+    final magnetisations, energies and counts), and compaction did run (its
+    two kernels per compaction add to the launch count)."""
+    n, R = 1024, 300
+    J = I.sk_pm1(n, 43)
+    inst = ctx.add_dense(J)
+    m0, t0 = I.replica_inputs(R, n, 0.0, 8.0, 44)
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("MARS_TC_COMPACT", flag)
+        out[flag] = ctx.solve(inst, R, 0.0, 8.0, c_step=0.5, m0=m0, t0=t0, precision=precision,
+                              outputs=("energies", "spins", "m_final", "sweeps", "levels", "capped"))
+    a, b = out["1"], out["0"]
+    assert np.array_equal(a.energies, b.energies) and np.array_equal(a.spins, b.spins)
+    assert np.array_equal(a.m_final, b.m_final)
+    assert np.array_equal(a.replica_sweeps, b.replica_sweeps)
+    assert np.array_equal(a.replica_levels, b.replica_levels)
+    assert np.array_equal(a.replica_capped, b.replica_capped)
+    assert a.best_energy == b.best_energy and a.best_replica == b.best_replica
+    assert a.kernel_launches > b.kernel_launches
+    ctx.free(inst)
