@@ -457,8 +457,17 @@ int run_dense_tc(mars_ctx* c, Instance* in, const mars_params* p, const DevSolve
     };
     if ((rc = tc_setup(c, in->dev, s, rep, t0_max, p->precision == MARS_FP8, st, get, &run))) return rc;
     prof->launches += 2;  // start states, active prefix
-    if (env_flag("MARS_TC_COMPACT", 1) != 0 && s.R > kTcBN) {
-        const size_t R = (size_t)s.R, rows = R * run.t.n_pad;
+    // The compaction's scratch (a copy of the per-slot arrays) is taken only
+    // when it fits in half of the free device memory and of what the budget
+    // has left; otherwise the solve runs without compaction.
+    const size_t cp_rows = (size_t)s.R * run.t.n_pad;
+    const size_t cp_bytes = cp_rows * (sizeof(float) + (run.t.S8 ? 1 : sizeof(__nv_bfloat16))) +
+                            (size_t)s.R * (sizeof(double) + 2 * sizeof(float) + 7 * sizeof(int32_t));
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const bool cp_fits = 2 * cp_bytes <= free_b && (!c->budget || c->used + 2 * cp_bytes <= c->budget);
+    if (env_flag("MARS_TC_COMPACT", 1) != 0 && s.R > kTcBN && cp_fits) {
+        const size_t R = (size_t)s.R, rows = cp_rows;
         TcCompact& cp = run.cp;
         if ((rc = S.get(R, &cp.perm)) || (rc = S.get(rows, &cp.S)) ||
             (run.t.S8 ? (rc = S.get(rows, &cp.S8)) : (rc = S.get(rows, &cp.Sb))) || (rc = S.get(R, &cp.T)) ||

@@ -450,3 +450,45 @@ def test_compaction_does_not_change_results(ctx, monkeypatch, precision):
     assert a.best_energy == b.best_energy and a.best_replica == b.best_replica
     assert a.kernel_launches > b.kernel_launches
     ctx.free(inst)
+
+
+def test_compaction_skipped_when_its_scratch_does_not_fit(monkeypatch):
+    """Compaction takes scratch only when it fits in the HBM budget: under the
+    smallest budget a solve needs without it (found by bisection), the
+    default solve still runs and returns the same results."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_05124_gb300 import build, mars
+    from paper_1907_05124_gb300.mars import MarsError
+    build.build()
+    n, R = 1024, 300
+    J = I.sk_pm1(n, 45)
+    m0, t0 = I.replica_inputs(R, n, 0.0, 8.0, 46)
+
+    def run(budget):
+        c = mars.Context(0, hbm_budget_bytes=budget)
+        try:
+            inst = c.add_dense(J)
+            return c.solve(inst, R, 0.0, 8.0, c_step=0.5, m0=m0, t0=t0, precision="bf16",
+                           outputs=("energies", "sweeps"))
+        except MarsError:
+            return None
+        finally:
+            c.close()
+
+    monkeypatch.setenv("MARS_TC_COMPACT", "0")
+    lo, hi = 1 << 20, 8 << 30
+    ref = run(hi)
+    assert ref is not None
+    while hi - lo > (1 << 20):
+        mid = (lo + hi) // 2
+        if run(mid) is not None:
+            hi = mid
+        else:
+            lo = mid
+    monkeypatch.setenv("MARS_TC_COMPACT", "1")
+    got = run(hi)
+    assert got is not None, "the default solve failed under the budget the solve itself needs"
+    assert np.array_equal(got.energies, ref.energies)
+    assert np.array_equal(got.replica_sweeps, ref.replica_sweeps)
