@@ -408,7 +408,7 @@ def fp32_path_comparison(ctx, n=1024, R=256, seeds=range(10)):
     Each path runs one solve of R replicas for every seed 0-9; a seed's time
     to target is its solve's wall time when the solve's best energy is at or
     below the target (within 1e-9 relative), else it is not reached. The
-    median over the seeds is reported when at least half reach the target;
+    median over the seeds is reported when more than half reach the target;
     with P the fraction of all replicas that reach it and t the mean solve
     time, t ln(0.01) / ln(1 - P) (the time to reach it with probability 0.99)
     is reported beside it, and the speedup uses the median where both paths
@@ -441,23 +441,39 @@ def fp32_path_comparison(ctx, n=1024, R=256, seeds=range(10)):
             hit.append(res.best_energy <= target + tol)
             reached += int(np.sum(res.energies <= target + tol))
             upd += res.spin_updates
-        P = reached / (R * len(secs))
-        t_sim = float(np.mean(secs))
-        ttt99 = t_sim * np.log(0.01) / np.log1p(-P) if 0 < P < 1 else (t_sim if P >= 1 else float("inf"))
-        ttt = sorted(s_ if h else float("inf") for s_, h in zip(secs, hit))
-        med = float(np.median(ttt)) if sum(hit) * 2 >= len(hit) else None
-        out[prec] = {"solve_s_mean": t_sim, "seeds_reaching_target": int(sum(hit)), "P": P,
-                     "ttt_median_s": med, "ttt99_s": ttt99,
-                     "spin_updates_per_s": upd / float(np.sum(secs))}
+        out[prec] = dict(ttt_summary(secs, hit, reached, R),
+                         spin_updates_per_s=upd / float(np.sum(secs)))
     ctx.free(inst)
-    a, b_ = out["fp32"], out["bf16"]
-    if a["ttt_median_s"] is not None and b_["ttt_median_s"] is not None:
-        out["speedup_at_equal_ttt"] = a["ttt_median_s"] / b_["ttt_median_s"]
-        out["speedup_from"] = "median over seeds 0-9"
-    else:
-        out["speedup_at_equal_ttt"] = a["ttt99_s"] / b_["ttt99_s"] if b_["ttt99_s"] > 0 else None
-        out["speedup_from"] = "t ln(0.01) / ln(1 - P)"
+    out.update(ttt_speedup(out["fp32"], out["bf16"]))
     return out
+
+
+def ttt_summary(secs, hit, reached, R):
+    """Time to target of one path from its per-seed solves: secs[i] is seed
+    i's solve time, hit[i] whether that solve's best reached the target, and
+    reached the number of replicas (R per solve) that reached it. The median
+    over seeds (a seed that missed counts as infinitely slow) when more than
+    half the seeds hit (so that the median is finite), else None; and t ln(0.01) / ln(1 - P), the time to
+    reach the target with probability 0.99 when a fraction P of replicas
+    reach it in a solve of mean time t."""
+    import numpy as np
+    P = reached / (R * len(secs))
+    t_sim = float(np.mean(secs))
+    ttt99 = t_sim * np.log(0.01) / np.log1p(-P) if 0 < P < 1 else (t_sim if P >= 1 else float("inf"))
+    ttt = sorted(s_ if h else float("inf") for s_, h in zip(secs, hit))
+    med = float(np.median(ttt)) if sum(hit) * 2 > len(hit) else None
+    return {"solve_s_mean": t_sim, "seeds_reaching_target": int(sum(hit)), "P": P,
+            "ttt_median_s": med, "ttt99_s": float(ttt99)}
+
+
+def ttt_speedup(slow, fast):
+    """The speedup at equal time to target: from the medians when both paths
+    have one, else from the probability form."""
+    if slow["ttt_median_s"] is not None and fast["ttt_median_s"] is not None:
+        return {"speedup_at_equal_ttt": slow["ttt_median_s"] / fast["ttt_median_s"],
+                "speedup_from": "median over seeds 0-9"}
+    sp = slow["ttt99_s"] / fast["ttt99_s"] if fast["ttt99_s"] > 0 else None
+    return {"speedup_at_equal_ttt": sp, "speedup_from": "t ln(0.01) / ln(1 - P)"}
 
 
 def run_mars(args, world, rank, local):

@@ -50,3 +50,38 @@ def test_workloads_listed():
     text = run_bench("--help", timeout=120)
     for name in ("ea2d", "ea3d_big", "sk8192", "sk8192pm1", "serve", "ttt", "batch", "sensitivity"):
         assert name in text, name
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_time_to_target_arithmetic():
+    """The time-to-target summary: the median over seeds counts a seed that
+    missed the target as infinitely slow and is reported only when more than
+    half the seeds hit; beside it t ln(0.01) / ln(1 - P); the speedup comes
+    from the medians when both exist, else from that form."""
+    import math
+    b = _bench_module()
+    secs = [1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 9.0, 10.0]
+    hit = [True] * 6 + [False] * 4
+    s = b.ttt_summary(secs, hit, reached=6, R=256)
+    assert s["ttt_median_s"] == 5.5  # sorted 1..6, inf x4: the 5th and 6th
+    P = 6 / 2560
+    assert s["P"] == P and s["seeds_reaching_target"] == 6
+    assert math.isclose(s["ttt99_s"], 5.5 * math.log(0.01) / math.log(1 - P), rel_tol=1e-12)
+    half = b.ttt_summary(secs, [True] * 5 + [False] * 5, reached=5, R=256)
+    assert half["ttt_median_s"] is None  # the median of five hits and five misses is not finite
+    never = b.ttt_summary(secs, [False] * 10, reached=0, R=256)
+    assert never["ttt99_s"] == math.inf and never["ttt_median_s"] is None
+    always = b.ttt_summary([2.0] * 10, [True] * 10, reached=2560, R=256)
+    assert always["ttt99_s"] == 2.0 and always["ttt_median_s"] == 2.0
+    fast = b.ttt_summary([0.5] * 10, hit, reached=6, R=256)
+    sp = b.ttt_speedup(s, fast)
+    assert sp["speedup_at_equal_ttt"] == 5.5 / 0.5 and sp["speedup_from"].startswith("median")
+    sp2 = b.ttt_speedup(half, fast)
+    assert math.isclose(sp2["speedup_at_equal_ttt"], half["ttt99_s"] / fast["ttt99_s"])
